@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark: finite-element sparse-matrix assembly on one GB300 (or N replicas).
+
+Workload (default): 64^3 trilinear Q1 hex mesh of the unit cube, 3 DOFs per
+node (823,875 DOFs, 262,144 elements), 24x24 FP64 isotropic-elasticity
+element matrices (E = 1, nu = 0.3, 2x2x2 Gauss), one materialised copy per
+element in HBM (1.21 GB).  One step = one pattern build (CSR + CRAC + slot
+maps + adjacency) followed by 10 numeric assemblies, inputs resident in HBM.
+
+Metric: element-matrix entries assembled per second (10 * 150,994,944 per
+step / step time), whole job.  Extra keys: the numeric kernel's HBM
+roofline fraction, per-variant times, end-to-end throughput through the C
+ABI with host buffers, and the serial CPU oracle as baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "element-matrix entries assembled/s"
+UNIT = "entries/s"
+N_ASSEMBLIES = 10
+VARIANTS = ("csr-atomic", "crac-atomic", "csr-det", "crac-det")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=64, help="hex mesh side (64 = the 64^3 elasticity workload)")
+    ap.add_argument("--variant", default="csr-det", choices=VARIANTS,
+                    help="numeric assembly used inside the timed step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    return ap.parse_args()
+
+
+def b_alg(n_e, n_loc, nnz):
+    """Bytes the numeric assembly must move: K read once, connectivity read
+    once, values written once."""
+    return 8 * n_e * n_loc * n_loc + 4 * n_e * n_loc + 8 * nnz
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("numeric.cu", "internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2012_00585_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current numeric kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    ent = d.get(kernel_key)
+    if not ent or ent.get("source_sha") != source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ GPU arm --
+
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import workloads as wl
+    from paper_2012_00585_gb300 import feasm
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = feasm.fe_create(local_rank)
+
+    n = args.n
+    D, n_dofs = wl.hex_q1_grid(n, 3)
+    n_e, n_loc = D.shape
+    N_ent = n_e * n_loc * n_loc
+    Kref = wl.elasticity_q1_hex(1.0 / n)
+    with torch.cuda.stream(stream):
+        Dd = torch.from_numpy(D).to(dev)
+        Kd = wl.broadcast_matrices(Kref, n_e, device=dev)
+    stream.synchronize()
+
+    fmt, mode_name = args.variant.split("-")
+    mode = feasm.FE_ATOMIC if mode_name == "atomic" else feasm.FE_DETERMINISTIC
+    assemble = feasm.fe_assemble_csr if fmt == "csr" else feasm.fe_assemble_crac
+
+    def build():
+        return feasm.fe_pattern_build(ctx, n_e, n_loc, n_dofs, Dd, feasm.FE_PATTERN_ALL, stream)
+
+    p0 = build()
+    info = feasm.fe_pattern_info_get(p0)
+    nnz = info["nnz"]
+    values = torch.empty(nnz, dtype=torch.float64, device=dev)
+    feasm.fe_pattern_free(p0)
+    B = b_alg(n_e, n_loc, nnz)
+
+    ev = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+          for _ in range(N_ASSEMBLIES * args.steps)]
+
+    def step(record=None):
+        p = build()
+        for a in range(N_ASSEMBLIES):
+            if record is not None:
+                record[a][0].record(stream)
+            assemble(ctx, p, Kd, values, mode, 0, stream)
+            if record is not None:
+                record[a][1].record(stream)
+        feasm.fe_pattern_free(p)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    launches0 = feasm.fe_kernel_launches()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for k in range(args.steps):
+        step(ev[k * N_ASSEMBLIES:(k + 1) * N_ASSEMBLIES])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = feasm.fe_kernel_launches() - launches0
+    if dist:
+        tdist.barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    value = world * N_ASSEMBLIES * N_ent / (ms * 1e-3)
+
+    # per-variant numeric times and the pattern build on its own
+    extra = {}
+    if not args.no_variants:
+        p = build()
+        var = {}
+        for vname in VARIANTS:
+            f, m = vname.split("-")
+            fn = feasm.fe_assemble_csr if f == "csr" else feasm.fe_assemble_crac
+            md = feasm.FE_ATOMIC if m == "atomic" else feasm.FE_DETERMINISTIC
+            for _ in range(3):
+                fn(ctx, p, Kd, values, md, 0, stream)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+            for a, b in evs:
+                a.record(stream)
+                fn(ctx, p, Kd, values, md, 0, stream)
+                b.record(stream)
+            torch.cuda.synchronize()
+            us = statistics.median(a.elapsed_time(b) for a, b in evs) * 1e3
+            var[vname] = {"us": round(us, 1), "alg_GBps": round(B / (us * 1e-6) / 1e9, 1),
+                          "Gentries_per_s": round(N_ent / (us * 1e-6) / 1e9, 2)}
+        feasm.fe_pattern_free(p)
+        pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for a, b in pe:
+            a.record(stream)
+            q = build()
+            b.record(stream)
+            feasm.fe_pattern_free(q)
+        torch.cuda.synchronize()
+        extra["variants"] = var
+        extra["pattern_build_ms"] = round(statistics.median(a.elapsed_time(b) for a, b in pe), 3)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, ctx, feasm, D, Kd, n_dofs, nnz, mode, assemble, stream, dev, world, dist)
+
+    hbm, src = measured_peaks()
+    achieved = B / (kern_ms * 1e-3) / 1e9
+    kkey = f"hex{n}_d3_{args.variant}"
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": recorded_traffic(kkey),
+                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.8 TB/s",
+                "kernel": f"fe_assemble_{fmt} {mode_name} (one call)", "alg_bytes_per_launch": B,
+                "kernel_ms": round(kern_ms, 4)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"hex Q1 {n}^3 elasticity, 3 DOF/node ({n_dofs} DOFs, {n_e} elements, 24x24 FP64 K)"
+                               f"; step = pattern build + {N_ASSEMBLIES} numeric assemblies ({args.variant})",
+                   "global_batch": world, "entries_per_assembly": N_ent, "nnz": nnz, "n_ca": info["n_ca"],
+                   "l2": "inputs larger than L2 (K = %.2f GB per assembly)" % (8 * N_ent / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "gpu_launches": int(launches),
+        "gpu_launches_per_step": launches / args.steps,
+    }
+    if clk:
+        out["clocks"] = clk
+    if e2e:
+        out["e2e"] = e2e
+    out.update(extra)
+    feasm.fe_destroy(ctx)
+    return out, (D, Kref, n_dofs)
+
+
+def run_e2e(args, ctx, feasm, D, Kd, n_dofs, nnz, mode, assemble, stream, dev, world, dist):
+    """Same step through the C ABI from pinned host buffers: H2D of the
+    connectivity and element matrices, pattern build, 10 assemblies, D2H of
+    the assembled CSR matrix (row_ptr, col_idx, values)."""
+    import torch
+    n_e, n_loc = D.shape
+    D_h = torch.from_numpy(D).pin_memory()
+    K_h = torch.empty(Kd.shape, dtype=torch.float64).pin_memory()
+    K_h.copy_(Kd.cpu())
+    D_d = torch.empty_like(D_h, device=dev)
+    K_d = torch.empty(Kd.shape, dtype=torch.float64, device=dev)
+    v_d = torch.empty(nnz, dtype=torch.float64, device=dev)
+    v_h = torch.empty(nnz, dtype=torch.float64).pin_memory()
+    rp_h = torch.empty(n_dofs + 1, dtype=torch.int64).pin_memory()
+    ci_h = torch.empty(nnz, dtype=torch.int32).pin_memory()
+
+    def step():
+        with torch.cuda.stream(stream):
+            D_d.copy_(D_h, non_blocking=True)
+            K_d.copy_(K_h, non_blocking=True)
+        p = feasm.fe_pattern_build(ctx, n_e, n_loc, n_dofs, D_d, feasm.FE_PATTERN_ALL, stream)
+        for _ in range(N_ASSEMBLIES):
+            assemble(ctx, p, K_d, v_d, mode, 0, stream)
+        rp_ptr, ci_ptr, _ = feasm.fe_pattern_csr(p)
+        with torch.cuda.stream(stream):
+            v_h.copy_(v_d, non_blocking=True)
+            rp_h.copy_(feasm.device_view(rp_ptr, n_dofs + 1, torch.int64), non_blocking=True)
+            ci_h.copy_(feasm.device_view(ci_ptr, nnz, torch.int32), non_blocking=True)
+        stream.synchronize()
+        feasm.fe_pattern_free(p)
+
+    for _ in range(3):
+        step()
+    steps = max(3, min(args.steps, 10))
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / steps
+    if dist:
+        import torch.distributed as tdist
+        t = torch.tensor([sec], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        sec = float(t.item())
+    h2d = D_h.numel() * 4 + K_h.numel() * 8
+    d2h = v_h.numel() * 8 + rp_h.numel() * 8 + ci_h.numel() * 4
+    return {"value": world * N_ASSEMBLIES * n_e * n_loc * n_loc / sec, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(sec * 1e3, 3)}
+
+
+# -------------------------------------------------------------- CPU oracle --
+
+def oracle_sample(n, n_numeric):
+    """Time the serial oracle on an n^3 elasticity mesh: pattern + CRAC once,
+    n_numeric assemblies.  Returns (t_pattern, t_numeric_each, N_ent)."""
+    import oracle
+    import workloads as wl
+    D, n_dofs = wl.hex_q1_grid(n, 3)
+    K = wl.broadcast_matrices(wl.elasticity_q1_hex(1.0 / n), D.shape[0])
+    t = time.perf_counter()
+    rp, ci = oracle.csr_pattern(D, n_dofs)
+    oracle.crac_from_csr(rp, ci, n_dofs)
+    t_pat = time.perf_counter() - t
+    t = time.perf_counter()
+    for _ in range(n_numeric):
+        oracle.assemble_csr(D, K, rp, ci)
+    t_num = (time.perf_counter() - t) / n_numeric
+    return t_pat, t_num, K.size
+
+
+def cpu_baseline(n):
+    t_pat, t_num, N_ent = oracle_sample(n, 2)
+    t_step = t_pat + N_ASSEMBLIES * t_num
+    return {"value": N_ASSEMBLIES * N_ent / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"hex Q1 {n}^3 elasticity: serial oracle pattern + CRAC once ({t_pat:.2f} s) and 2 numeric "
+                      f"assemblies ({t_num:.2f} s each), step time = pattern + {N_ASSEMBLIES} x numeric"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is a bounded sample (a
+    16^3 mesh of the same family: pattern + 10 assemblies)."""
+    import oracle
+    import workloads as wl
+    n = 16
+    D, n_dofs = wl.hex_q1_grid(n, 3)
+    K = wl.broadcast_matrices(wl.elasticity_q1_hex(1.0 / n), D.shape[0])
+
+    def step():
+        rp, ci = oracle.csr_pattern(D, n_dofs)
+        oracle.crac_from_csr(rp, ci, n_dofs)
+        for _ in range(N_ASSEMBLIES):
+            oracle.assemble_csr(D, K, rp, ci)
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    sec = (time.perf_counter() - t) / args.steps
+    value = N_ASSEMBLIES * K.size / sec
+    sample = f"hex Q1 {n}^3 elasticity (3 DOF/node, {D.shape[0]} elements): serial oracle pattern + CRAC + " \
+             f"{N_ASSEMBLIES} assemblies per step"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"hex Q1 {args.n}^3 elasticity, 3 DOF/node; step = pattern build + "
+                                   f"{N_ASSEMBLIES} numeric assemblies", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    out, _ = run_gpu(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.n)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

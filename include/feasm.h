@@ -1,0 +1,198 @@
+/*
+ * feasm.h -- C ABI of a GB300 (sm_103a) library that assembles dense finite
+ * element matrices into a global sparse matrix, after Sky et al., "A flexible
+ * sparse matrix data format and parallel algorithms for the assembly of
+ * sparse matrices in general finite element applications using atomic
+ * synchronisation primitives" (arXiv 2012.00585).
+ *
+ * The problem (§2.1): n_e elements, each with a dense row-major matrix K_e of
+ * n_loc x n_loc doubles and an element_dofs_array D_e of n_loc global DOF
+ * indices.  Assembly adds K_e(r, c) into G(D_e(r), D_e(c)) for every element
+ * (Listing 2).  G is stored in CSR or in CRAC (§2.2, Fig. 1); both share one
+ * values array.  The sparsity pattern is built once and reused by every
+ * numeric assembly; values are reset between assemblies (§3).
+ *
+ * Conventions
+ *   - Indices are 0-based.  DOFs are int32 in [0, n_dofs); n_dofs rows and
+ *     n_dofs columns.
+ *   - Pointers documented "device" must point to memory of the context's
+ *     device; "host" pointers to host memory.  Sizes are element counts.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls enqueue work on it and return without waiting, except
+ *     where stated.
+ *   - Every call returns FE_OK (0) or a negative FE_ERR_* code; no exception
+ *     crosses this boundary and no kernel traps.  fe_strerror() names a code.
+ *   - Not thread-safe per context unless stated; distinct contexts are
+ *     independent.
+ */
+#ifndef FEASM_H
+#define FEASM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define FE_OK 0
+#define FE_ERR_INVALID_ARG (-1)   /* bad pointer, size or flag                 */
+#define FE_ERR_DOF_RANGE (-2)     /* a DOF outside [0, n_dofs)                 */
+#define FE_ERR_DUP_DOF (-3)       /* a DOF listed twice in one element         */
+#define FE_ERR_OVERFLOW (-4)      /* nnz or n_ca >= 2^31, or n_e*n_loc >= 2^32 */
+#define FE_ERR_OOM (-5)           /* device allocation failed                  */
+#define FE_ERR_ADMISSION (-6)     /* request larger than the HBM budget        */
+#define FE_ERR_TIMEOUT (-7)       /* a bounded device or host wait ran out     */
+#define FE_ERR_DEVICE (-8)        /* a CUDA call failed                        */
+#define FE_ERR_NOT_BUILT (-9)     /* the pattern lacks the requested part      */
+#define FE_ERR_UNSUPPORTED (-10)  /* size beyond an implementation limit       */
+#define FE_ERR_NOT_FOUND (-11)    /* unknown ticket                            */
+#define FE_ERR_CANCELLED (-12)    /* request cancelled before it ran           */
+
+/* Largest element supported (DOFs per element). */
+#define FE_MAX_NLOC 128
+
+/* ---- pattern parts (fe_pattern_build flags) ----------------------------- */
+#define FE_PATTERN_CSR 0x1u       /* row_ptr + col_idx (always built)          */
+#define FE_PATTERN_CRAC 0x2u      /* CRAC row pointers + column alignments     */
+#define FE_PATTERN_MAP_CSR 0x4u   /* per-entry slot map for fe_assemble_csr    */
+#define FE_PATTERN_MAP_CRAC 0x8u  /* per-run slot map for fe_assemble_crac     */
+#define FE_PATTERN_ADJ 0x10u      /* DOF -> (element, local row) adjacency,
+                                     needed by FE_DETERMINISTIC               */
+#define FE_PATTERN_ALL 0x1Fu
+
+/* ---- numeric modes ------------------------------------------------------ */
+#define FE_ATOMIC 0         /* element-parallel scatter with FP64 atomic adds
+                               (Listing 3); sum order is unspecified          */
+#define FE_DETERMINISTIC 1  /* row-parallel gather, no atomics; every value is
+                               summed in ascending element order from +0.0
+                               (Listing 2's order), bit-reproducible          */
+
+typedef struct fe_ctx fe_ctx;
+typedef struct fe_pattern fe_pattern;
+
+typedef struct fe_pattern_info {
+    int64_t n_elem;        /* n_e                                          */
+    int32_t n_loc;         /* DOFs per element                             */
+    int32_t map_bytes;     /* 1 or 2: width of the slot-map entries        */
+    int64_t n_dofs;        /* rows = columns                               */
+    int64_t nnz;           /* CSR entries = length of the values array     */
+    int64_t n_ca;          /* length of the CRAC column-alignments array   */
+    int64_t n_elem_runs;   /* sum over elements of maximal DOF runs (§2.1) */
+    int32_t max_row_len;   /* longest CSR row                              */
+    int32_t max_degree;    /* most elements sharing one DOF                */
+    uint32_t flags;        /* parts that were built                        */
+    uint32_t reserved;
+    int64_t device_bytes;  /* device memory held by the pattern            */
+} fe_pattern_info;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  `hbm_budget_bytes` bounds the
+ * device memory the batching/serving scheduler admits at once (0 = 90 % of
+ * the device's free memory at creation).  The context owns a stream-ordered
+ * memory pool for patterns and workspace.  *out receives the handle. */
+int fe_create(fe_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Destroy a context: waits for its device work, then frees its memory.  Every
+ * pattern created from it must have been freed. */
+int fe_destroy(fe_ctx *ctx);
+
+/* Static string for an FE_* code (never NULL). */
+const char *fe_strerror(int code);
+
+/* Text of the last CUDA error this thread's calls met (for FE_ERR_DEVICE /
+ * FE_ERR_OOM diagnostics); empty when there was none.  Never NULL. */
+const char *fe_last_cuda_error(void);
+
+/* Number of kernels this library has launched in this process so far (all
+ * contexts and threads); a caller brackets a region with two reads to count
+ * the launches inside it. */
+uint64_t fe_kernel_launches(void);
+
+/* ---- symbolic phase ----------------------------------------------------- */
+
+/*
+ * Build the sparsity pattern of the matrix assembled from `n_elem` elements
+ * with `dofs_per_elem` DOFs each (§3: "initialisation of the sparse matrix",
+ * done once; §2.2 for CSR and CRAC).
+ *   elem_dofs  device, int32 [n_elem * dofs_per_elem], row-major, element e's
+ *              DOFs in local order (the element_dofs_array of §2.1).  Read
+ *              only; the pattern keeps its own copy.
+ *   n_dofs     number of rows (= columns); DOFs no element lists give empty
+ *              rows.
+ *   flags      FE_PATTERN_* parts to build (CSR is always built).
+ *   stream     all work is ordered on it; the call blocks twice on it to size
+ *              the outputs (after validation and after counting the rows),
+ *              then returns with the rest enqueued.
+ *   out        receives a pattern owned by the library; free with
+ *              fe_pattern_free.
+ * Errors: FE_ERR_DOF_RANGE / FE_ERR_DUP_DOF for bad connectivity (nothing is
+ * allocated), FE_ERR_OVERFLOW, FE_ERR_UNSUPPORTED (dofs_per_elem >
+ * FE_MAX_NLOC or a DOF shared by too many elements), FE_ERR_OOM.
+ */
+int fe_pattern_build(fe_ctx *ctx, int64_t n_elem, int32_t dofs_per_elem, int64_t n_dofs,
+                     const int32_t *elem_dofs, uint32_t flags, void *stream,
+                     fe_pattern **out);
+
+/* Release a pattern.  Waits for the device to finish pending work first. */
+int fe_pattern_free(fe_pattern *pattern);
+
+/* Borrowed device pointers to the CSR arrays (§2.2, Fig. 1c): row_ptr int64
+ * [n_dofs + 1], col_idx int32 [nnz] sorted ascending within each row.  Valid
+ * until fe_pattern_free.  Any output pointer may be NULL. */
+int fe_pattern_csr(const fe_pattern *pattern, const int64_t **row_ptr, const int32_t **col_idx,
+                   int64_t *nnz);
+
+/* Borrowed device pointers to the CRAC arrays (§2.2, Fig. 1d): row_ptr int64
+ * [n_dofs + 1] in int units of col_align; col_align int32 [n_ca] holding, per
+ * maximal run of consecutive columns of a row, the pair (first column, value
+ * position), followed by the final pair (n_dofs, nnz).  n_ca = 2*(runs+1).
+ * FE_ERR_NOT_BUILT without FE_PATTERN_CRAC. */
+int fe_pattern_crac(const fe_pattern *pattern, const int64_t **row_ptr, const int32_t **col_align,
+                    int64_t *n_ca);
+
+/* Borrowed device pointer to the DOF adjacency: adj_ptr int64 [n_dofs + 1],
+ * adj uint32 [n_elem * dofs_per_elem] holding e*dofs_per_elem + r for every
+ * element e whose local DOF r is the row, ascending.  FE_ERR_NOT_BUILT
+ * without FE_PATTERN_ADJ. */
+int fe_pattern_adjacency(const fe_pattern *pattern, const int64_t **adj_ptr, const uint32_t **adj);
+
+/* Sizes and parts of a pattern. */
+int fe_pattern_info_get(const fe_pattern *pattern, fe_pattern_info *out);
+
+/* ---- numeric phase ------------------------------------------------------ */
+
+/*
+ * Assemble the element matrices into the CSR values array (Listing 2 for the
+ * result; Listing 3 for FE_ATOMIC).
+ *   elem_mats  device, double [n_elem * n_loc * n_loc]: K_e row-major, element
+ *              after element.  Read only.
+ *   values     device, double [nnz], caller-owned; entry k belongs to
+ *              (row of k, col_idx[k]).
+ *   mode       FE_ATOMIC (needs FE_PATTERN_MAP_CSR) or FE_DETERMINISTIC (needs
+ *              FE_PATTERN_MAP_CSR and FE_PATTERN_ADJ).
+ *   accumulate 0: values are overwritten (reset to zero first, §3);
+ *              1: contributions are added to the values already there.
+ * Asynchronous on `stream`.  FE_DETERMINISTIC reproduces the oracle's
+ * ascending-element sum bit for bit; FE_ATOMIC agrees within rounding.
+ */
+int fe_assemble_csr(fe_ctx *ctx, const fe_pattern *pattern, const double *elem_mats,
+                    double *values, int mode, int accumulate, void *stream);
+
+/*
+ * The same assembly located through the CRAC arrays and the compressed DOF
+ * runs of each element (§2.1, §2.2, Listing 5's slices): one slot look-up per
+ * run of consecutive DOFs instead of one per entry.  The values array has the
+ * CSR order (Fig. 1c and 1d share it).  Needs FE_PATTERN_CRAC and
+ * FE_PATTERN_MAP_CRAC (and FE_PATTERN_ADJ for FE_DETERMINISTIC).
+ */
+int fe_assemble_crac(fe_ctx *ctx, const fe_pattern *pattern, const double *elem_mats,
+                     double *values, int mode, int accumulate, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEASM_H */

@@ -1,0 +1,89 @@
+// Internal definitions shared by the translation units of libfeasm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+
+#include "../../include/feasm.h"
+
+#define FE_WARP 32
+
+// Return FE_ERR_DEVICE from the enclosing function when a CUDA call fails.
+#define FE_CUDA(call)                                      \
+    do {                                                   \
+        cudaError_t fe_e_ = (call);                        \
+        if (fe_e_ != cudaSuccess) {                        \
+            fe_set_last_cuda_error(fe_e_, #call, __LINE__); \
+            return fe_e_ == cudaErrorMemoryAllocation ? FE_ERR_OOM : FE_ERR_DEVICE; \
+        }                                                  \
+    } while (0)
+
+#define FE_TRY(expr)                 \
+    do {                             \
+        int fe_rc_ = (expr);         \
+        if (fe_rc_ != FE_OK) return fe_rc_; \
+    } while (0)
+
+void fe_set_last_cuda_error(cudaError_t e, const char *what, int line);
+
+struct fe_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t hbm_budget = 0;
+    cudaMemPool_t pool = nullptr;
+    struct fe_batch_state *batch = nullptr;  // batching / serving scheduler
+};
+
+struct fe_pattern {
+    fe_ctx *ctx = nullptr;
+    int64_t n_e = 0;
+    int32_t n_loc = 0;
+    int32_t mask_words = 0;   // 32-bit words per element in run_mask
+    int64_t n_dofs = 0;
+    int64_t nnz = 0;
+    int64_t n_ca = 0;
+    int64_t n_runs = 0;       // sum over elements of DOF runs
+    int32_t max_row_len = 0;
+    int32_t max_deg = 0;
+    int32_t map_bytes = 1;
+    uint32_t flags = 0;
+    int64_t device_bytes = 0;
+    bool uniform_runs = false;  // every element has the same run mask
+    int32_t runs_per_elem = 0;  // valid when uniform_runs
+
+    int32_t *elem_dofs = nullptr;  // [n_e * n_loc]
+    int64_t *row_ptr = nullptr;    // [n_dofs + 1]
+    int32_t *col_idx = nullptr;    // [nnz]
+    int64_t *crac_ptr = nullptr;   // [n_dofs + 1], int units
+    int32_t *col_align = nullptr;  // [n_ca]
+    int64_t *adj_ptr = nullptr;    // [n_dofs + 1]
+    uint32_t *adj = nullptr;       // [n_e * n_loc]
+    void *map_csr = nullptr;       // [n_e * n_loc * n_loc] uint8 / uint16
+    uint32_t *run_mask = nullptr;  // [n_e * mask_words]
+    int64_t *run_ptr = nullptr;    // [n_e + 1]
+    void *map_crac = nullptr;      // [n_runs * n_loc] uint8 / uint16
+};
+
+void fe_batch_state_destroy(fe_ctx *ctx);
+
+// Host-side count of kernel launches made by this library (all threads).
+void fe_note_launch();
+
+// Stream-ordered allocation from the context's pool.
+int fe_alloc(fe_ctx *ctx, void **p, size_t bytes, cudaStream_t s);
+void fe_free_async(void *p, cudaStream_t s);
+
+// Exclusive scan of n counts into out[0..n]; out[n] = total.
+int fe_scan_i32_to_i64(fe_ctx *ctx, const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+int fe_scan_i64(fe_ctx *ctx, const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+
+static inline int fe_grid_for(int64_t work, int threads, int num_sms, int per_sm = 8)
+{
+    int64_t blocks = (work + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return (int)blocks;
+}

@@ -1,0 +1,262 @@
+"""ctypes binding of libfeasm (include/feasm.h), same names as the C ABI.
+
+Argument marshalling only: every step of the assembly runs in the CUDA
+library.  Device buffers are passed as torch CUDA tensors (or raw integer
+device addresses); streams as torch.cuda.Stream, raw cudaStream_t integers,
+or None for torch's current stream.  There is no CPU fallback: if the CUDA
+library cannot be loaded, every call raises.
+"""
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+FE_OK = 0
+FE_ERR_INVALID_ARG = -1
+FE_ERR_DOF_RANGE = -2
+FE_ERR_DUP_DOF = -3
+FE_ERR_OVERFLOW = -4
+FE_ERR_OOM = -5
+FE_ERR_ADMISSION = -6
+FE_ERR_TIMEOUT = -7
+FE_ERR_DEVICE = -8
+FE_ERR_NOT_BUILT = -9
+FE_ERR_UNSUPPORTED = -10
+FE_ERR_NOT_FOUND = -11
+FE_ERR_CANCELLED = -12
+FE_MAX_NLOC = 128
+
+FE_PATTERN_CSR = 0x1
+FE_PATTERN_CRAC = 0x2
+FE_PATTERN_MAP_CSR = 0x4
+FE_PATTERN_MAP_CRAC = 0x8
+FE_PATTERN_ADJ = 0x10
+FE_PATTERN_ALL = 0x1F
+
+FE_ATOMIC = 0
+FE_DETERMINISTIC = 1
+
+_lib = None
+_lock = threading.Lock()
+
+
+class FeError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = int(code)
+        msg = fe_strerror(code) if _lib is not None else f"error {code}"
+        detail = ""
+        if self.code == FE_ERR_DEVICE and _lib is not None:
+            detail = " [" + _lib.fe_last_cuda_error().decode() + "]"
+        super().__init__(f"{where}: {msg} ({code}){detail}")
+
+
+class fe_pattern_info(ctypes.Structure):
+    _fields_ = [
+        ("n_elem", ctypes.c_int64),
+        ("n_loc", ctypes.c_int32),
+        ("map_bytes", ctypes.c_int32),
+        ("n_dofs", ctypes.c_int64),
+        ("nnz", ctypes.c_int64),
+        ("n_ca", ctypes.c_int64),
+        ("n_elem_runs", ctypes.c_int64),
+        ("max_row_len", ctypes.c_int32),
+        ("max_degree", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("device_bytes", ctypes.c_int64),
+    ]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load the CUDA library (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libfeasm not found at {path}; the CUDA path has no fallback")
+        lib = ctypes.CDLL(path)
+        vp, i64, i32, u32, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int
+        pp = ctypes.POINTER(vp)
+        sig = {
+            "fe_create": (i, [pp, i, ctypes.c_size_t]),
+            "fe_destroy": (i, [vp]),
+            "fe_strerror": (ctypes.c_char_p, [i]),
+            "fe_last_cuda_error": (ctypes.c_char_p, []),
+            "fe_kernel_launches": (ctypes.c_uint64, []),
+            "fe_pattern_build": (i, [vp, i64, i32, i64, vp, u32, vp, pp]),
+            "fe_pattern_free": (i, [vp]),
+            "fe_pattern_csr": (i, [vp, pp, pp, ctypes.POINTER(i64)]),
+            "fe_pattern_crac": (i, [vp, pp, pp, ctypes.POINTER(i64)]),
+            "fe_pattern_adjacency": (i, [vp, pp, pp]),
+            "fe_pattern_info_get": (i, [vp, ctypes.POINTER(fe_pattern_info)]),
+            "fe_assemble_csr": (i, [vp, vp, vp, vp, i, i, vp]),
+            "fe_assemble_crac": (i, [vp, vp, vp, vp, i, i, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc, where):
+    if rc != FE_OK:
+        raise FeError(rc, where)
+
+
+def _addr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a device pointer")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def fe_strerror(code: int) -> str:
+    return load().fe_strerror(int(code)).decode()
+
+
+def fe_last_cuda_error() -> str:
+    return load().fe_last_cuda_error().decode()
+
+
+def fe_kernel_launches() -> int:
+    return int(load().fe_kernel_launches())
+
+
+def fe_create(device: int = 0, hbm_budget_bytes: int = 0):
+    out = ctypes.c_void_p()
+    _check(load().fe_create(ctypes.byref(out), int(device), int(hbm_budget_bytes)), "fe_create")
+    return out
+
+
+def fe_destroy(ctx):
+    _check(load().fe_destroy(ctx), "fe_destroy")
+
+
+def fe_pattern_build(ctx, n_elem, dofs_per_elem, n_dofs, elem_dofs, flags=FE_PATTERN_ALL, stream=None):
+    if hasattr(elem_dofs, "dtype"):
+        import torch
+        if elem_dofs.dtype != torch.int32:
+            raise TypeError("elem_dofs must be int32")
+    out = ctypes.c_void_p()
+    _check(load().fe_pattern_build(ctx, int(n_elem), int(dofs_per_elem), int(n_dofs), _addr(elem_dofs),
+                                   int(flags), _stream(stream), ctypes.byref(out)), "fe_pattern_build")
+    return out
+
+
+def fe_pattern_free(pattern):
+    _check(load().fe_pattern_free(pattern), "fe_pattern_free")
+
+
+def fe_pattern_csr(pattern):
+    rp, ci, nnz = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
+    _check(load().fe_pattern_csr(pattern, ctypes.byref(rp), ctypes.byref(ci), ctypes.byref(nnz)), "fe_pattern_csr")
+    return rp.value, ci.value, nnz.value
+
+
+def fe_pattern_crac(pattern):
+    rp, ca, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
+    _check(load().fe_pattern_crac(pattern, ctypes.byref(rp), ctypes.byref(ca), ctypes.byref(n)), "fe_pattern_crac")
+    return rp.value, ca.value, n.value
+
+
+def fe_pattern_adjacency(pattern):
+    ap, a = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load().fe_pattern_adjacency(pattern, ctypes.byref(ap), ctypes.byref(a)), "fe_pattern_adjacency")
+    return ap.value, a.value
+
+
+def fe_pattern_info_get(pattern) -> dict:
+    info = fe_pattern_info()
+    _check(load().fe_pattern_info_get(pattern, ctypes.byref(info)), "fe_pattern_info_get")
+    return {name: getattr(info, name) for name, _ in fe_pattern_info._fields_}
+
+
+def fe_assemble_csr(ctx, pattern, elem_mats, values, mode=FE_ATOMIC, accumulate=0, stream=None):
+    _check(load().fe_assemble_csr(ctx, pattern, _addr(elem_mats), _addr(values), int(mode), int(accumulate),
+                                  _stream(stream)), "fe_assemble_csr")
+
+
+def fe_assemble_crac(ctx, pattern, elem_mats, values, mode=FE_ATOMIC, accumulate=0, stream=None):
+    _check(load().fe_assemble_crac(ctx, pattern, _addr(elem_mats), _addr(values), int(mode), int(accumulate),
+                                   _stream(stream)), "fe_assemble_crac")
+
+
+# ---- views of library-owned device arrays --------------------------------
+
+class _DeviceArray:
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr or 0), False),
+                                         "version": 2, "strides": None}
+
+
+def device_view(ptr, n, dtype):
+    """A torch CUDA tensor aliasing n elements at a library-owned address."""
+    import torch
+    typestr = {torch.int64: "<i8", torch.int32: "<i4", torch.uint32: "<u4", torch.float64: "<f8",
+               torch.uint8: "|u1"}[dtype]
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    return torch.as_tensor(_DeviceArray(ptr, n, typestr), device="cuda")
+
+
+class Pattern:
+    """Owns an fe_pattern handle; exposes its arrays as torch views."""
+
+    def __init__(self, ctx, elem_dofs, n_dofs, flags=FE_PATTERN_ALL, stream=None):
+        n_e, n_loc = elem_dofs.shape
+        self.ctx = ctx
+        self.handle = fe_pattern_build(ctx, n_e, n_loc, n_dofs, elem_dofs, flags, stream)
+        self.info = fe_pattern_info_get(self.handle)
+
+    def csr(self):
+        import torch
+        rp, ci, nnz = fe_pattern_csr(self.handle)
+        return device_view(rp, self.info["n_dofs"] + 1, torch.int64), device_view(ci, nnz, torch.int32)
+
+    def crac(self):
+        import torch
+        rp, ca, n = fe_pattern_crac(self.handle)
+        return device_view(rp, self.info["n_dofs"] + 1, torch.int64), device_view(ca, n, torch.int32)
+
+    def adjacency(self):
+        import torch
+        ap, a = fe_pattern_adjacency(self.handle)
+        n_inc = self.info["n_elem"] * self.info["n_loc"]
+        return device_view(ap, self.info["n_dofs"] + 1, torch.int64), device_view(a, n_inc, torch.uint32)
+
+    def free(self):
+        if self.handle is not None:
+            fe_pattern_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,290 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle.
+
+Bar: the pattern (CSR, CRAC, adjacency) bit-exact; FE_DETERMINISTIC values
+bit-exact (same ascending-element sum as Listing 2); FE_ATOMIC values within
+|d| <= 1e-12 * sum_j |G_ij| per row, and bit-exact when every sum is an exact
+integer (the paper's all-ones element).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2012_00585_gb300 import feasm
+    c = feasm.fe_create(0)
+    yield c
+    feasm.fe_destroy(c)
+
+
+def _check_pattern(g, D, n_dofs):
+    rp_o, ci_o = oracle.csr_pattern(D, n_dofs)
+    rp, ci = g.csr_host()
+    assert np.array_equal(rp, rp_o)
+    assert np.array_equal(ci, ci_o)
+    crp_o, ca_o = oracle.crac_from_csr(rp_o, ci_o, n_dofs)
+    crp, ca = g.crac_host()
+    assert np.array_equal(crp, crp_o)
+    assert np.array_equal(ca, ca_o)
+    ap, adj = [x.cpu().numpy() for x in g.pattern.adjacency()]
+    deg = np.bincount(D.ravel(), minlength=n_dofs)
+    assert np.array_equal(np.diff(ap), deg)
+    n_loc = D.shape[1]
+    inc = np.arange(D.size, dtype=np.int64)
+    order = np.argsort(D.ravel(), kind="stable")  # stable: ascending incidence id per DOF
+    assert np.array_equal(adj.astype(np.int64), inc[order])
+    info = g.pattern.info
+    assert info["nnz"] == rp_o[-1] and info["n_ca"] == ca_o.shape[0]
+    assert info["max_row_len"] == int(np.max(np.diff(rp_o))) if n_dofs else True
+    assert info["n_elem_runs"] == sum(len(oracle.compress_dofs(row)) // 2 for row in D) or n_loc > 64
+    return rp_o, ci_o, crp_o, ca_o
+
+
+def _run_all_modes(g, D, K, n_dofs, rp_o, ci_o, crp_o, ca_o, exact_atomic=False):
+    from paper_2012_00585_gb300 import feasm
+    v_o = oracle.assemble_csr(D, K, rp_o, ci_o)
+    v_oc = oracle.assemble_crac(D, K, crp_o, ca_o, ci_o.shape[0])
+    assert np.array_equal(v_o, v_oc)
+    tau = gu.row_tolerance(rp_o, v_o, gu.contribution_abs_row_sums(D, K, n_dofs))
+    out = {}
+    for fmt in ("csr", "crac"):
+        det = g.assemble(K, fmt, feasm.FE_DETERMINISTIC).cpu().numpy()
+        assert np.array_equal(det.view(np.uint64), v_o.view(np.uint64)), f"{fmt} deterministic not bit-exact"
+        at = g.assemble(K, fmt, feasm.FE_ATOMIC).cpu().numpy()
+        if exact_atomic:
+            assert np.array_equal(at, v_o)
+        else:
+            gu.assert_within_row_tol(rp_o, at, v_o, tau)
+        out[fmt] = (det, at)
+    return v_o, out
+
+
+# ------------------------------------------------------------ configs ---
+
+def test_c1_quad_laplace_16x16(ctx):
+    """Config 1: 16x16 Q1 quads, 1 DOF/node, 4x4 Laplace by 2x2 Gauss."""
+    D, n_dofs = wl.quad_q1_grid(16, 1)
+    K = wl.broadcast_matrices(wl.laplace_q1_quad(), D.shape[0])
+    g = gu.GpuAssembly(ctx, D, n_dofs)
+    pat = _check_pattern(g, D, n_dofs)
+    assert g.pattern.info["nnz"] == 2401 and g.pattern.info["n_ca"] == 1668
+    v_o, _ = _run_all_modes(g, D, K, n_dofs, *pat)
+    g.free()
+
+
+@pytest.mark.parametrize("n", [4, 9])
+def test_c2_hex_elasticity_small(ctx, n):
+    """Config 2's mesh family at reduced size (several tiles, ragged tail)."""
+    D, n_dofs = wl.hex_q1_grid(n, 3)
+    K = wl.broadcast_matrices(wl.elasticity_q1_hex(1.0 / n), D.shape[0])
+    K[3, 5, 7] += 0.125  # one perturbed element: no kernel may assume K is uniform
+    K[3, 7, 5] += 0.125
+    g = gu.GpuAssembly(ctx, D, n_dofs)
+    pat = _check_pattern(g, D, n_dofs)
+    assert g.pattern.info["nnz"] == 9 * (3 * n + 1) ** 3
+    _run_all_modes(g, D, K, n_dofs, *pat)
+    g.free()
+
+
+@pytest.mark.parametrize("n", [2, 4])
+def test_c3_p2_tets_permuted_spd(ctx, n):
+    """Config 3's generator at reduced size: permuted P2 tets, random SPD 30x30."""
+    D, n_dofs = wl.tet_p2_kuhn(n, d=3, seed=n)
+    K = wl.random_spd_matrices(D.shape[0], 30, seed=n)
+    g = gu.GpuAssembly(ctx, D, n_dofs)
+    pat = _check_pattern(g, D, n_dofs)
+    assert not g.pattern.info["reserved"]  # run structure varies per element
+    _run_all_modes(g, D, K, n_dofs, *pat)
+    g.free()
+
+
+def test_c4_mixed_sizes_one_by_one(ctx):
+    """Config 4's two element kinds: Q1 Laplace (8x8, d=1) and elasticity (24x24)."""
+    for n, d in [(5, 1), (7, 1), (5, 3), (6, 3)]:
+        D, n_dofs = wl.hex_q1_grid(n, d)
+        Kr = wl.laplace_q1_hex(1.0 / n) if d == 1 else wl.elasticity_q1_hex(1.0 / n)
+        K = wl.scaled_matrices(Kr, D.shape[0], seed=n)
+        g = gu.GpuAssembly(ctx, D, n_dofs)
+        pat = _check_pattern(g, D, n_dofs)
+        _run_all_modes(g, D, K, n_dofs, *pat)
+        g.free()
+
+
+@pytest.mark.slow
+def test_c2_full_size_64cubed(ctx):
+    """Config 2 at full size (262,144 hexes, 823,875 DOFs), every entry."""
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    n = 64
+    D, n_dofs = wl.hex_q1_grid(n, 3)
+    assert n_dofs == 823_875
+    Kr = wl.elasticity_q1_hex(1.0 / n)
+    g = gu.GpuAssembly(ctx, D, n_dofs)
+    info = g.pattern.info
+    assert info["nnz"] == 64_701_513 and info["n_ca"] == 14_527_112
+    rp_o, ci_o = oracle.csr_pattern(D, n_dofs)
+    rp, ci = g.csr_host()
+    assert np.array_equal(rp, rp_o) and np.array_equal(ci, ci_o)
+    crp_o, ca_o = oracle.crac_from_csr(rp_o, ci_o, n_dofs)
+    crp, ca = g.crac_host()
+    assert np.array_equal(crp, crp_o) and np.array_equal(ca, ca_o)
+    Kd = wl.broadcast_matrices(Kr, D.shape[0], device="cuda")
+    K = Kd.cpu().numpy()
+    v_o = oracle.assemble_csr(D, K, rp_o, ci_o)
+    tau = gu.row_tolerance(rp_o, v_o, gu.contribution_abs_row_sums(D, K, n_dofs))
+    for fmt in ("csr", "crac"):
+        det = g.assemble(Kd, fmt, feasm.FE_DETERMINISTIC).cpu().numpy()
+        assert np.array_equal(det.view(np.uint64), v_o.view(np.uint64))
+        at = g.assemble(Kd, fmt, feasm.FE_ATOMIC).cpu().numpy()
+        gu.assert_within_row_tol(rp_o, at, v_o, tau)
+    del Kd
+    torch.cuda.empty_cache()
+    g.free()
+
+
+# --------------------------------------------------------- edge cases ---
+
+def test_all_ones_atomic_is_exact(ctx):
+    """Paper's dummy element: integer sums, so atomic order cannot matter."""
+    D, n_dofs = wl.tet_p2_kuhn(3, d=2, seed=1)
+    K = wl.ones_matrices(*D.shape[:1], D.shape[1])
+    g = gu.GpuAssembly(ctx, D, n_dofs)
+    pat = _check_pattern(g, D, n_dofs)
+    _run_all_modes(g, D, K, n_dofs, *pat, exact_atomic=True)
+    g.free()
+
+
+@pytest.mark.parametrize("case", ["qp3_d1", "qp2_d4", "hex_d2", "q8_rows_over_256", "d20_quad",
+                                  "scattered", "single", "unused_dofs"])
+def test_generic_sizes_and_layouts(ctx, case):
+    """Element sizes without a specialised kernel (9, 36, 16, 81, 80, ...),
+    rows longer than 256 (16-bit slot maps), scattered DOFs, empty rows."""
+    rng = np.random.default_rng(0)
+    if case == "qp3_d1":
+        D, n_dofs = wl.quad_qp_grid(5, 3, 1)          # n_loc 16
+    elif case == "qp2_d4":
+        D, n_dofs = wl.quad_qp_grid(4, 2, 4)          # n_loc 36
+    elif case == "hex_d2":
+        D, n_dofs = wl.hex_q1_grid(4, 2)              # n_loc 16
+    elif case == "q8_rows_over_256":
+        D, n_dofs = wl.quad_qp_grid(3, 8, 1)          # n_loc 81, rows up to 289
+    elif case == "d20_quad":
+        D, n_dofs = wl.quad_q1_grid(3, 20)            # n_loc 80
+    elif case == "scattered":
+        D = np.stack([rng.choice(500, size=9, replace=False) for _ in range(300)]).astype(np.int32)
+        n_dofs = 520
+    elif case == "single":
+        D, n_dofs = np.array([[3, 1, 2]], dtype=np.int32), 4
+    else:
+        D = np.array([[0, 1, 5, 6], [5, 6, 9, 10], [0, 1, 9, 10]], dtype=np.int32)
+        n_dofs = 14
+    K = wl.random_matrices(D.shape[0], D.shape[1], seed=3)
+    g = gu.GpuAssembly(ctx, D, n_dofs)
+    if case == "q8_rows_over_256":
+        assert g.pattern.info["map_bytes"] == 2
+    pat = _check_pattern(g, D, n_dofs)
+    _run_all_modes(g, D, K, n_dofs, *pat)
+    g.free()
+
+
+def test_accumulate_both_modes(ctx):
+    from paper_2012_00585_gb300 import feasm
+    D, n_dofs = wl.tet_p2_kuhn(2, d=3, seed=9)
+    K1 = wl.random_spd_matrices(D.shape[0], 30, seed=1)
+    K2 = wl.random_spd_matrices(D.shape[0], 30, seed=2)
+    g = gu.GpuAssembly(ctx, D, n_dofs)
+    rp, ci = oracle.csr_pattern(D, n_dofs)
+    v1 = oracle.assemble_csr(D, K1, rp, ci)
+    v12 = oracle.assemble_csr(D, K2, rp, ci, values=v1)
+    for fmt in ("csr", "crac"):
+        base = g.assemble(K1, fmt, feasm.FE_DETERMINISTIC)
+        got = g.assemble(K2, fmt, feasm.FE_DETERMINISTIC, accumulate=1, values=base).cpu().numpy()
+        assert np.array_equal(got, v12)
+        base = g.assemble(K1, fmt, feasm.FE_ATOMIC)
+        got = g.assemble(K2, fmt, feasm.FE_ATOMIC, accumulate=1, values=base).cpu().numpy()
+        tau = gu.row_tolerance(rp, v12)
+        gu.assert_within_row_tol(rp, got, v12, 2 * tau)
+    g.free()
+
+
+def test_deterministic_is_reproducible_and_formats_agree(ctx):
+    from paper_2012_00585_gb300 import feasm
+    D, n_dofs = wl.tet_p2_kuhn(3, d=3, seed=4)
+    K = wl.random_spd_matrices(D.shape[0], 30, seed=4)
+    g = gu.GpuAssembly(ctx, D, n_dofs)
+    a = g.assemble(K, "csr", feasm.FE_DETERMINISTIC).cpu().numpy()
+    b = g.assemble(K, "csr", feasm.FE_DETERMINISTIC).cpu().numpy()
+    c = g.assemble(K, "crac", feasm.FE_DETERMINISTIC).cpu().numpy()
+    assert a.tobytes() == b.tobytes() == c.tobytes()
+    g.free()
+
+
+def test_empty_mesh(ctx):
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    Dd = torch.empty((0, 4), dtype=torch.int32, device="cuda")
+    p = feasm.Pattern(ctx, Dd, 5)
+    assert p.info["nnz"] == 0 and p.info["n_ca"] == 2
+    rp, ci = p.csr()
+    assert rp.cpu().tolist() == [0] * 6
+    crp, ca = p.crac()
+    assert ca.cpu().tolist() == [5, 0]
+    v = torch.empty(0, dtype=torch.float64, device="cuda")
+    K = torch.empty(0, dtype=torch.float64, device="cuda")
+    for f in (feasm.fe_assemble_csr, feasm.fe_assemble_crac):
+        for mode in (feasm.FE_ATOMIC, feasm.FE_DETERMINISTIC):
+            f(ctx, p.handle, K, v, mode, 0)
+    torch.cuda.synchronize()
+    p.free()
+
+
+def test_invalid_connectivity_reports_errors(ctx):
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    bad_range = torch.tensor([[0, 1, 7]], dtype=torch.int32, device="cuda")
+    with pytest.raises(feasm.FeError) as ei:
+        feasm.fe_pattern_build(ctx, 1, 3, 5, bad_range)
+    assert ei.value.code == feasm.FE_ERR_DOF_RANGE
+    neg = torch.tensor([[0, -1, 2]], dtype=torch.int32, device="cuda")
+    with pytest.raises(feasm.FeError) as ei:
+        feasm.fe_pattern_build(ctx, 1, 3, 5, neg)
+    assert ei.value.code == feasm.FE_ERR_DOF_RANGE
+    dup = torch.tensor([[0, 2, 4], [1, 3, 1]], dtype=torch.int32, device="cuda")
+    with pytest.raises(feasm.FeError) as ei:
+        feasm.fe_pattern_build(ctx, 2, 3, 5, dup)
+    assert ei.value.code == feasm.FE_ERR_DUP_DOF
+    ok = torch.tensor([[0, 2, 4]], dtype=torch.int32, device="cuda")
+    with pytest.raises(feasm.FeError) as ei:
+        feasm.fe_pattern_build(ctx, 1, 3, 5, ok, flags=0x100)
+    assert ei.value.code == feasm.FE_ERR_INVALID_ARG
+    with pytest.raises(feasm.FeError) as ei:
+        feasm.fe_pattern_build(ctx, 1, 200, 5, ok)
+    assert ei.value.code == feasm.FE_ERR_UNSUPPORTED
+    # the context stays usable after rejected inputs
+    p = feasm.Pattern(ctx, ok, 5)
+    assert p.info["nnz"] == 9
+    # parts that were not built are reported, not used
+    p2 = feasm.Pattern(ctx, ok, 5, flags=feasm.FE_PATTERN_CSR | feasm.FE_PATTERN_MAP_CSR)
+    K = torch.ones(9, dtype=torch.float64, device="cuda")
+    v = torch.zeros(9, dtype=torch.float64, device="cuda")
+    with pytest.raises(feasm.FeError) as ei:
+        feasm.fe_assemble_crac(ctx, p2.handle, K, v)
+    assert ei.value.code == feasm.FE_ERR_NOT_BUILT
+    with pytest.raises(feasm.FeError) as ei:
+        feasm.fe_assemble_csr(ctx, p2.handle, K, v, feasm.FE_DETERMINISTIC)
+    assert ei.value.code == feasm.FE_ERR_NOT_BUILT
+    feasm.fe_assemble_csr(ctx, p2.handle, K, v, feasm.FE_ATOMIC)
+    torch.cuda.synchronize()
+    assert v.cpu().tolist() == [1.0] * 9
+    p.free()
+    p2.free()
