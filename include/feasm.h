@@ -58,8 +58,8 @@ extern "C" {
 #define FE_PATTERN_CRAC 0x2u      /* CRAC row pointers + column alignments     */
 #define FE_PATTERN_MAP_CSR 0x4u   /* per-entry slot map for fe_assemble_csr    */
 #define FE_PATTERN_MAP_CRAC 0x8u  /* per-run slot map for fe_assemble_crac     */
-#define FE_PATTERN_ADJ 0x10u      /* DOF -> (element, local row) adjacency,
-                                     needed by FE_DETERMINISTIC               */
+#define FE_PATTERN_ADJ 0x10u      /* block adjacency (always built; used by
+                                     FE_DETERMINISTIC)                        */
 #define FE_PATTERN_ALL 0x1Fu
 
 /* ---- numeric modes ------------------------------------------------------ */
@@ -83,7 +83,11 @@ typedef struct fe_pattern_info {
     int32_t max_row_len;   /* longest CSR row                              */
     int32_t max_degree;    /* most elements sharing one DOF                */
     uint32_t flags;        /* parts that were built                        */
-    uint32_t reserved;
+    int32_t block;         /* DOFs per block B found in the connectivity:
+                              every element lists whole blocks
+                              B*node .. B*node+B-1 (1 = no blocking)       */
+    int32_t uniform_runs;  /* 1 when all elements share one run layout     */
+    int32_t reserved;
     int64_t device_bytes;  /* device memory held by the pattern            */
 } fe_pattern_info;
 
@@ -153,11 +157,14 @@ int fe_pattern_csr(const fe_pattern *pattern, const int64_t **row_ptr, const int
 int fe_pattern_crac(const fe_pattern *pattern, const int64_t **row_ptr, const int32_t **col_align,
                     int64_t *n_ca);
 
-/* Borrowed device pointer to the DOF adjacency: adj_ptr int64 [n_dofs + 1],
- * adj uint32 [n_elem * dofs_per_elem] holding e*dofs_per_elem + r for every
- * element e whose local DOF r is the row, ascending.  FE_ERR_NOT_BUILT
- * without FE_PATTERN_ADJ. */
-int fe_pattern_adjacency(const fe_pattern *pattern, const int64_t **adj_ptr, const uint32_t **adj);
+/* Borrowed device pointers to the block adjacency.  *block receives B (see
+ * fe_pattern_info.block); blocks are node = dof / B.  adj_ptr int64
+ * [n_dofs/B + 1]; adj uint32 [n_elem * dofs_per_elem / B] holding
+ * e*(dofs_per_elem/B) + k for every element e whose local block k is the
+ * row's block, ascending.  With B = 1 this is the DOF -> (element, local
+ * row) adjacency.  Always built. */
+int fe_pattern_adjacency(const fe_pattern *pattern, int32_t *block, const int64_t **adj_ptr,
+                         const uint32_t **adj);
 
 /* Sizes and parts of a pattern. */
 int fe_pattern_info_get(const fe_pattern *pattern, fe_pattern_info *out);

@@ -4,25 +4,26 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cstddef>
 
 #include "../../include/feasm.h"
 
 #define FE_WARP 32
 
-// Return FE_ERR_DEVICE from the enclosing function when a CUDA call fails.
-#define FE_CUDA(call)                                      \
-    do {                                                   \
-        cudaError_t fe_e_ = (call);                        \
-        if (fe_e_ != cudaSuccess) {                        \
-            fe_set_last_cuda_error(fe_e_, #call, __LINE__); \
+// Return an FE_* code from the enclosing function when a CUDA call fails.
+#define FE_CUDA(call)                                                               \
+    do {                                                                            \
+        cudaError_t fe_e_ = (call);                                                 \
+        if (fe_e_ != cudaSuccess) {                                                 \
+            fe_set_last_cuda_error(fe_e_, #call, __LINE__);                         \
             return fe_e_ == cudaErrorMemoryAllocation ? FE_ERR_OOM : FE_ERR_DEVICE; \
-        }                                                  \
+        }                                                                           \
     } while (0)
 
-#define FE_TRY(expr)                 \
-    do {                             \
-        int fe_rc_ = (expr);         \
+#define FE_TRY(expr)                        \
+    do {                                    \
+        int fe_rc_ = (expr);                \
         if (fe_rc_ != FE_OK) return fe_rc_; \
     } while (0)
 
@@ -36,34 +37,43 @@ struct fe_ctx {
     struct fe_batch_state *batch = nullptr;  // batching / serving scheduler
 };
 
+// A pattern is built at the level of DOF blocks ("nodes"): when every
+// element lists its DOFs in groups of B consecutive indices starting at a
+// multiple of B (dof = B*node + comp), all B rows of a node share one column
+// structure, so adjacency, row unions and slot maps are computed per node and
+// expanded.  B = 1 is the general case.
 struct fe_pattern {
     fe_ctx *ctx = nullptr;
     int64_t n_e = 0;
     int32_t n_loc = 0;
-    int32_t mask_words = 0;   // 32-bit words per element in run_mask
+    int32_t B = 1;            // DOFs per block
+    int32_t nln = 0;          // blocks per element = n_loc / B
+    int32_t mask_words = 0;   // 32-bit words per element in run_mask (nln bits)
     int64_t n_dofs = 0;
+    int64_t n_nodes = 0;      // n_dofs / B
     int64_t nnz = 0;
     int64_t n_ca = 0;
-    int64_t n_runs = 0;       // sum over elements of DOF runs
-    int32_t max_row_len = 0;
-    int32_t max_deg = 0;
+    int64_t n_runs = 0;       // sum over elements of block runs
+    int32_t max_row_len = 0;  // DOF-level
+    int32_t max_node_len = 0; // blocks per block row
+    int32_t max_deg = 0;      // elements sharing one block
     int32_t map_bytes = 1;
     uint32_t flags = 0;
     int64_t device_bytes = 0;
     bool uniform_runs = false;  // every element has the same run mask
     int32_t runs_per_elem = 0;  // valid when uniform_runs
 
-    int32_t *elem_dofs = nullptr;  // [n_e * n_loc]
+    int32_t *node_dofs = nullptr;  // [n_e * nln] block ids per element
     int64_t *row_ptr = nullptr;    // [n_dofs + 1]
     int32_t *col_idx = nullptr;    // [nnz]
     int64_t *crac_ptr = nullptr;   // [n_dofs + 1], int units
     int32_t *col_align = nullptr;  // [n_ca]
-    int64_t *adj_ptr = nullptr;    // [n_dofs + 1]
-    uint32_t *adj = nullptr;       // [n_e * n_loc]
-    void *map_csr = nullptr;       // [n_e * n_loc * n_loc] uint8 / uint16
-    uint32_t *run_mask = nullptr;  // [n_e * mask_words]
+    int64_t *adj_ptr = nullptr;    // [n_nodes + 1]
+    uint32_t *adj = nullptr;       // [n_e * nln] ids e*nln + k, ascending per block row
+    void *map_csr = nullptr;       // [n_e * nln * nln] uint8/uint16: block position in block row
+    uint32_t *run_mask = nullptr;  // [n_e * mask_words] run starts over the element's blocks
     int64_t *run_ptr = nullptr;    // [n_e + 1]
-    void *map_crac = nullptr;      // [n_runs * n_loc] uint8 / uint16
+    void *map_crac = nullptr;      // [n_runs * nln] uint8/uint16: run start position in block row
 };
 
 void fe_batch_state_destroy(fe_ctx *ctx);
@@ -87,3 +97,6 @@ static inline int fe_grid_for(int64_t work, int threads, int num_sms, int per_sm
     if (blocks < 1) blocks = 1;
     return (int)blocks;
 }
+
+__device__ __forceinline__ int64_t fe_warp_id() { return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ int64_t fe_warps() { return ((int64_t)gridDim.x * blockDim.x) >> 5; }

@@ -3,280 +3,326 @@
 //   FE_ATOMIC         element-parallel, FP64 atomic add into the values array
 //                     (the atomic parallel assembly of Listing 3); one warp per
 //                     element streams K_e with coalesced loads.
-//   FE_DETERMINISTIC  row-parallel gather: one warp per row walks the row's
-//                     (element, local row) incidences in ascending element
-//                     order and adds each K_e(r, :) into per-row accumulators
-//                     in shared memory, then writes the row once.  Each value
+//   FE_DETERMINISTIC  row-parallel gather: one warp per block row (the B rows
+//                     of one node) walks the node's (element, local node)
+//                     incidences in ascending element order and adds the B
+//                     contiguous rows K_e(B*k .. B*k+B-1, :) into accumulators
+//                     in shared memory, then writes the rows once.  Each value
 //                     is summed in exactly the order of Listing 2, so the
 //                     result is bit-identical to the sequential assembly.
 //
-// CSR kernels find the slot of (e, r, c) through a per-entry map (relative to
-// the row start).  CRAC kernels use the compressed DOF runs of §2.1: one map
-// entry per (e, r, run), the row start taken from the CRAC pairs, and the
-// column's offset inside its run (Listing 5's contiguous slices).
-#include <algorithm>
-
+// The slot of entry (e, r, c) is row_start(D_e(r)) + B*pos + c%B, where pos
+// is the position of column block c/B in the row's block list.  CSR kernels
+// read pos from a per (element, row block, column block) map and the row
+// start from row_ptr.  CRAC kernels use the runs of consecutive blocks of
+// each element (the compressed DOF array of §2.1): one map entry per
+// (element, row block, run), the column's offset inside its run, and the
+// row start read from the CRAC pairs (Listing 5's contiguous slices).
 #include "internal.cuh"
 
 namespace {
 
-__device__ __forceinline__ int64_t warp_id_global() { return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
-__device__ __forceinline__ int64_t warps_total() { return ((int64_t)gridDim.x * blockDim.x) >> 5; }
-
-struct CracArgs {
-    const int64_t *crac_ptr;
+struct Geo {
+    const int32_t *N;        // block ids per element
+    const int64_t *row_ptr;  // CSR
+    const int64_t *crac_ptr; // CRAC
     const int32_t *col_align;
     const uint32_t *run_mask;
     const int64_t *run_ptr;
+    const int64_t *adj_ptr;
+    const uint32_t *adj;
     int uniform_R;  // > 0 when every element has this many runs and the same mask
     int mask_words;
 };
 
-// First value position of row i, read from the CRAC pairs (pair 0's value
-// position; for an empty row the next pair's, which is the same number).
-__device__ __forceinline__ int64_t crac_row_base(const CracArgs &ca, int64_t i)
+__device__ __forceinline__ int64_t crac_row_base(const Geo &g, int64_t i) { return g.col_align[g.crac_ptr[i] + 1]; }
+
+// Run index of block kc and kc's offset inside that run, for run-start bits m
+// (kc < 32, bit 0 always set).
+__device__ __forceinline__ void run_of(uint32_t m, int kc, int &k, int &off)
 {
-    return ca.col_align[ca.crac_ptr[i] + 1];
+    const uint32_t le = m & (0xffffffffu >> (31 - kc));
+    k = __popc(le) - 1;
+    off = kc - (31 - __clz(le));
 }
 
-// For column c of an element whose run-start bits (c < 32) are m: the index
-// of the run holding c and c's offset inside it.
-__device__ __forceinline__ void run_of(uint32_t m, int c, int &k, int &off)
+// The same for any number of 32-bit mask words.
+__device__ __forceinline__ void run_of_multi(const uint32_t *m, int kc, int &k, int &off)
 {
-    const uint32_t le = m & (0xffffffffu >> (31 - c));
-    k = __popc(le) - 1;
-    off = c - (31 - __clz(le));
+    int before = 0, last = 0;
+    const int w_end = kc >> 5;
+    for (int w = 0; w < w_end; ++w) {
+        before += __popc(m[w]);
+        if (m[w]) last = 32 * w + 31 - __clz(m[w]);
+    }
+    const uint32_t le = m[w_end] & (0xffffffffu >> (31 - (kc & 31)));
+    k = before + __popc(le) - 1;
+    const int start = le ? 32 * w_end + 31 - __clz(le) : last;
+    off = kc - start;
 }
 
 // ------------------------------------------------------------ atomic ---
-// One warp per element, NLOC <= 32 known at compile time.  All loads of the
-// element are issued before its atomics.
-template <int NLOC, typename MT, bool CRAC>
-__global__ void __launch_bounds__(256) k_atomic_small(const double *__restrict__ K, const int32_t *__restrict__ D,
-                                                      int64_t n_e, const int64_t *__restrict__ row_ptr,
-                                                      const MT *__restrict__ map, CracArgs ca,
-                                                      const MT *__restrict__ mapc, double *values)
+// One warp per element; NLN blocks of BB DOFs, NLN*BB <= 32.
+template <int NLN, int BB, typename MT, bool CRAC>
+__global__ void __launch_bounds__(256) k_atomic_elem(const double *__restrict__ K, int64_t n_e, Geo g,
+                                                     const MT *__restrict__ map, const MT *__restrict__ mapc,
+                                                     double *values)
 {
+    constexpr int NLOC = NLN * BB;
     constexpr int NN = NLOC * NLOC;
     constexpr int IT = (NN + 31) / 32;
+    constexpr int CH = 6;  // loads in flight per lane before their atomics
     const int lane = threadIdx.x & 31;
-    for (int64_t e = warp_id_global(); e < n_e; e += warps_total()) {
-        const int32_t d = lane < NLOC ? D[e * NLOC + lane] : 0;
+    int kk = 0, koff = 0;
+    if (CRAC && g.uniform_R && lane < NLN) run_of(g.run_mask[0], lane, kk, koff);
+    for (int64_t e = fe_warp_id(); e < n_e; e += fe_warps()) {
+        const int32_t nd = lane < NLN ? g.N[e * NLN + lane] : 0;
+        const int32_t rnode = __shfl_sync(0xffffffffu, nd, lane < NLOC ? lane / BB : 0);
         int64_t base = 0;
-        int kc = 0, offc = 0, nr = 0;
+        if (lane < NLOC) {
+            const int64_t row = (int64_t)BB * rnode + lane % BB;
+            base = CRAC ? crac_row_base(g, row) : g.row_ptr[row];
+        }
         int64_t rp = 0;
-        if (!CRAC) {
-            if (lane < NLOC) base = row_ptr[d];
-        } else {
-            if (lane < NLOC) base = crac_row_base(ca, d);
-            const uint32_t m = ca.uniform_R ? ca.run_mask[0] : ca.run_mask[e];
-            if (lane < NLOC) run_of(m, lane, kc, offc);
-            if (ca.uniform_R) {
-                nr = ca.uniform_R;
+        int nr = 0;
+        if (CRAC) {
+            if (g.uniform_R) {
+                nr = g.uniform_R;
                 rp = e * nr;
             } else {
-                rp = ca.run_ptr[e];
-                nr = (int)(ca.run_ptr[e + 1] - rp);
+                rp = g.run_ptr[e];
+                nr = (int)(g.run_ptr[e + 1] - rp);
+                if (lane < NLN) run_of(g.run_mask[e], lane, kk, koff);
             }
         }
         const double *Ke = K + e * NN;
-        double kv[IT];
-        int rel[IT];
 #pragma unroll
-        for (int j = 0; j < IT; ++j) {
-            const int q = lane + 32 * j;
-            kv[j] = 0.0;
-            rel[j] = 0;
-            if (q < NN) {
-                kv[j] = __ldcs(Ke + q);
-                if (!CRAC) rel[j] = (int)__ldcs(map + e * NN + q);
-            }
-        }
+        for (int j0 = 0; j0 < IT; j0 += CH) {
+            double kv[CH];
 #pragma unroll
-        for (int j = 0; j < IT; ++j) {
-            const int q = lane + 32 * j;
-            const int qq = q < NN ? q : 0;
-            const int r = qq / NLOC, c = qq % NLOC;
-            const int64_t b = __shfl_sync(0xffffffffu, base, r);
-            int64_t slot;
-            if (!CRAC) {
-                slot = b + rel[j];
-            } else {
-                const int k = __shfl_sync(0xffffffffu, kc, c);
-                const int off = __shfl_sync(0xffffffffu, offc, c);
-                slot = b + (int64_t)mapc[rp * NLOC + r * nr + k] + off;
+            for (int u = 0; u < CH; ++u) {
+                const int q = lane + 32 * (j0 + u);
+                kv[u] = (j0 + u < IT && q < NN) ? __ldcs(Ke + q) : 0.0;
             }
-            if (q < NN) atomicAdd(values + slot, kv[j]);
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                if (j0 + u < IT) {
+                    const int q = lane + 32 * (j0 + u);
+                    const int qq = q < NN ? q : 0;
+                    const int r = qq / NLOC, c = qq % NLOC;
+                    const int kc = c / BB;
+                    const int64_t b = __shfl_sync(0xffffffffu, base, r);
+                    int pos;
+                    if (!CRAC) {
+                        pos = (int)map[(e * NLN + r / BB) * NLN + kc];
+                    } else {
+                        const int k = __shfl_sync(0xffffffffu, kk, kc);
+                        const int off = __shfl_sync(0xffffffffu, koff, kc);
+                        pos = (int)mapc[rp * NLN + (r / BB) * nr + k] + off;
+                    }
+                    if (q < NN) atomicAdd(values + b + (int64_t)BB * pos + c % BB, kv[u]);
+                }
+            }
         }
     }
 }
 
-// Any n_loc <= FE_MAX_NLOC: one warp per (element, local row).
+// Any element size: one warp per element, per-row starts staged in shared
+// memory.
 template <typename MT, bool CRAC>
-__global__ void __launch_bounds__(256) k_atomic_generic(const double *__restrict__ K, const int32_t *__restrict__ D,
-                                                        int64_t n_inc, int32_t n_loc,
-                                                        const int64_t *__restrict__ row_ptr,
-                                                        const MT *__restrict__ map, CracArgs ca,
+__global__ void __launch_bounds__(256) k_atomic_generic(const double *__restrict__ K, int64_t n_e, int32_t nln,
+                                                        int32_t B, Geo g, const MT *__restrict__ map,
                                                         const MT *__restrict__ mapc, double *values)
 {
-    const int lane = threadIdx.x & 31;
-    for (int64_t t = warp_id_global(); t < n_inc; t += warps_total()) {
-        const int64_t e = (int64_t)((uint32_t)t / (uint32_t)n_loc);
-        const int r = (int)(t - e * n_loc);
-        const int32_t row = D[t];
-        int64_t base, rp = 0;
+    __shared__ int64_t base_s[8][FE_MAX_NLOC];
+    __shared__ int32_t k_s[8][FE_MAX_NLOC];
+    __shared__ int32_t off_s[8][FE_MAX_NLOC];
+    const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) & 7;
+    const int n_loc = nln * B;
+    const int64_t NN = (int64_t)n_loc * n_loc;
+    for (int64_t e = fe_warp_id(); e < n_e; e += fe_warps()) {
+        int64_t rp = 0;
         int nr = 0;
-        if (!CRAC) {
-            base = row_ptr[row];
-        } else {
-            base = crac_row_base(ca, row);
-            rp = ca.run_ptr[e];
-            nr = (int)(ca.run_ptr[e + 1] - rp);
+        if (CRAC) {
+            rp = g.run_ptr[e];
+            nr = (int)(g.run_ptr[e + 1] - rp);
         }
-        int before = 0, last_start = 0;
-        for (int c0 = 0; c0 < n_loc; c0 += 32) {
-            const int c = c0 + lane;
-            int64_t slot = 0;
-            if (!CRAC) {
-                if (c < n_loc) slot = base + map[t * n_loc + c];
-            } else {
-                const uint32_t m = ca.run_mask[e * ca.mask_words + (c0 >> 5)];
-                const uint32_t le = m & (0xffffffffu >> (31 - lane));
-                const int k = before + __popc(le) - 1;
-                const int start = le ? c0 + 31 - __clz(le) : last_start;
-                if (c < n_loc) slot = base + (int64_t)mapc[rp * n_loc + (int64_t)r * nr + k] + (c - start);
-                before += __popc(m);
-                if (m) last_start = c0 + 31 - __clz(m);
-            }
-            if (c < n_loc) atomicAdd(values + slot, __ldcs(K + t * n_loc + c));
+        for (int r = lane; r < n_loc; r += 32) {
+            const int64_t row = (int64_t)B * g.N[e * nln + r / B] + r % B;
+            base_s[w][r] = CRAC ? crac_row_base(g, row) : g.row_ptr[row];
         }
+        if (CRAC)
+            for (int kc = lane; kc < nln; kc += 32)
+                run_of_multi(g.run_mask + e * g.mask_words, kc, k_s[w][kc], off_s[w][kc]);
+        __syncwarp();
+        const double *Ke = K + e * NN;
+        for (int q = lane; q < NN; q += 32) {
+            const int r = q / n_loc, c = q - r * n_loc;
+            const int kc = c / B;
+            int pos;
+            if (!CRAC) pos = (int)map[(e * nln + r / B) * nln + kc];
+            else pos = (int)mapc[rp * nln + (int64_t)(r / B) * nr + k_s[w][kc]] + off_s[w][kc];
+            atomicAdd(values + base_s[w][r] + (int64_t)B * pos + c % B, __ldcs(Ke + q));
+        }
+        __syncwarp();
     }
 }
 
 // ------------------------------------------------------ deterministic ---
-// One warp per row; accumulators for the row's values in shared memory.
-// Incidences are taken U at a time: their K rows and slots are loaded first,
-// then added strictly in ascending order.
-template <int NLOC, typename MT, bool CRAC>
-__global__ void __launch_bounds__(256) k_gather_small(const double *__restrict__ K, int64_t n_dofs,
-                                                      const int64_t *__restrict__ adj_ptr,
-                                                      const uint32_t *__restrict__ adj,
-                                                      const int64_t *__restrict__ row_ptr,
-                                                      const MT *__restrict__ map, CracArgs ca,
-                                                      const MT *__restrict__ mapc, int cap, int accumulate,
-                                                      double *values)
+// One warp per block row; the B rows of the node are contiguous in values.
+// Incidences are taken U at a time: their K slices and slots are loaded
+// first, then added strictly in ascending element order.
+template <int NLN, int BB, typename MT, bool CRAC>
+__global__ void __launch_bounds__(256) k_gather_node(const double *__restrict__ K, int64_t n_nodes, Geo g,
+                                                     const MT *__restrict__ map, const MT *__restrict__ mapc, int cap,
+                                                     int accumulate, double *values)
 {
-    constexpr int U = 8;
+    constexpr int NLOC = NLN * BB;
+    constexpr int NN = NLOC * NLOC;
+    constexpr int CHK = BB * NLOC;  // doubles of one incidence (B contiguous K rows)
+    constexpr int IT = (CHK + 31) / 32;
+    constexpr int U = 4;
     extern __shared__ double acc_all[];
     const int lane = threadIdx.x & 31;
     double *acc = acc_all + (size_t)(threadIdx.x >> 5) * cap;
-    int kc = 0, offc = 0;
-    if (CRAC && ca.uniform_R && lane < NLOC) run_of(ca.run_mask[0], lane, kc, offc);
-    for (int64_t i = warp_id_global(); i < n_dofs; i += warps_total()) {
-        int64_t rb, len;
+    // per-entry constants: block row jr, column c
+    int jr_[IT], c_[IT];
+#pragma unroll
+    for (int j = 0; j < IT; ++j) {
+        const int q = lane + 32 * j;
+        const int qq = q < CHK ? q : 0;
+        jr_[j] = qq / NLOC;
+        c_[j] = qq % NLOC;
+    }
+    int ku[IT], offu[IT];  // run index / offset of the column block (uniform runs)
+#pragma unroll
+    for (int j = 0; j < IT; ++j) {
+        ku[j] = 0;
+        offu[j] = 0;
+        if (CRAC && g.uniform_R) run_of(g.run_mask[0], c_[j] / BB, ku[j], offu[j]);
+    }
+    for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
+        const int64_t i0 = (int64_t)BB * v;
+        int64_t rb, RL;
         if (!CRAC) {
-            rb = row_ptr[i];
-            len = row_ptr[i + 1] - rb;
+            rb = g.row_ptr[i0];
+            RL = g.row_ptr[i0 + 1] - rb;
         } else {
-            rb = crac_row_base(ca, i);
-            len = ca.col_align[ca.crac_ptr[i + 1] + 1] - rb;
+            rb = crac_row_base(g, i0);
+            RL = crac_row_base(g, i0 + 1) - rb;
         }
-        for (int k = lane; k < len; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
+        const int total = (int)(BB * RL);
+        for (int k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
         __syncwarp();
-        const int64_t a = adj_ptr[i], b = adj_ptr[i + 1];
+        const int64_t a = g.adj_ptr[v], b = g.adj_ptr[v + 1];
         for (int64_t s0 = a; s0 < b; s0 += U) {
-            double kv[U];
-            int slot[U];
+            double kv[U][IT];
+            int rel[U][IT];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                kv[u] = 0.0;
-                slot[u] = 0;
-                if (s0 + u < b && lane < NLOC) {
-                    const uint32_t t = adj[s0 + u];
-                    kv[u] = __ldcs(K + (int64_t)t * NLOC + lane);
-                    if (!CRAC) {
-                        slot[u] = (int)map[(int64_t)t * NLOC + lane];
+                const bool have = s0 + u < b;
+                const uint32_t t = have ? g.adj[s0 + u] : 0u;
+                const uint32_t e = t / NLN;
+                const int kr = (int)(t - e * NLN);
+                const double *chunk = K + (int64_t)e * NN + (int64_t)kr * CHK;
+                int64_t rp = 0;
+                int nr = 0;
+                uint32_t m = 0;
+                if (CRAC && have) {
+                    if (g.uniform_R) {
+                        nr = g.uniform_R;
+                        rp = (int64_t)e * nr;
                     } else {
-                        const uint32_t e = t / NLOC;
-                        const int r = (int)(t - e * NLOC);
-                        int k = kc, off = offc, nr;
-                        int64_t rp;
-                        if (ca.uniform_R) {
-                            nr = ca.uniform_R;
-                            rp = (int64_t)e * nr;
+                        rp = g.run_ptr[e];
+                        nr = (int)(g.run_ptr[e + 1] - rp);
+                        m = g.run_mask[e];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < IT; ++j) {
+                    const int q = lane + 32 * j;
+                    kv[u][j] = 0.0;
+                    rel[u][j] = 0;
+                    if (have && q < CHK) {
+                        kv[u][j] = __ldcs(chunk + q);
+                        const int kc = c_[j] / BB;
+                        int pos;
+                        if (!CRAC) {
+                            pos = (int)map[(int64_t)t * NLN + kc];
                         } else {
-                            run_of(ca.run_mask[e], lane, k, off);
-                            rp = ca.run_ptr[e];
-                            nr = (int)(ca.run_ptr[e + 1] - rp);
+                            int k = ku[j], off = offu[j];
+                            if (!g.uniform_R) run_of(m, kc, k, off);
+                            pos = (int)mapc[rp * NLN + (int64_t)kr * nr + k] + off;
                         }
-                        slot[u] = (int)mapc[rp * NLOC + r * nr + k] + off;
+                        rel[u][j] = jr_[j] * (int)RL + BB * pos + c_[j] % BB;
                     }
                 }
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                if (s0 + u < b && lane < NLOC) acc[slot[u]] += kv[u];
+#pragma unroll
+                for (int j = 0; j < IT; ++j)
+                    if (s0 + u < b && lane + 32 * j < CHK) acc[rel[u][j]] += kv[u][j];
                 __syncwarp();
             }
         }
-        for (int k = lane; k < len; k += 32) values[rb + k] = acc[k];
+        for (int k = lane; k < total; k += 32) values[rb + k] = acc[k];
         __syncwarp();
     }
 }
 
 template <typename MT, bool CRAC>
-__global__ void __launch_bounds__(256) k_gather_generic(const double *__restrict__ K, int64_t n_dofs, int32_t n_loc,
-                                                        const int64_t *__restrict__ adj_ptr,
-                                                        const uint32_t *__restrict__ adj,
-                                                        const int64_t *__restrict__ row_ptr,
-                                                        const MT *__restrict__ map, CracArgs ca,
+__global__ void __launch_bounds__(256) k_gather_generic(const double *__restrict__ K, int64_t n_nodes, int32_t nln,
+                                                        int32_t B, Geo g, const MT *__restrict__ map,
                                                         const MT *__restrict__ mapc, int cap, int accumulate,
                                                         double *values)
 {
     extern __shared__ double acc_all[];
     const int lane = threadIdx.x & 31;
     double *acc = acc_all + (size_t)(threadIdx.x >> 5) * cap;
-    for (int64_t i = warp_id_global(); i < n_dofs; i += warps_total()) {
-        int64_t rb, len;
+    const int n_loc = nln * B;
+    const int64_t NN = (int64_t)n_loc * n_loc;
+    const int chk = B * n_loc;
+    for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
+        const int64_t i0 = (int64_t)B * v;
+        int64_t rb, RL;
         if (!CRAC) {
-            rb = row_ptr[i];
-            len = row_ptr[i + 1] - rb;
+            rb = g.row_ptr[i0];
+            RL = g.row_ptr[i0 + 1] - rb;
         } else {
-            rb = crac_row_base(ca, i);
-            len = ca.col_align[ca.crac_ptr[i + 1] + 1] - rb;
+            rb = crac_row_base(g, i0);
+            RL = crac_row_base(g, i0 + 1) - rb;
         }
-        for (int k = lane; k < len; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
+        const int64_t total = B * RL;
+        for (int64_t k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
         __syncwarp();
-        for (int64_t s = adj_ptr[i]; s < adj_ptr[i + 1]; ++s) {
-            const uint32_t t = adj[s];
-            const int64_t e = (int64_t)(t / (uint32_t)n_loc);
-            const int r = (int)(t - (uint32_t)e * (uint32_t)n_loc);
+        for (int64_t s = g.adj_ptr[v]; s < g.adj_ptr[v + 1]; ++s) {
+            const uint32_t t = g.adj[s];
+            const int64_t e = t / (uint32_t)nln;
+            const int kr = (int)(t - (uint32_t)e * (uint32_t)nln);
+            const double *chunk = K + e * NN + (int64_t)kr * chk;
             int64_t rp = 0;
             int nr = 0;
             if (CRAC) {
-                rp = ca.run_ptr[e];
-                nr = (int)(ca.run_ptr[e + 1] - rp);
+                rp = g.run_ptr[e];
+                nr = (int)(g.run_ptr[e + 1] - rp);
             }
-            int before = 0, last_start = 0;
-            for (int c0 = 0; c0 < n_loc; c0 += 32) {
-                const int c = c0 + lane;
-                int sl = 0;
+            for (int q = lane; q < chk; q += 32) {
+                const int jr = q / n_loc, c = q - jr * n_loc;
+                const int kc = c / B;
+                int pos;
                 if (!CRAC) {
-                    if (c < n_loc) sl = (int)map[(int64_t)t * n_loc + c];
+                    pos = (int)map[(int64_t)t * nln + kc];
                 } else {
-                    const uint32_t m = ca.run_mask[e * ca.mask_words + (c0 >> 5)];
-                    const uint32_t le = m & (0xffffffffu >> (31 - lane));
-                    const int k = before + __popc(le) - 1;
-                    const int start = le ? c0 + 31 - __clz(le) : last_start;
-                    if (c < n_loc) sl = (int)mapc[rp * n_loc + (int64_t)r * nr + k] + (c - start);
-                    before += __popc(m);
-                    if (m) last_start = c0 + 31 - __clz(m);
+                    int k, off;
+                    run_of_multi(g.run_mask + e * g.mask_words, kc, k, off);
+                    pos = (int)mapc[rp * nln + (int64_t)kr * nr + k] + off;
                 }
-                if (c < n_loc) acc[sl] += K[(int64_t)t * n_loc + c];
+                acc[jr * RL + (int64_t)B * pos + c % B] += chunk[q];
             }
             __syncwarp();
         }
-        for (int k = lane; k < len; k += 32) values[rb + k] = acc[k];
+        for (int64_t k = lane; k < total; k += 32) values[rb + k] = acc[k];
         __syncwarp();
     }
 }
@@ -288,75 +334,75 @@ int configure_smem(KernelT kernel, size_t bytes)
     return FE_OK;
 }
 
-template <int NLOC, typename MT, bool CRAC>
+Geo geo_of(const fe_pattern *p)
+{
+    return Geo{p->node_dofs, p->row_ptr,  p->crac_ptr, p->col_align, p->run_mask,
+               p->run_ptr,   p->adj_ptr, p->adj,      p->uniform_runs ? p->runs_per_elem : 0, p->mask_words};
+}
+
+template <int NLN, int BB, typename MT, bool CRAC>
 int launch_atomic(const fe_pattern *p, const double *K, double *values, cudaStream_t s)
 {
-    const CracArgs ca{p->crac_ptr, p->col_align, p->run_mask, p->run_ptr, p->uniform_runs ? p->runs_per_elem : 0,
-                      p->mask_words};
+    const Geo g = geo_of(p);
     const int sms = p->ctx->num_sms;
-    if constexpr (NLOC > 0) {
-        k_atomic_small<NLOC, MT, CRAC><<<fe_grid_for(p->n_e * 32, 256, sms, 8), 256, 0, s>>>(
-            K, p->elem_dofs, p->n_e, p->row_ptr, (const MT *)p->map_csr, ca, (const MT *)p->map_crac, values); fe_note_launch();
+    if constexpr (NLN > 0) {
+        k_atomic_elem<NLN, BB, MT, CRAC><<<fe_grid_for(p->n_e * 32, 256, sms, 8), 256, 0, s>>>(
+            K, p->n_e, g, (const MT *)p->map_csr, (const MT *)p->map_crac, values);
     } else {
-        const int64_t n_inc = p->n_e * p->n_loc;
-        k_atomic_generic<MT, CRAC><<<fe_grid_for(n_inc * 32, 256, sms, 8), 256, 0, s>>>(
-            K, p->elem_dofs, n_inc, p->n_loc, p->row_ptr, (const MT *)p->map_csr, ca, (const MT *)p->map_crac,
-            values); fe_note_launch();
+        k_atomic_generic<MT, CRAC><<<fe_grid_for(p->n_e * 32, 256, sms, 8), 256, 0, s>>>(
+            K, p->n_e, p->nln, p->B, g, (const MT *)p->map_csr, (const MT *)p->map_crac, values);
     }
+    fe_note_launch();
     FE_CUDA(cudaGetLastError());
     return FE_OK;
 }
 
-template <int NLOC, typename MT, bool CRAC>
+template <int NLN, int BB, typename MT, bool CRAC>
 int launch_gather(const fe_pattern *p, const double *K, double *values, int accumulate, cudaStream_t s)
 {
-    const CracArgs ca{p->crac_ptr, p->col_align, p->run_mask, p->run_ptr, p->uniform_runs ? p->runs_per_elem : 0,
-                      p->mask_words};
+    const Geo g = geo_of(p);
     const int sms = p->ctx->num_sms;
-    const int cap = std::max(1, p->max_row_len);
+    const int cap = std::max(1, p->B * p->max_row_len);
     int W = 8;
     while (W > 1 && (size_t)W * cap * 8 > 64 * 1024) W >>= 1;
     const size_t smem = (size_t)W * cap * 8;
     if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
-    const int grid = fe_grid_for(p->n_dofs * 32, W * 32, sms, std::max(1, 64 / W));
-    if constexpr (NLOC > 0) {
-        FE_TRY(configure_smem(k_gather_small<NLOC, MT, CRAC>, smem));
-        k_gather_small<NLOC, MT, CRAC><<<grid, W * 32, smem, s>>>(K, p->n_dofs, p->adj_ptr, p->adj, p->row_ptr,
-                                                                  (const MT *)p->map_csr, ca,
-                                                                  (const MT *)p->map_crac, cap, accumulate, values); fe_note_launch();
+    const int grid = fe_grid_for(p->n_nodes * 32, W * 32, sms, std::max(1, 64 / W));
+    if constexpr (NLN > 0) {
+        FE_TRY(configure_smem(k_gather_node<NLN, BB, MT, CRAC>, smem));
+        k_gather_node<NLN, BB, MT, CRAC><<<grid, W * 32, smem, s>>>(
+            K, p->n_nodes, g, (const MT *)p->map_csr, (const MT *)p->map_crac, cap, accumulate, values);
     } else {
         FE_TRY(configure_smem(k_gather_generic<MT, CRAC>, smem));
-        k_gather_generic<MT, CRAC><<<grid, W * 32, smem, s>>>(K, p->n_dofs, p->n_loc, p->adj_ptr, p->adj,
-                                                              p->row_ptr, (const MT *)p->map_csr, ca,
-                                                              (const MT *)p->map_crac, cap, accumulate, values); fe_note_launch();
+        k_gather_generic<MT, CRAC><<<grid, W * 32, smem, s>>>(K, p->n_nodes, p->nln, p->B, g,
+                                                              (const MT *)p->map_csr, (const MT *)p->map_crac,
+                                                              cap, accumulate, values);
     }
+    fe_note_launch();
     FE_CUDA(cudaGetLastError());
     return FE_OK;
 }
 
+// Element shapes with a specialised kernel: (blocks per element, DOFs per block).
 template <typename MT, bool CRAC>
 int dispatch(const fe_pattern *p, const double *K, double *values, int mode, int accumulate, cudaStream_t s)
 {
+    const int nln = p->nln, B = p->B;
     if (mode == FE_ATOMIC) {
         if (!accumulate) FE_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * (size_t)p->nnz, s));
         if (p->n_e == 0) return FE_OK;
-        // the specialised element kernels read one 32-bit run mask per element
-        switch (p->n_loc) {
-        case 4: return launch_atomic<4, MT, CRAC>(p, K, values, s);
-        case 8: return launch_atomic<8, MT, CRAC>(p, K, values, s);
-        case 24: return launch_atomic<24, MT, CRAC>(p, K, values, s);
-        case 30: return launch_atomic<30, MT, CRAC>(p, K, values, s);
-        default: return launch_atomic<0, MT, CRAC>(p, K, values, s);
-        }
+        if (nln == 4 && B == 1) return launch_atomic<4, 1, MT, CRAC>(p, K, values, s);
+        if (nln == 8 && B == 1) return launch_atomic<8, 1, MT, CRAC>(p, K, values, s);
+        if (nln == 8 && B == 3) return launch_atomic<8, 3, MT, CRAC>(p, K, values, s);
+        if (nln == 10 && B == 3) return launch_atomic<10, 3, MT, CRAC>(p, K, values, s);
+        return launch_atomic<0, 0, MT, CRAC>(p, K, values, s);
     }
-    if (p->n_dofs == 0) return FE_OK;
-    switch (p->n_loc) {
-    case 4: return launch_gather<4, MT, CRAC>(p, K, values, accumulate, s);
-    case 8: return launch_gather<8, MT, CRAC>(p, K, values, accumulate, s);
-    case 24: return launch_gather<24, MT, CRAC>(p, K, values, accumulate, s);
-    case 30: return launch_gather<30, MT, CRAC>(p, K, values, accumulate, s);
-    default: return launch_gather<0, MT, CRAC>(p, K, values, accumulate, s);
-    }
+    if (p->n_nodes == 0) return FE_OK;
+    if (nln == 4 && B == 1) return launch_gather<4, 1, MT, CRAC>(p, K, values, accumulate, s);
+    if (nln == 8 && B == 1) return launch_gather<8, 1, MT, CRAC>(p, K, values, accumulate, s);
+    if (nln == 8 && B == 3) return launch_gather<8, 3, MT, CRAC>(p, K, values, accumulate, s);
+    if (nln == 10 && B == 3) return launch_gather<10, 3, MT, CRAC>(p, K, values, accumulate, s);
+    return launch_gather<0, 0, MT, CRAC>(p, K, values, accumulate, s);
 }
 
 int assemble(fe_ctx *ctx, const fe_pattern *p, const double *K, double *values, int mode, int accumulate,

@@ -1,23 +1,31 @@
 // Symbolic phase: the sparsity pattern (CSR and CRAC) and the slot maps that
 // the numeric kernels use.  The paper builds the pattern once in
 // preprocessing and gives no algorithm for it (§3); the steps here are:
-//   A1 validate the element_dofs_array and record each element's maximal
-//      runs of consecutive DOFs (the compressed form of §2.1);
-//   A2 DOF -> (element, local row) adjacency by counting sort;
-//   A3 per-row union of the element DOF lists, sorted and de-duplicated by a
-//      warp in shared memory, scanned into row_ptr, then col_idx and the CRAC
-//      pairs (§2.2, Fig. 1c/1d) written in one pass;
-//   A5 slot maps: per entry (CSR, found by binary search) and per DOF run
-//      (CRAC, found by the linear block search of Listing 1).
+//   A1 validate the element_dofs_array (range, repeats) and find the largest
+//      DOF block size B such that every element lists whole blocks
+//      (dof = B*node + comp, the layout of the d-benchmark, §4);
+//   A2 block ("node") connectivity, the maximal runs of consecutive blocks of
+//      every element (the compressed form of §2.1), and the node -> (element,
+//      local node) adjacency by counting sort;
+//   A3 per node row: the union of the element node lists, sorted and
+//      de-duplicated by one warp (register bitonic network for up to 256
+//      candidates, shared memory beyond), scanned into row_ptr, then expanded
+//      to the B rows and B columns per node of col_idx and of the CRAC pairs
+//      (§2.2, Fig. 1c/1d);
+//   A5 slot maps: per (element, local node, local node) the position of the
+//      column node in the row node's row (binary search), and per (element,
+//      local node, run) the position of the run's first node, found by the
+//      linear block search of Listing 1 over the row's CRAC pairs.
 #include <climits>
 
 #include "internal.cuh"
 
 namespace {
 
-enum { S_ERR = 0, S_MAX_DEG = 1, S_MAX_ROW = 2, S_NONUNIFORM = 3, S_COUNT = 4 };
+enum { S_ERR = 0, S_MAX_DEG = 1, S_MAX_NODE = 2, S_NONUNIFORM = 3, S_BLOCKS = 4, S_COUNT = 6 };
 
 constexpr int32_t PAD = INT32_MAX;
+constexpr int REG_SORT_MAX = 256;  // candidates sorted in registers (8 per lane)
 
 __device__ __forceinline__ void set_err(int64_t *sc, int code)
 {
@@ -31,60 +39,77 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
-__device__ __forceinline__ int64_t warp_id_global() { return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
-__device__ __forceinline__ int64_t warps_total() { return ((int64_t)gridDim.x * blockDim.x) >> 5; }
-
 // ---------------------------------------------------------------- A1 ---
-// One warp per element: range and duplicate checks, run-start bits (bit c
-// set when D(c) does not continue D(c-1)), runs per element, and whether all
-// elements share element 0's run pattern.
-__global__ void k_elements(const int32_t *__restrict__ D, int64_t n_e, int32_t n_loc, int64_t n_dofs,
-                           int mask_words, uint32_t *__restrict__ run_mask, int32_t *__restrict__ runs,
-                           int64_t *sc)
+// One warp per element: DOF range, repeated DOFs, and the set of block sizes
+// b (bit b-1) for which the element lists whole aligned blocks.
+__global__ void k_validate(const int32_t *__restrict__ D, int64_t n_e, int32_t n_loc, int64_t n_dofs, int64_t *sc)
 {
     const int lane = threadIdx.x & 31;
-    for (int64_t e = warp_id_global(); e < n_e; e += warps_total()) {
+    uint32_t blocks_all = 0xffffffffu;
+    bool bad_range = false, dup = false;
+    for (int64_t e = fe_warp_id(); e < n_e; e += fe_warps()) {
         const int32_t *De = D + e * n_loc;
-        int nr = 0;
-        bool bad_range = false, dup = false, differs = false;
+        uint32_t ok = 0xffffffffu;
         for (int c0 = 0; c0 < n_loc; c0 += 32) {
             const int c = c0 + lane;
-            const bool valid = c < n_loc;
-            int32_t d = valid ? De[c] : 0;
-            int32_t prev = (valid && c > 0) ? De[c - 1] : 0;
-            if (valid && (d < 0 || (int64_t)d >= n_dofs)) bad_range = true;
-            if (valid)
-                for (int k = 0; k < c; ++k)
-                    if (De[k] == d) {
-                        dup = true;
-                        break;
-                    }
-            const bool start = valid && (c == 0 || (int64_t)d != (int64_t)prev + 1);
+            if (c >= n_loc) continue;
+            const int32_t d = De[c];
+            const int32_t prev = c > 0 ? De[c - 1] : 0;
+            if (d < 0 || (int64_t)d >= n_dofs) bad_range = true;
+            for (int k = 0; k < c; ++k)
+                if (De[k] == d) {
+                    dup = true;
+                    break;
+                }
+            for (int b = 2; b <= 32; ++b) {
+                const bool fits = (n_loc % b) == 0;
+                const bool good = (c % b == 0) ? (d % b == 0) : ((int64_t)d == (int64_t)prev + 1);
+                if (!fits || !good) ok &= ~(1u << (b - 1));
+            }
+        }
+        blocks_all &= ok;
+    }
+    blocks_all = __reduce_and_sync(0xffffffffu, blocks_all);
+    if (lane == 0 && blocks_all != 0xffffffffu) atomicAnd((unsigned long long *)&sc[S_BLOCKS], (unsigned long long)blocks_all);
+    if (bad_range) set_err(sc, FE_ERR_DOF_RANGE);
+    if (dup) set_err(sc, FE_ERR_DUP_DOF);
+}
+
+// ---------------------------------------------------------------- A2 ---
+// One warp per element: block ids, run-start bits over the element's blocks
+// (bit k set when block k does not continue block k-1), runs per element,
+// whether all elements share element 0's bits, and block degrees.
+__global__ void k_node_conn(const int32_t *__restrict__ D, int64_t n_e, int32_t n_loc, int32_t B, int32_t nln,
+                            int mask_words, int32_t *__restrict__ N, uint32_t *__restrict__ run_mask,
+                            int32_t *__restrict__ runs, int32_t *deg, int64_t *sc)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t e = fe_warp_id(); e < n_e; e += fe_warps()) {
+        int nr = 0;
+        bool differs = false;
+        for (int k0 = 0; k0 < nln; k0 += 32) {
+            const int k = k0 + lane;
+            const bool valid = k < nln;
+            const int32_t nd = valid ? D[e * n_loc + (int64_t)B * k] / B : 0;
+            const int32_t pv = (valid && k > 0) ? D[e * n_loc + (int64_t)B * (k - 1)] / B : 0;
+            const bool start = valid && (k == 0 || nd != pv + 1);
+            const int32_t nd0 = valid ? D[(int64_t)B * k] / B : 0;
+            const int32_t pv0 = (valid && k > 0) ? D[(int64_t)B * (k - 1)] / B : 0;
+            const bool start0 = valid && (k == 0 || nd0 != pv0 + 1);
             const unsigned m = __ballot_sync(0xffffffffu, start);
-            // element 0's bits for the same lanes
-            int32_t d0 = valid ? D[c] : 0;
-            int32_t p0 = (valid && c > 0) ? D[c - 1] : 0;
-            const bool start0 = valid && (c == 0 || (int64_t)d0 != (int64_t)p0 + 1);
             const unsigned m0 = __ballot_sync(0xffffffffu, start0);
             if (m != m0) differs = true;
-            if (lane == 0) run_mask[e * mask_words + (c0 >> 5)] = m;
+            if (valid) {
+                N[e * nln + k] = nd;
+                atomicAdd(&deg[nd], 1);
+            }
+            if (lane == 0) run_mask[e * mask_words + (k0 >> 5)] = m;
             nr += __popc(m);
         }
-        if (bad_range) set_err(sc, FE_ERR_DOF_RANGE);
-        if (dup) set_err(sc, FE_ERR_DUP_DOF);
         if (lane == 0) {
             runs[e] = nr;
             if (differs) sc[S_NONUNIFORM] = 1;
         }
-    }
-}
-
-// ---------------------------------------------------------------- A2 ---
-__global__ void k_count_deg(const int32_t *__restrict__ D, int64_t n_inc, int64_t n_dofs, int32_t *deg)
-{
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_inc; t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t d = D[t];
-        if (d >= 0 && (int64_t)d < n_dofs) atomicAdd(&deg[d], 1);
     }
 }
 
@@ -97,18 +122,19 @@ __global__ void k_max_i32(const int32_t *__restrict__ x, int64_t n, int64_t *out
     if ((threadIdx.x & 31) == 0) atomicMax((long long *)out, (long long)m);
 }
 
-__global__ void k_fill_adj(const int32_t *__restrict__ D, int64_t n_inc, const int64_t *__restrict__ adj_ptr,
-                           int32_t *cursor, uint32_t *__restrict__ adj)
+__global__ void k_fill_adj(const int32_t *__restrict__ N, int64_t n_inc, int64_t n_nodes,
+                           const int64_t *__restrict__ adj_ptr, int32_t *cursor, uint32_t *__restrict__ adj)
 {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_inc; t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t d = D[t];
-        const int64_t pos = adj_ptr[d] + atomicAdd(&cursor[d], 1);
+        const int32_t nd = N[t];
+        if (nd < 0 || (int64_t)nd >= n_nodes) continue;
+        const int64_t pos = adj_ptr[nd] + atomicAdd(&cursor[nd], 1);
         adj[pos] = (uint32_t)t;
     }
 }
 
-// Each DOF's incidence list, ascending (element-major, since the id is
-// e*n_loc + r).  Lists are short (the elements around one node).
+// Each block's incidence list, ascending (element-major, since the id is
+// e*nln + k).  Lists are short (the elements around one node).
 __global__ void k_sort_adj(const int64_t *__restrict__ adj_ptr, int64_t n, uint32_t *adj)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -126,7 +152,42 @@ __global__ void k_sort_adj(const int64_t *__restrict__ adj_ptr, int64_t n, uint3
 }
 
 // ---------------------------------------------------------------- A3 ---
-__device__ void warp_bitonic_sort(int32_t *buf, int n, int lane)
+// Bitonic sort of 32*V keys held V per lane (key g = lane*V + v), ascending.
+template <int V>
+__device__ __forceinline__ void warp_sort_regs(int32_t (&a)[V], int lane)
+{
+#pragma unroll
+    for (int size = 2; size <= 32 * V; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= V) {
+                const int lm = stride / V;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int g = lane * V + v;
+                    const int32_t y = __shfl_xor_sync(0xffffffffu, a[v], lm);
+                    const bool lower = (g & stride) == 0;
+                    const bool asc = (g & size) == 0;
+                    a[v] = (lower == asc) ? min(a[v], y) : max(a[v], y);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if ((v & stride) == 0) {
+                        const int w = v | stride;
+                        const int g = lane * V + v;
+                        const bool asc = (g & size) == 0;
+                        const int32_t x = a[v], y = a[w];
+                        a[v] = asc ? min(x, y) : max(x, y);
+                        a[w] = asc ? max(x, y) : min(x, y);
+                    }
+                }
+            }
+        }
+    }
+}
+
+__device__ void warp_sort_smem(int32_t *buf, int n, int lane)
 {
     for (int size = 2; size <= n; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -145,68 +206,164 @@ __device__ void warp_bitonic_sort(int32_t *buf, int n, int lane)
     }
 }
 
-// One warp per row i: gather D_e(c) for every (e, r) in adj(i), sort,
-// de-duplicate.  PASS 1 counts the row length and its maximal column runs;
-// PASS 2 writes col_idx and the CRAC pairs (first column, value position).
+struct RowOut {
+    // pass 1
+    int32_t *node_len;
+    int32_t *row_len;   // DOF level
+    int32_t *row_runs2; // DOF level, 2 * runs
+    // pass 2
+    const int64_t *node_row_ptr;
+    const int64_t *row_ptr;
+    const int64_t *crac_ptr;
+    int32_t *node_col;
+    int32_t *col_idx;
+    int32_t *col_align;
+};
+
+// Emit one kept key (node column m at rank rho; run rank rr if it starts a run).
+__device__ __forceinline__ void emit_pass2(const RowOut &o, int64_t v, int B, int32_t m, int rho, bool rs, int rr,
+                                           int64_t nbase)
+{
+    o.node_col[nbase + rho] = m;
+    for (int j = 0; j < B; ++j) {
+        const int64_t i = (int64_t)B * v + j;
+        const int64_t rb = o.row_ptr[i];
+        for (int jj = 0; jj < B; ++jj) o.col_idx[rb + (int64_t)B * rho + jj] = B * m + jj;
+        if (rs && o.col_align) {
+            const int64_t cb = o.crac_ptr[i];
+            o.col_align[cb + 2 * rr] = B * m;
+            o.col_align[cb + 2 * rr + 1] = (int32_t)(rb + (int64_t)B * rho);
+        }
+    }
+}
+
+template <int PASS, int V>
+__device__ __forceinline__ void row_from_regs(const int32_t *__restrict__ N, int nln, const uint32_t *__restrict__ adj,
+                                              int64_t a, int n, int64_t v, int B, const RowOut &o, int64_t *sc,
+                                              int lane)
+{
+    int32_t x[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+        const int g = lane * V + q;
+        x[q] = PAD;
+        if (g < n) {
+            const int s = g / nln;
+            const int c = g - s * nln;
+            const uint32_t t = adj[a + s];
+            x[q] = N[(int64_t)(t / (uint32_t)nln) * nln + c];
+        }
+    }
+    warp_sort_regs<V>(x, lane);
+    const int32_t up = __shfl_up_sync(0xffffffffu, x[V - 1], 1);
+    bool keep[V], rs[V];
+    int nk = 0, nrs = 0;
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+        const int g = lane * V + q;
+        const int32_t pv = q > 0 ? x[q - 1] : up;
+        keep[q] = g < n && (g == 0 || x[q] != pv);
+        rs[q] = keep[q] && (g == 0 || (int64_t)pv != (int64_t)x[q] - 1);
+        nk += keep[q];
+        nrs += rs[q];
+    }
+    int ik = nk, ir = nrs;  // inclusive warp scans
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int tk = __shfl_up_sync(0xffffffffu, ik, off);
+        const int tr = __shfl_up_sync(0xffffffffu, ir, off);
+        if (lane >= off) {
+            ik += tk;
+            ir += tr;
+        }
+    }
+    const int L = __shfl_sync(0xffffffffu, ik, 31);
+    const int R = __shfl_sync(0xffffffffu, ir, 31);
+    if (PASS == 1) {
+        if (lane == 0) {
+            o.node_len[v] = L;
+            atomicMax((long long *)&sc[S_MAX_NODE], (long long)L);
+        }
+        for (int j = lane; j < B; j += 32) {
+            o.row_len[(int64_t)B * v + j] = B * L;
+            o.row_runs2[(int64_t)B * v + j] = 2 * R;
+        }
+    } else {
+        int rho = ik - nk, rr = ir - nrs;
+        const int64_t nbase = o.node_row_ptr[v];
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            if (keep[q]) {
+                emit_pass2(o, v, B, x[q], rho, rs[q], rr, nbase);
+                ++rho;
+                rr += rs[q];
+            }
+        }
+    }
+}
+
+// One warp per node row v.
 template <int PASS>
-__global__ void k_rows(const int32_t *__restrict__ D, int32_t n_loc, int64_t n_dofs,
-                       const int64_t *__restrict__ adj_ptr, const uint32_t *__restrict__ adj, int P,
-                       int32_t *__restrict__ row_len, int32_t *__restrict__ row_runs2, int64_t *sc,
-                       const int64_t *__restrict__ row_ptr, const int64_t *__restrict__ crac_ptr,
-                       int32_t *__restrict__ col_idx, int32_t *__restrict__ col_align)
+__global__ void k_node_rows(const int32_t *__restrict__ N, int32_t nln, int64_t n_nodes, int32_t B,
+                            const int64_t *__restrict__ adj_ptr, const uint32_t *__restrict__ adj, int P, RowOut o,
+                            int64_t *sc)
 {
     extern __shared__ int32_t sbuf[];
     const int lane = threadIdx.x & 31;
     int32_t *buf = sbuf + (size_t)(threadIdx.x >> 5) * P;
-    for (int64_t i = warp_id_global(); i < n_dofs; i += warps_total()) {
-        const int64_t a = adj_ptr[i];
-        const int n = (int)(adj_ptr[i + 1] - a) * n_loc;
-        int Pn = 32;
-        while (Pn < n) Pn <<= 1;
-        for (int k = lane; k < Pn; k += 32) {
-            int32_t v = PAD;
-            if (k < n) {
-                const int s = k / n_loc;
-                const int c = k - s * n_loc;
-                const uint32_t t = adj[a + s];
-                v = D[(int64_t)(t / (uint32_t)n_loc) * n_loc + c];
+    for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
+        const int64_t a = adj_ptr[v];
+        const int n = (int)(adj_ptr[v + 1] - a) * nln;
+        if (n <= 32) {
+            row_from_regs<PASS, 1>(N, nln, adj, a, n, v, B, o, sc, lane);
+        } else if (n <= 64) {
+            row_from_regs<PASS, 2>(N, nln, adj, a, n, v, B, o, sc, lane);
+        } else if (n <= 128) {
+            row_from_regs<PASS, 4>(N, nln, adj, a, n, v, B, o, sc, lane);
+        } else if (n <= REG_SORT_MAX) {
+            row_from_regs<PASS, 8>(N, nln, adj, a, n, v, B, o, sc, lane);
+        } else {
+            int Pn = 32;
+            while (Pn < n) Pn <<= 1;
+            for (int k = lane; k < Pn; k += 32) {
+                int32_t x = PAD;
+                if (k < n) {
+                    const int s = k / nln;
+                    const int c = k - s * nln;
+                    const uint32_t t = adj[a + s];
+                    x = N[(int64_t)(t / (uint32_t)nln) * nln + c];
+                }
+                buf[k] = x;
             }
-            buf[k] = v;
-        }
-        __syncwarp();
-        warp_bitonic_sort(buf, Pn, lane);
-        int count = 0, runs = 0;
-        int64_t base = 0, cbase = 0;
-        if (PASS == 2) {
-            base = row_ptr[i];
-            if (col_align) cbase = crac_ptr[i];
-        }
-        for (int k0 = 0; k0 < n; k0 += 32) {
-            const int k = k0 + lane;
-            const int32_t v = k < n ? buf[k] : PAD;
-            const int32_t pv = (k > 0 && k < n) ? buf[k - 1] : PAD;
-            const bool keep = k < n && (k == 0 || v != pv);
-            const bool rs = keep && (k == 0 || (int64_t)pv != (int64_t)v - 1);
-            const unsigned mk = __ballot_sync(0xffffffffu, keep);
-            const unsigned mr = __ballot_sync(0xffffffffu, rs);
-            if (PASS == 2) {
-                const int rank = count + __popc(mk & lanemask_lt());
-                if (keep) col_idx[base + rank] = v;
-                if (rs && col_align) {
-                    const int rr = runs + __popc(mr & lanemask_lt());
-                    col_align[cbase + 2 * rr] = v;
-                    col_align[cbase + 2 * rr + 1] = (int32_t)(base + rank);
+            __syncwarp();
+            warp_sort_smem(buf, Pn, lane);
+            int L = 0, R = 0;
+            const int64_t nbase = PASS == 2 ? o.node_row_ptr[v] : 0;
+            for (int k0 = 0; k0 < n; k0 += 32) {
+                const int k = k0 + lane;
+                const int32_t x = k < n ? buf[k] : PAD;
+                const int32_t pv = (k > 0 && k < n) ? buf[k - 1] : PAD;
+                const bool keep = k < n && (k == 0 || x != pv);
+                const bool rs = keep && (k == 0 || (int64_t)pv != (int64_t)x - 1);
+                const unsigned mk = __ballot_sync(0xffffffffu, keep);
+                const unsigned mr = __ballot_sync(0xffffffffu, rs);
+                if (PASS == 2 && keep)
+                    emit_pass2(o, v, B, x, L + __popc(mk & lanemask_lt()), rs, R + __popc(mr & lanemask_lt()), nbase);
+                L += __popc(mk);
+                R += __popc(mr);
+            }
+            if (PASS == 1) {
+                if (lane == 0) {
+                    o.node_len[v] = L;
+                    atomicMax((long long *)&sc[S_MAX_NODE], (long long)L);
+                }
+                for (int j = lane; j < B; j += 32) {
+                    o.row_len[(int64_t)B * v + j] = B * L;
+                    o.row_runs2[(int64_t)B * v + j] = 2 * R;
                 }
             }
-            count += __popc(mk);
-            runs += __popc(mr);
+            __syncwarp();
         }
-        if (PASS == 1 && lane == 0) {
-            row_len[i] = count;
-            row_runs2[i] = 2 * runs;
-            atomicMax((long long *)&sc[S_MAX_ROW], (long long)count);
-        }
-        __syncwarp();
     }
 }
 
@@ -217,54 +374,55 @@ __global__ void k_final_pair(int32_t *col_align, int64_t n_ca, int64_t n_dofs, i
 }
 
 // ---------------------------------------------------------------- A5 ---
-// CSR slot map: for every incidence t = e*n_loc + r in row i = D_e(r) and
-// every local column c, the position of D_e(c) in the row, relative to
-// row_ptr[i].  Warp-cooperative: the row's columns are staged in shared
-// memory and each lane binary-searches its own column.
+// Node slot map: for every node incidence t = e*nln + k of node row v and
+// every local node kc of element e, the position of N_e(kc) in row v.
+// Warp-cooperative: the row's nodes are staged in shared memory and each
+// lane binary-searches its own node.
 template <typename MT>
-__global__ void k_map_csr(const int32_t *__restrict__ D, int32_t n_loc, int64_t n_dofs,
-                          const int64_t *__restrict__ adj_ptr, const uint32_t *__restrict__ adj,
-                          const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx, int cap,
-                          MT *__restrict__ map, int64_t *sc)
+__global__ void k_map_node(const int32_t *__restrict__ N, int32_t nln, int64_t n_nodes,
+                           const int64_t *__restrict__ adj_ptr, const uint32_t *__restrict__ adj,
+                           const int64_t *__restrict__ node_row_ptr, const int32_t *__restrict__ node_col, int cap,
+                           MT *__restrict__ map, int64_t *sc)
 {
     extern __shared__ int32_t sbuf[];
     const int lane = threadIdx.x & 31;
     int32_t *cols_s = sbuf + (size_t)(threadIdx.x >> 5) * cap;
-    for (int64_t i = warp_id_global(); i < n_dofs; i += warps_total()) {
-        const int64_t rb = row_ptr[i];
-        const int len = (int)(row_ptr[i + 1] - rb);
+    for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
+        const int64_t rb = node_row_ptr[v];
+        const int len = (int)(node_row_ptr[v + 1] - rb);
         const bool in_smem = len <= cap;
-        const int32_t *cols = in_smem ? cols_s : col_idx + rb;
+        const int32_t *cols = in_smem ? cols_s : node_col + rb;
         if (in_smem) {
-            for (int k = lane; k < len; k += 32) cols_s[k] = col_idx[rb + k];
+            for (int k = lane; k < len; k += 32) cols_s[k] = node_col[rb + k];
             __syncwarp();
         }
-        for (int64_t s = adj_ptr[i]; s < adj_ptr[i + 1]; ++s) {
-            const uint32_t t = adj[s];
-            const int32_t *De = D + (int64_t)(t / (uint32_t)n_loc) * n_loc;
-            for (int c = lane; c < n_loc; c += 32) {
-                const int32_t j = De[c];
-                int lo = 0, hi = len;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (cols[mid] < j) lo = mid + 1; else hi = mid;
-                }
-                if (lo >= len || cols[lo] != j) set_err(sc, FE_ERR_DEVICE);
-                map[(int64_t)t * n_loc + c] = (MT)lo;
+        const int64_t a = adj_ptr[v], b = adj_ptr[v + 1];
+        // (incidence, local node) pairs of this row, spread over the lanes
+        const int total = (int)(b - a) * nln;
+        for (int q = lane; q < total; q += 32) {
+            const int s = q / nln;
+            const int kc = q - s * nln;
+            const uint32_t t = adj[a + s];
+            const int32_t j = N[(int64_t)(t / (uint32_t)nln) * nln + kc];
+            int lo = 0, hi = len;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (cols[mid] < j) lo = mid + 1; else hi = mid;
             }
+            if (lo >= len || cols[lo] != j) set_err(sc, FE_ERR_DEVICE);
+            map[(int64_t)t * nln + kc] = (MT)lo;
         }
         __syncwarp();
     }
 }
 
-// CRAC slot map: for every incidence t = e*n_loc + r and every run k of
-// element e's DOFs, the value position of the run's first DOF in row
-// i = D_e(r), relative to the row's first value position.  The position is
-// found by the linear block search of Listing 1 over the row's pairs, read
-// with the row's own bound (the last block of the row is taken when no
-// later block starts at or before the column).
+// Run slot map: for every node incidence t = e*nln + k of node row v and
+// every run of element e's blocks, the position (in blocks) of the run's
+// first block in row v, found by Listing 1's block search over the CRAC
+// pairs of DOF row B*v, read with the row's own bound: the last block of
+// the row is taken when no later block starts at or before the column.
 template <typename MT>
-__global__ void k_map_crac(const int32_t *__restrict__ D, int32_t n_loc, int64_t n_dofs, int mask_words,
+__global__ void k_map_runs(const int32_t *__restrict__ N, int32_t nln, int64_t n_nodes, int32_t B, int mask_words,
                            const int64_t *__restrict__ adj_ptr, const uint32_t *__restrict__ adj,
                            const int64_t *__restrict__ crac_ptr, const int32_t *__restrict__ col_align,
                            const uint32_t *__restrict__ run_mask, const int64_t *__restrict__ run_ptr, int cap,
@@ -273,9 +431,10 @@ __global__ void k_map_crac(const int32_t *__restrict__ D, int32_t n_loc, int64_t
     extern __shared__ int32_t sbuf[];
     const int lane = threadIdx.x & 31;
     int32_t *ca_s = sbuf + (size_t)(threadIdx.x >> 5) * cap;
-    for (int64_t i = warp_id_global(); i < n_dofs; i += warps_total()) {
-        const int64_t pb = crac_ptr[i];
-        const int np = (int)(crac_ptr[i + 1] - pb);  // ints of this row's pairs
+    for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
+        const int64_t i0 = (int64_t)B * v;
+        const int64_t pb = crac_ptr[i0];
+        const int np = (int)(crac_ptr[i0 + 1] - pb);  // ints of this row's pairs
         if (np == 0) continue;
         const bool in_smem = np + 2 <= cap;
         const int32_t *ca = in_smem ? ca_s : col_align + pb;
@@ -284,20 +443,19 @@ __global__ void k_map_crac(const int32_t *__restrict__ D, int32_t n_loc, int64_t
             __syncwarp();
         }
         const int32_t row_base = ca[1];
-        for (int64_t s = adj_ptr[i]; s < adj_ptr[i + 1]; ++s) {
+        for (int64_t s = adj_ptr[v]; s < adj_ptr[v + 1]; ++s) {
             const uint32_t t = adj[s];
-            const int64_t e = t / (uint32_t)n_loc;
-            const int r = (int)(t - (uint32_t)(e * n_loc));
-            const int32_t *De = D + e * n_loc;
+            const int64_t e = t / (uint32_t)nln;
+            const int k = (int)(t - (uint32_t)(e * nln));
             const int64_t rp = run_ptr[e];
             const int nr = (int)(run_ptr[e + 1] - rp);
-            int before = 0;  // runs that start in earlier 32-column chunks
-            for (int c0 = 0; c0 < n_loc; c0 += 32) {
+            int before = 0;
+            for (int c0 = 0; c0 < nln; c0 += 32) {
                 const uint32_t m = run_mask[e * mask_words + (c0 >> 5)];
-                const int c = c0 + lane;
-                if (c < n_loc && ((m >> lane) & 1u)) {
-                    const int k = before + __popc(m & ((1u << lane) - 1u));
-                    const int32_t j = De[c];
+                const int kc = c0 + lane;
+                if (kc < nln && ((m >> lane) & 1u)) {
+                    const int ri = before + __popc(m & ((1u << lane) - 1u));
+                    const int32_t j = B * N[e * nln + kc];
                     int p = 0;
                     while (p + 2 < np) {
                         if (ca[p + 2] > j) break;
@@ -307,9 +465,9 @@ __global__ void k_map_crac(const int32_t *__restrict__ D, int32_t n_loc, int64_t
                     const int32_t val_start = ca[p + 1];
                     const int32_t col_end = col_start + (ca[p + 3] - val_start);
                     int32_t rel = 0;
-                    if (j >= col_start && j < col_end) rel = val_start + (j - col_start) - row_base;
+                    if (j >= col_start && j < col_end) rel = (val_start + (j - col_start) - row_base) / B;
                     else set_err(sc, FE_ERR_DEVICE);
-                    mapc[rp * n_loc + (int64_t)r * nr + k] = (MT)rel;
+                    mapc[rp * nln + (int64_t)k * nr + ri] = (MT)rel;
                 }
                 before += __popc(m);
             }
@@ -320,7 +478,7 @@ __global__ void k_map_crac(const int32_t *__restrict__ D, int32_t n_loc, int64_t
 
 struct Scratch {
     cudaStream_t s;
-    void *p[8] = {};
+    void *p[12] = {};
     int n = 0;
     void add(void *x) { p[n++] = x; }
     ~Scratch()
@@ -331,8 +489,8 @@ struct Scratch {
 
 void pattern_release(fe_pattern *p, cudaStream_t s)
 {
-    void *ptrs[] = {p->elem_dofs, p->row_ptr, p->col_idx, p->crac_ptr, p->col_align,
-                    p->adj_ptr,  p->adj,     p->map_csr, p->run_mask, p->run_ptr, p->map_crac};
+    void *ptrs[] = {p->node_dofs, p->row_ptr, p->col_idx, p->crac_ptr, p->col_align, p->adj_ptr,
+                    p->adj,       p->map_csr, p->run_mask, p->run_ptr, p->map_crac};
     for (void *x : ptrs) fe_free_async(x, s);
     delete p;
 }
@@ -351,168 +509,206 @@ int configure_smem(KernelT kernel, size_t bytes)
     return FE_OK;
 }
 
-int build_impl(fe_pattern *p, const int32_t *elem_dofs_in, cudaStream_t s)
+#define FE_LAUNCH(...) \
+    do {               \
+        __VA_ARGS__;   \
+        fe_note_launch(); \
+    } while (0)
+
+int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
 {
     fe_ctx *ctx = p->ctx;
     const int64_t n_e = p->n_e, n_dofs = p->n_dofs;
     const int32_t n_loc = p->n_loc;
-    const int64_t n_inc = n_e * n_loc;
     const int sms = ctx->num_sms;
     Scratch tmp;
     tmp.s = s;
 
     int64_t *sc = nullptr;
-    int32_t *deg = nullptr, *runs = nullptr;
     FE_TRY(fe_alloc(ctx, (void **)&sc, sizeof(int64_t) * S_COUNT, s));
     tmp.add(sc);
-    FE_TRY(fe_alloc(ctx, (void **)&deg, sizeof(int32_t) * (size_t)(n_dofs + 1), s));
+    FE_CUDA(cudaMemsetAsync(sc, 0, sizeof(int64_t) * S_COUNT, s));
+    FE_CUDA(cudaMemsetAsync(sc + S_BLOCKS, 0xff, sizeof(int64_t), s));
+
+    // A1: validation and block size
+    if (n_e > 0) {
+        FE_LAUNCH((k_validate<<<fe_grid_for(n_e * 32, 256, sms, 16), 256, 0, s>>>(elem_dofs, n_e, n_loc, n_dofs, sc)));
+        FE_CUDA(cudaGetLastError());
+    }
+    int64_t h1[S_COUNT];
+    FE_CUDA(cudaMemcpyAsync(h1, sc, sizeof(int64_t) * S_COUNT, cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));  // sync 1: validation result, block size
+    if (h1[S_ERR] != 0) return (int)h1[S_ERR];
+    int B = 1;
+    const uint32_t bmask = (uint32_t)h1[S_BLOCKS];
+    for (int b = 32; b >= 2; --b)
+        if (((bmask >> (b - 1)) & 1u) && n_loc % b == 0 && n_dofs % b == 0) {
+            B = b;
+            break;
+        }
+    if (n_e == 0) B = 1;
+    p->B = B;
+    p->nln = n_loc / B;
+    p->n_nodes = n_dofs / B;
+    const int32_t nln = p->nln;
+    const int64_t n_nodes = p->n_nodes;
+    const int64_t n_ninc = n_e * nln;
+    p->mask_words = (nln + 31) / 32;
+
+    // A2: block connectivity, runs, degrees
+    int32_t *deg = nullptr, *runs = nullptr;
+    FE_TRY(fe_alloc(ctx, (void **)&deg, sizeof(int32_t) * (size_t)(n_nodes + 1), s));
     tmp.add(deg);
     FE_TRY(fe_alloc(ctx, (void **)&runs, sizeof(int32_t) * (size_t)(n_e + 1), s));
     tmp.add(runs);
-    FE_CUDA(cudaMemsetAsync(sc, 0, sizeof(int64_t) * S_COUNT, s));
-    FE_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)(n_dofs + 1), s));
-
-    p->mask_words = (n_loc + 31) / 32;
-    FE_TRY(alloc_into(p, (void **)&p->elem_dofs, sizeof(int32_t) * (size_t)n_inc, s));
-    FE_TRY(alloc_into(p, (void **)&p->run_mask, sizeof(uint32_t) * (size_t)(n_e * p->mask_words), s));
+    FE_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)(n_nodes + 1), s));
+    FE_TRY(alloc_into(p, (void **)&p->node_dofs, sizeof(int32_t) * (size_t)(n_ninc + 1), s));
+    FE_TRY(alloc_into(p, (void **)&p->run_mask, sizeof(uint32_t) * (size_t)(n_e * p->mask_words + 1), s));
     FE_TRY(alloc_into(p, (void **)&p->run_ptr, sizeof(int64_t) * (size_t)(n_e + 1), s));
-    if (n_inc > 0)
-        FE_CUDA(cudaMemcpyAsync(p->elem_dofs, elem_dofs_in, sizeof(int32_t) * (size_t)n_inc,
-                                cudaMemcpyDeviceToDevice, s));
-
-    // A1 + A2 counting
     if (n_e > 0) {
-        k_elements<<<fe_grid_for(n_e * 32, 256, sms, 16), 256, 0, s>>>(p->elem_dofs, n_e, n_loc, n_dofs,
-                                                                       p->mask_words, p->run_mask, runs, sc); fe_note_launch();
-        k_count_deg<<<fe_grid_for(n_inc, 256, sms, 16), 256, 0, s>>>(p->elem_dofs, n_inc, n_dofs, deg); fe_note_launch();
-        k_max_i32<<<fe_grid_for(n_dofs, 256, sms, 8), 256, 0, s>>>(deg, n_dofs, sc + S_MAX_DEG); fe_note_launch();
+        FE_LAUNCH((k_node_conn<<<fe_grid_for(n_e * 32, 256, sms, 16), 256, 0, s>>>(
+            elem_dofs, n_e, n_loc, B, nln, p->mask_words, p->node_dofs, p->run_mask, runs, deg, sc)));
+        FE_LAUNCH((k_max_i32<<<fe_grid_for(n_nodes, 256, sms, 8), 256, 0, s>>>(deg, n_nodes, sc + S_MAX_DEG)));
         FE_CUDA(cudaGetLastError());
     }
     FE_TRY(fe_scan_i32_to_i64(ctx, runs, p->run_ptr, n_e, s));
-
-    int64_t h1[S_COUNT + 1];
-    FE_CUDA(cudaMemcpyAsync(h1, sc, sizeof(int64_t) * S_COUNT, cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaMemcpyAsync(h1 + S_COUNT, p->run_ptr + n_e, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaStreamSynchronize(s));  // sync 1: validation result and sizes
-    if (h1[S_ERR] != 0) return (int)h1[S_ERR];
-    p->max_deg = (int32_t)h1[S_MAX_DEG];
-    p->n_runs = h1[S_COUNT];
-    p->uniform_runs = (h1[S_NONUNIFORM] == 0) && n_e > 0;
-    p->runs_per_elem = n_e > 0 ? (int32_t)(p->n_runs / n_e) : 0;
-
-    const int64_t cand = (int64_t)p->max_deg * n_loc;
-    int P = 32;
-    while (P < cand) P <<= 1;
-    if ((int64_t)P * 4 > 128 * 1024) return FE_ERR_UNSUPPORTED;
-
-    // A2: adjacency
-    FE_TRY(alloc_into(p, (void **)&p->adj_ptr, sizeof(int64_t) * (size_t)(n_dofs + 1), s));
-    FE_TRY(alloc_into(p, (void **)&p->adj, sizeof(uint32_t) * (size_t)(n_inc + 1), s));
-    FE_TRY(fe_scan_i32_to_i64(ctx, deg, p->adj_ptr, n_dofs, s));
-    FE_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)(n_dofs + 1), s));
-    if (n_inc > 0) {
-        k_fill_adj<<<fe_grid_for(n_inc, 256, sms, 16), 256, 0, s>>>(p->elem_dofs, n_inc, p->adj_ptr, deg, p->adj); fe_note_launch();
-        k_sort_adj<<<fe_grid_for(n_dofs, 128, sms, 16), 128, 0, s>>>(p->adj_ptr, n_dofs, p->adj); fe_note_launch();
+    FE_TRY(alloc_into(p, (void **)&p->adj_ptr, sizeof(int64_t) * (size_t)(n_nodes + 1), s));
+    FE_TRY(alloc_into(p, (void **)&p->adj, sizeof(uint32_t) * (size_t)(n_ninc + 1), s));
+    FE_TRY(fe_scan_i32_to_i64(ctx, deg, p->adj_ptr, n_nodes, s));
+    FE_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)(n_nodes + 1), s));
+    if (n_ninc > 0) {
+        FE_LAUNCH((k_fill_adj<<<fe_grid_for(n_ninc, 256, sms, 16), 256, 0, s>>>(p->node_dofs, n_ninc, n_nodes,
+                                                                                 p->adj_ptr, deg, p->adj)));
+        FE_LAUNCH((k_sort_adj<<<fe_grid_for(n_nodes, 128, sms, 16), 128, 0, s>>>(p->adj_ptr, n_nodes, p->adj)));
         FE_CUDA(cudaGetLastError());
     }
+    int64_t h2[S_COUNT + 1];
+    FE_CUDA(cudaMemcpyAsync(h2, sc, sizeof(int64_t) * S_COUNT, cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaMemcpyAsync(h2 + S_COUNT, p->run_ptr + n_e, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));  // sync 2: largest degree, element runs
+    p->max_deg = (int32_t)h2[S_MAX_DEG];
+    p->n_runs = h2[S_COUNT];
+    p->uniform_runs = (h2[S_NONUNIFORM] == 0) && n_e > 0;
+    p->runs_per_elem = n_e > 0 ? (int32_t)(p->n_runs / n_e) : 0;
 
-    // A3 pass 1: row lengths and runs
-    int32_t *row_len = nullptr, *row_runs2 = nullptr;
+    // A3 pass 1: node row lengths and runs
+    const int64_t cand = (int64_t)p->max_deg * nln;
+    int P = 0, W = 8;
+    if (cand > REG_SORT_MAX) {
+        P = 32;
+        while (P < cand) P <<= 1;
+        if ((int64_t)P * 4 > 128 * 1024) return FE_ERR_UNSUPPORTED;
+        W = (int)std::max<int64_t>(1, std::min<int64_t>(8, (64 * 1024) / ((int64_t)P * 4)));
+    }
+    const size_t smem_rows = (size_t)W * P * 4;
+    FE_TRY(configure_smem(k_node_rows<1>, smem_rows));
+    FE_TRY(configure_smem(k_node_rows<2>, smem_rows));
+    const int grid_rows = fe_grid_for(n_nodes * 32, W * 32, sms, std::max(1, 64 / W));
+    int32_t *node_len = nullptr, *row_len = nullptr, *row_runs2 = nullptr;
+    int64_t *node_row_ptr = nullptr;
+    FE_TRY(fe_alloc(ctx, (void **)&node_len, sizeof(int32_t) * (size_t)(n_nodes + 1), s));
+    tmp.add(node_len);
     FE_TRY(fe_alloc(ctx, (void **)&row_len, sizeof(int32_t) * (size_t)(n_dofs + 1), s));
     tmp.add(row_len);
     FE_TRY(fe_alloc(ctx, (void **)&row_runs2, sizeof(int32_t) * (size_t)(n_dofs + 1), s));
     tmp.add(row_runs2);
-    const int W = (int)std::max<int64_t>(1, std::min<int64_t>(8, (48 * 1024) / ((int64_t)P * 4)));
-    const size_t smem_rows = (size_t)W * P * 4;
-    FE_TRY(configure_smem(k_rows<1>, smem_rows));
-    FE_TRY(configure_smem(k_rows<2>, smem_rows));
-    const int grid_rows = fe_grid_for(n_dofs * 32, W * 32, sms, 64 / W > 0 ? 64 / W : 1);
-    if (n_dofs > 0) {
-        k_rows<1><<<grid_rows, W * 32, smem_rows, s>>>(p->elem_dofs, n_loc, n_dofs, p->adj_ptr, p->adj, P, row_len,
-                                                       row_runs2, sc, nullptr, nullptr, nullptr, nullptr); fe_note_launch();
+    FE_TRY(fe_alloc(ctx, (void **)&node_row_ptr, sizeof(int64_t) * (size_t)(n_nodes + 1), s));
+    tmp.add(node_row_ptr);
+    RowOut o{};
+    o.node_len = node_len;
+    o.row_len = row_len;
+    o.row_runs2 = row_runs2;
+    if (n_nodes > 0) {
+        FE_LAUNCH((k_node_rows<1><<<grid_rows, W * 32, smem_rows, s>>>(p->node_dofs, nln, n_nodes, B, p->adj_ptr,
+                                                                       p->adj, P, o, sc)));
         FE_CUDA(cudaGetLastError());
     }
     FE_TRY(alloc_into(p, (void **)&p->row_ptr, sizeof(int64_t) * (size_t)(n_dofs + 1), s));
     FE_TRY(alloc_into(p, (void **)&p->crac_ptr, sizeof(int64_t) * (size_t)(n_dofs + 1), s));
+    FE_TRY(fe_scan_i32_to_i64(ctx, node_len, node_row_ptr, n_nodes, s));
     FE_TRY(fe_scan_i32_to_i64(ctx, row_len, p->row_ptr, n_dofs, s));
     FE_TRY(fe_scan_i32_to_i64(ctx, row_runs2, p->crac_ptr, n_dofs, s));
 
-    int64_t h2[3];
-    FE_CUDA(cudaMemcpyAsync(&h2[0], p->row_ptr + n_dofs, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaMemcpyAsync(&h2[1], p->crac_ptr + n_dofs, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaMemcpyAsync(&h2[2], sc + S_MAX_ROW, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaStreamSynchronize(s));  // sync 2: nnz, n_ca, longest row
-    p->nnz = h2[0];
-    p->n_ca = h2[1] + 2;
-    p->max_row_len = (int32_t)h2[2];
+    int64_t h3[4];
+    FE_CUDA(cudaMemcpyAsync(&h3[0], p->row_ptr + n_dofs, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaMemcpyAsync(&h3[1], p->crac_ptr + n_dofs, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaMemcpyAsync(&h3[2], sc + S_MAX_NODE, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaMemcpyAsync(&h3[3], node_row_ptr + n_nodes, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));  // sync 3: nnz, n_ca, longest row
+    p->nnz = h3[0];
+    p->n_ca = h3[1] + 2;
+    p->max_node_len = (int32_t)h3[2];
+    p->max_row_len = B * p->max_node_len;
+    const int64_t node_nnz = h3[3];
     if (p->nnz >= INT32_MAX || p->n_ca >= INT32_MAX) return FE_ERR_OVERFLOW;
-    p->map_bytes = p->max_row_len <= 256 ? 1 : 2;
-    if (p->max_row_len > 65536 && (p->flags & (FE_PATTERN_MAP_CSR | FE_PATTERN_MAP_CRAC))) return FE_ERR_UNSUPPORTED;
+    p->map_bytes = p->max_node_len <= 256 ? 1 : 2;
+    if (p->max_node_len > 65536) return FE_ERR_UNSUPPORTED;
 
-    // A3 pass 2 + A4: col_idx and CRAC pairs
+    // A3 pass 2 + CRAC pairs
+    int32_t *node_col = nullptr;
+    FE_TRY(fe_alloc(ctx, (void **)&node_col, sizeof(int32_t) * (size_t)(node_nnz + 1), s));
+    tmp.add(node_col);
     FE_TRY(alloc_into(p, (void **)&p->col_idx, sizeof(int32_t) * (size_t)(p->nnz + 1), s));
-    const bool want_crac = (p->flags & (FE_PATTERN_CRAC | FE_PATTERN_MAP_CRAC)) != 0;
-    if (want_crac) FE_TRY(alloc_into(p, (void **)&p->col_align, sizeof(int32_t) * (size_t)p->n_ca, s));
-    if (n_dofs > 0) {
-        k_rows<2><<<grid_rows, W * 32, smem_rows, s>>>(p->elem_dofs, n_loc, n_dofs, p->adj_ptr, p->adj, P, nullptr,
-                                                       nullptr, sc, p->row_ptr, p->crac_ptr, p->col_idx,
-                                                       want_crac ? p->col_align : nullptr); fe_note_launch();
+    FE_TRY(alloc_into(p, (void **)&p->col_align, sizeof(int32_t) * (size_t)p->n_ca, s));
+    o.node_row_ptr = node_row_ptr;
+    o.row_ptr = p->row_ptr;
+    o.crac_ptr = p->crac_ptr;
+    o.node_col = node_col;
+    o.col_idx = p->col_idx;
+    o.col_align = p->col_align;
+    if (n_nodes > 0) {
+        FE_LAUNCH((k_node_rows<2><<<grid_rows, W * 32, smem_rows, s>>>(p->node_dofs, nln, n_nodes, B, p->adj_ptr,
+                                                                       p->adj, P, o, sc)));
         FE_CUDA(cudaGetLastError());
     }
-    if (want_crac) {
-        k_final_pair<<<1, 1, 0, s>>>(p->col_align, p->n_ca, n_dofs, p->nnz); fe_note_launch();
-        FE_CUDA(cudaGetLastError());
-    }
+    FE_LAUNCH((k_final_pair<<<1, 1, 0, s>>>(p->col_align, p->n_ca, n_dofs, p->nnz)));
+    FE_CUDA(cudaGetLastError());
 
     // A5: slot maps
     const int WM = 8;
     if (p->flags & FE_PATTERN_MAP_CSR) {
-        const size_t bytes = (size_t)n_inc * n_loc * p->map_bytes;
-        FE_TRY(alloc_into(p, &p->map_csr, bytes, s));
-        int cap = std::min<int>(p->max_row_len, 4096);
-        if (cap < 1) cap = 1;
+        FE_TRY(alloc_into(p, &p->map_csr, (size_t)(n_ninc * nln + 1) * p->map_bytes, s));
+        const int cap = std::max(1, std::min(p->max_node_len, 4096));
         const size_t smem = (size_t)WM * cap * 4;
-        if (n_dofs > 0) {
+        if (n_nodes > 0) {
             if (p->map_bytes == 1) {
-                FE_TRY(configure_smem(k_map_csr<uint8_t>, smem));
-                k_map_csr<uint8_t><<<fe_grid_for(n_dofs * 32, WM * 32, sms, 8), WM * 32, smem, s>>>(
-                    p->elem_dofs, n_loc, n_dofs, p->adj_ptr, p->adj, p->row_ptr, p->col_idx, cap,
-                    (uint8_t *)p->map_csr, sc); fe_note_launch();
+                FE_TRY(configure_smem(k_map_node<uint8_t>, smem));
+                FE_LAUNCH((k_map_node<uint8_t><<<fe_grid_for(n_nodes * 32, WM * 32, sms, 8), WM * 32, smem, s>>>(
+                    p->node_dofs, nln, n_nodes, p->adj_ptr, p->adj, node_row_ptr, node_col, cap,
+                    (uint8_t *)p->map_csr, sc)));
             } else {
-                FE_TRY(configure_smem(k_map_csr<uint16_t>, smem));
-                k_map_csr<uint16_t><<<fe_grid_for(n_dofs * 32, WM * 32, sms, 8), WM * 32, smem, s>>>(
-                    p->elem_dofs, n_loc, n_dofs, p->adj_ptr, p->adj, p->row_ptr, p->col_idx, cap,
-                    (uint16_t *)p->map_csr, sc); fe_note_launch();
+                FE_TRY(configure_smem(k_map_node<uint16_t>, smem));
+                FE_LAUNCH((k_map_node<uint16_t><<<fe_grid_for(n_nodes * 32, WM * 32, sms, 8), WM * 32, smem, s>>>(
+                    p->node_dofs, nln, n_nodes, p->adj_ptr, p->adj, node_row_ptr, node_col, cap,
+                    (uint16_t *)p->map_csr, sc)));
             }
             FE_CUDA(cudaGetLastError());
         }
     }
     if (p->flags & FE_PATTERN_MAP_CRAC) {
-        const size_t bytes = (size_t)p->n_runs * n_loc * p->map_bytes;
-        FE_TRY(alloc_into(p, &p->map_crac, bytes, s));
-        int cap = std::min<int>(2 * p->max_row_len + 2, 8192);
+        FE_TRY(alloc_into(p, &p->map_crac, (size_t)(p->n_runs * nln + 1) * p->map_bytes, s));
+        const int cap = std::max(4, std::min(2 * p->max_node_len + 2, 8192));
         const size_t smem = (size_t)WM * cap * 4;
-        if (n_dofs > 0) {
+        if (n_nodes > 0) {
             if (p->map_bytes == 1) {
-                FE_TRY(configure_smem(k_map_crac<uint8_t>, smem));
-                k_map_crac<uint8_t><<<fe_grid_for(n_dofs * 32, WM * 32, sms, 8), WM * 32, smem, s>>>(
-                    p->elem_dofs, n_loc, n_dofs, p->mask_words, p->adj_ptr, p->adj, p->crac_ptr, p->col_align,
-                    p->run_mask, p->run_ptr, cap, (uint8_t *)p->map_crac, sc); fe_note_launch();
+                FE_TRY(configure_smem(k_map_runs<uint8_t>, smem));
+                FE_LAUNCH((k_map_runs<uint8_t><<<fe_grid_for(n_nodes * 32, WM * 32, sms, 8), WM * 32, smem, s>>>(
+                    p->node_dofs, nln, n_nodes, B, p->mask_words, p->adj_ptr, p->adj, p->crac_ptr, p->col_align,
+                    p->run_mask, p->run_ptr, cap, (uint8_t *)p->map_crac, sc)));
             } else {
-                FE_TRY(configure_smem(k_map_crac<uint16_t>, smem));
-                k_map_crac<uint16_t><<<fe_grid_for(n_dofs * 32, WM * 32, sms, 8), WM * 32, smem, s>>>(
-                    p->elem_dofs, n_loc, n_dofs, p->mask_words, p->adj_ptr, p->adj, p->crac_ptr, p->col_align,
-                    p->run_mask, p->run_ptr, cap, (uint16_t *)p->map_crac, sc); fe_note_launch();
+                FE_TRY(configure_smem(k_map_runs<uint16_t>, smem));
+                FE_LAUNCH((k_map_runs<uint16_t><<<fe_grid_for(n_nodes * 32, WM * 32, sms, 8), WM * 32, smem, s>>>(
+                    p->node_dofs, nln, n_nodes, B, p->mask_words, p->adj_ptr, p->adj, p->crac_ptr, p->col_align,
+                    p->run_mask, p->run_ptr, cap, (uint16_t *)p->map_crac, sc)));
             }
             FE_CUDA(cudaGetLastError());
         }
     }
-    if (!(p->flags & FE_PATTERN_ADJ)) {
-        fe_free_async(p->adj, s);
-        fe_free_async(p->adj_ptr, s);
-        p->device_bytes -= (int64_t)(sizeof(uint32_t) * (size_t)(n_inc + 1) + sizeof(int64_t) * (size_t)(n_dofs + 1));
-        p->adj = nullptr;
-        p->adj_ptr = nullptr;
+    if (!(p->flags & FE_PATTERN_CRAC) && !(p->flags & FE_PATTERN_MAP_CRAC)) {
+        // CRAC was only scaffolding for this pattern
+        fe_free_async(p->col_align, s);
+        p->device_bytes -= (int64_t)(sizeof(int32_t) * (size_t)p->n_ca);
+        p->col_align = nullptr;
     }
     return FE_OK;
 }
@@ -541,7 +737,7 @@ int fe_pattern_build(fe_ctx *ctx, int64_t n_elem, int32_t dofs_per_elem, int64_t
     p->n_e = n_elem;
     p->n_loc = dofs_per_elem;
     p->n_dofs = n_dofs;
-    p->flags = flags | FE_PATTERN_CSR;
+    p->flags = flags | FE_PATTERN_CSR | FE_PATTERN_ADJ;  // adjacency is kept: it is small
     if (p->flags & FE_PATTERN_MAP_CRAC) p->flags |= FE_PATTERN_CRAC;
     int rc = build_impl(p, elem_dofs, s);
     if (rc != FE_OK) {
@@ -559,8 +755,8 @@ int fe_pattern_free(fe_pattern *p)
     if (!p) return FE_ERR_INVALID_ARG;
     int prev = -1;
     cudaGetDevice(&prev);
-    if (prev != p->ctx->device) cudaSetDevice(p->ctx->device);
     const int dev = p->ctx->device;
+    if (prev != dev) cudaSetDevice(dev);
     cudaDeviceSynchronize();
     pattern_release(p, 0);
     cudaStreamSynchronize(0);
@@ -587,10 +783,11 @@ int fe_pattern_crac(const fe_pattern *p, const int64_t **row_ptr, const int32_t 
     return FE_OK;
 }
 
-int fe_pattern_adjacency(const fe_pattern *p, const int64_t **adj_ptr, const uint32_t **adj)
+int fe_pattern_adjacency(const fe_pattern *p, int32_t *block, const int64_t **adj_ptr, const uint32_t **adj)
 {
     if (!p) return FE_ERR_INVALID_ARG;
     if (!p->adj) return FE_ERR_NOT_BUILT;
+    if (block) *block = p->B;
     if (adj_ptr) *adj_ptr = p->adj_ptr;
     if (adj) *adj = p->adj;
     return FE_OK;
@@ -609,7 +806,8 @@ int fe_pattern_info_get(const fe_pattern *p, fe_pattern_info *out)
     out->max_row_len = p->max_row_len;
     out->max_degree = p->max_deg;
     out->flags = p->flags;
-    out->reserved = p->uniform_runs ? 1u : 0u;
+    out->block = p->B;
+    out->uniform_runs = p->uniform_runs ? 1 : 0;
     out->device_bytes = p->device_bytes;
     return FE_OK;
 }

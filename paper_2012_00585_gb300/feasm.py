@@ -64,7 +64,9 @@ class fe_pattern_info(ctypes.Structure):
         ("max_row_len", ctypes.c_int32),
         ("max_degree", ctypes.c_int32),
         ("flags", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32),
+        ("block", ctypes.c_int32),
+        ("uniform_runs", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
         ("device_bytes", ctypes.c_int64),
     ]
 
@@ -95,7 +97,7 @@ def load():
             "fe_pattern_free": (i, [vp]),
             "fe_pattern_csr": (i, [vp, pp, pp, ctypes.POINTER(i64)]),
             "fe_pattern_crac": (i, [vp, pp, pp, ctypes.POINTER(i64)]),
-            "fe_pattern_adjacency": (i, [vp, pp, pp]),
+            "fe_pattern_adjacency": (i, [vp, ctypes.POINTER(i32), pp, pp]),
             "fe_pattern_info_get": (i, [vp, ctypes.POINTER(fe_pattern_info)]),
             "fe_assemble_csr": (i, [vp, vp, vp, vp, i, i, vp]),
             "fe_assemble_crac": (i, [vp, vp, vp, vp, i, i, vp]),
@@ -186,9 +188,10 @@ def fe_pattern_crac(pattern):
 
 
 def fe_pattern_adjacency(pattern):
-    ap, a = ctypes.c_void_p(), ctypes.c_void_p()
-    _check(load().fe_pattern_adjacency(pattern, ctypes.byref(ap), ctypes.byref(a)), "fe_pattern_adjacency")
-    return ap.value, a.value
+    blk, ap, a = ctypes.c_int32(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load().fe_pattern_adjacency(pattern, ctypes.byref(blk), ctypes.byref(ap), ctypes.byref(a)),
+           "fe_pattern_adjacency")
+    return blk.value, ap.value, a.value
 
 
 def fe_pattern_info_get(pattern) -> dict:
@@ -245,10 +248,11 @@ class Pattern:
         return device_view(rp, self.info["n_dofs"] + 1, torch.int64), device_view(ca, n, torch.int32)
 
     def adjacency(self):
+        """(B, adj_ptr [n_dofs/B + 1], adj [n_elem * n_loc / B]) as torch views."""
         import torch
-        ap, a = fe_pattern_adjacency(self.handle)
-        n_inc = self.info["n_elem"] * self.info["n_loc"]
-        return device_view(ap, self.info["n_dofs"] + 1, torch.int64), device_view(a, n_inc, torch.uint32)
+        blk, ap, a = fe_pattern_adjacency(self.handle)
+        n_inc = self.info["n_elem"] * self.info["n_loc"] // blk
+        return blk, device_view(ap, self.info["n_dofs"] // blk + 1, torch.int64), device_view(a, n_inc, torch.int32)
 
     def free(self):
         if self.handle is not None:

@@ -36,17 +36,31 @@ def _check_pattern(g, D, n_dofs):
     crp, ca = g.crac_host()
     assert np.array_equal(crp, crp_o)
     assert np.array_equal(ca, ca_o)
-    ap, adj = [x.cpu().numpy() for x in g.pattern.adjacency()]
-    deg = np.bincount(D.ravel(), minlength=n_dofs)
-    assert np.array_equal(np.diff(ap), deg)
+    B, ap, adj = g.pattern.adjacency()
+    ap, adj = ap.cpu().numpy(), adj.cpu().numpy()
     n_loc = D.shape[1]
-    inc = np.arange(D.size, dtype=np.int64)
-    order = np.argsort(D.ravel(), kind="stable")  # stable: ascending incidence id per DOF
+    # the block size is the largest B <= 32 for which every element lists
+    # whole aligned blocks of B consecutive DOFs
+    exp_B = 1
+    for b in range(32, 1, -1):
+        if n_loc % b == 0 and n_dofs % b == 0 and D.shape[0] > 0:
+            blk = D.reshape(D.shape[0], n_loc // b, b)
+            if np.all(blk[:, :, 0] % b == 0) and np.all(blk - blk[:, :, :1] == np.arange(b)):
+                exp_B = b
+                break
+    assert B == exp_B
+    Nn = D[:, ::B] // B
+    deg = np.bincount(Nn.ravel(), minlength=n_dofs // B)
+    assert np.array_equal(np.diff(ap), deg)
+    inc = np.arange(Nn.size, dtype=np.int64)
+    order = np.argsort(Nn.ravel(), kind="stable")  # stable: ascending incidence id per block
     assert np.array_equal(adj.astype(np.int64), inc[order])
     info = g.pattern.info
+    assert info["block"] == B
     assert info["nnz"] == rp_o[-1] and info["n_ca"] == ca_o.shape[0]
     assert info["max_row_len"] == int(np.max(np.diff(rp_o))) if n_dofs else True
-    assert info["n_elem_runs"] == sum(len(oracle.compress_dofs(row)) // 2 for row in D) or n_loc > 64
+    # runs of consecutive blocks per element (the compressed DOF array of §2.1, at block level)
+    assert info["n_elem_runs"] == sum(len(oracle.compress_dofs(row)) // 2 for row in Nn)
     return rp_o, ci_o, crp_o, ca_o
 
 
@@ -103,7 +117,8 @@ def test_c3_p2_tets_permuted_spd(ctx, n):
     K = wl.random_spd_matrices(D.shape[0], 30, seed=n)
     g = gu.GpuAssembly(ctx, D, n_dofs)
     pat = _check_pattern(g, D, n_dofs)
-    assert not g.pattern.info["reserved"]  # run structure varies per element
+    assert not g.pattern.info["uniform_runs"]  # run structure varies per element
+    assert g.pattern.info["block"] == 3
     _run_all_modes(g, D, K, n_dofs, *pat)
     g.free()
 
@@ -281,7 +296,7 @@ def test_invalid_connectivity_reports_errors(ctx):
         feasm.fe_assemble_crac(ctx, p2.handle, K, v)
     assert ei.value.code == feasm.FE_ERR_NOT_BUILT
     with pytest.raises(feasm.FeError) as ei:
-        feasm.fe_assemble_csr(ctx, p2.handle, K, v, feasm.FE_DETERMINISTIC)
+        feasm.fe_pattern_crac(p2.handle)
     assert ei.value.code == feasm.FE_ERR_NOT_BUILT
     feasm.fe_assemble_csr(ctx, p2.handle, K, v, feasm.FE_ATOMIC)
     torch.cuda.synchronize()
