@@ -110,10 +110,35 @@ const char *fe_strerror(int code);
  * FE_ERR_OOM diagnostics); empty when there was none.  Never NULL. */
 const char *fe_last_cuda_error(void);
 
+/* Waits for `stream`, then returns the first error a kernel of this context
+ * recorded on the device since the last call (FE_OK if none) and clears it.
+ * Kernels record instead of trapping: a bounded wait that ran out gives
+ * FE_ERR_TIMEOUT and the kernel returns early, leaving its output
+ * incomplete. */
+int fe_device_status(fe_ctx *ctx, void *stream);
+
 /* Number of kernels this library has launched in this process so far (all
  * contexts and threads); a caller brackets a region with two reads to count
  * the launches inside it. */
 uint64_t fe_kernel_launches(void);
+
+/* ---- schedule knobs ------------------------------------------------------
+ * Kernel and launch-shape choices of the numeric phase, per context.  0 means
+ * the library's default; an autotuner may set them.  Results do not depend on
+ * them (FE_DETERMINISTIC stays bit-identical), only speed does. */
+#define FE_KNOB_GATHER_KERNEL 0  /* FE_DETERMINISTIC: 1 register-batched row gather,
+                                    2 shared-memory-staged row gather        */
+#define FE_KNOB_GATHER_BATCH 1   /* incidences per register batch: 4 or 8   */
+#define FE_KNOB_GATHER_WARPS 2   /* warps per block of the gather: 1..8      */
+#define FE_KNOB_ATOMIC_KERNEL 3  /* FE_ATOMIC: 1 register warp-per-element,
+                                    2 bulk-copy (TMA) staged warp-per-element */
+#define FE_KNOB_ATOMIC_WARPS 4   /* warps per block of the staged kernel     */
+#define FE_KNOB_COUNT 8
+
+/* Set / read one schedule knob.  FE_ERR_INVALID_ARG for an unknown knob or a
+ * value outside its range. */
+int fe_tune_set(fe_ctx *ctx, int knob, int value);
+int fe_tune_get(const fe_ctx *ctx, int knob, int *value);
 
 /* ---- symbolic phase ----------------------------------------------------- */
 

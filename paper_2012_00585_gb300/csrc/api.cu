@@ -214,6 +214,8 @@ int fe_create(fe_ctx **out, int device, size_t hbm_budget_bytes)
     props.location.type = cudaMemLocationTypeDevice;
     props.location.id = device;
     if (e == cudaSuccess) e = cudaMemPoolCreate(&ctx->pool, &props);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_status, 16);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, 16);
     if (e == cudaSuccess) {
         uint64_t keep = UINT64_MAX;  // keep freed blocks for reuse
         e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
@@ -221,6 +223,7 @@ int fe_create(fe_ctx **out, int device, size_t hbm_budget_bytes)
     if (e != cudaSuccess) {
         fe_set_last_cuda_error(e, "fe_create", __LINE__);
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+        if (ctx->d_status) cudaFree(ctx->d_status);
         delete ctx;
         return FE_ERR_DEVICE;
     }
@@ -241,8 +244,46 @@ int fe_destroy(fe_ctx *ctx)
     fe_batch_state_destroy(ctx);
     cudaDeviceSynchronize();
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    if (ctx->d_status) cudaFree(ctx->d_status);
     delete ctx;
     return FE_OK;
+}
+
+int fe_tune_set(fe_ctx *ctx, int knob, int value)
+{
+    if (!ctx || knob < 0 || knob >= FE_KNOB_COUNT) return FE_ERR_INVALID_ARG;
+    int lo = 0, hi = 0;
+    switch (knob) {
+    case FE_KNOB_GATHER_KERNEL: hi = 2; break;
+    case FE_KNOB_GATHER_BATCH: hi = 8; break;
+    case FE_KNOB_GATHER_WARPS: hi = 8; break;
+    case FE_KNOB_ATOMIC_KERNEL: hi = 2; break;
+    case FE_KNOB_ATOMIC_WARPS: hi = 8; break;
+    default: return FE_ERR_INVALID_ARG;
+    }
+    if (value < lo || value > hi) return FE_ERR_INVALID_ARG;
+    if (knob == FE_KNOB_GATHER_BATCH && value != 0 && value != 4 && value != 8) return FE_ERR_INVALID_ARG;
+    ctx->knob[knob] = value;
+    return FE_OK;
+}
+
+int fe_tune_get(const fe_ctx *ctx, int knob, int *value)
+{
+    if (!ctx || !value || knob < 0 || knob >= FE_KNOB_COUNT) return FE_ERR_INVALID_ARG;
+    *value = ctx->knob[knob];
+    return FE_OK;
+}
+
+int fe_device_status(fe_ctx *ctx, void *stream)
+{
+    if (!ctx) return FE_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    FE_CUDA(cudaMemcpyAsync(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    return h;
 }
 
 }  // extern "C"

@@ -34,6 +34,8 @@ struct fe_ctx {
     int num_sms = 0;
     size_t hbm_budget = 0;
     cudaMemPool_t pool = nullptr;
+    int *d_status = nullptr;  // device status word: first FE_ERR_* a kernel recorded
+    int knob[FE_KNOB_COUNT] = {};  // schedule choices (0 = library default)
     struct fe_batch_state *batch = nullptr;  // batching / serving scheduler
 };
 

@@ -19,6 +19,7 @@
 // (element, row block, run), the column's offset inside its run, and the
 // row start read from the CRAC pairs (Listing 5's contiguous slices).
 #include "internal.cuh"
+#include "tma.cuh"
 
 namespace {
 
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(256) k_atomic_generic(const double *__restrict
 // One warp per block row; the B rows of the node are contiguous in values.
 // Incidences are taken U at a time: their K slices and slots are loaded
 // first, then added strictly in ascending element order.
-template <int NLN, int BB, typename MT, bool CRAC>
+template <int NLN, int BB, typename MT, bool CRAC, int U>
 __global__ void __launch_bounds__(256) k_gather_node(const double *__restrict__ K, int64_t n_nodes, Geo g,
                                                      const MT *__restrict__ map, const MT *__restrict__ mapc, int cap,
                                                      int accumulate, double *values)
@@ -181,7 +182,6 @@ __global__ void __launch_bounds__(256) k_gather_node(const double *__restrict__ 
     constexpr int NN = NLOC * NLOC;
     constexpr int CHK = BB * NLOC;  // doubles of one incidence (B contiguous K rows)
     constexpr int IT = (CHK + 31) / 32;
-    constexpr int U = 4;
     extern __shared__ double acc_all[];
     const int lane = threadIdx.x & 31;
     double *acc = acc_all + (size_t)(threadIdx.x >> 5) * cap;
@@ -327,6 +327,264 @@ __global__ void __launch_bounds__(256) k_gather_generic(const double *__restrict
     }
 }
 
+
+// ------------------------------------------------- staged in smem ---
+// The same two assemblies with the element-matrix stream staged in shared
+// memory, double buffered: while a warp reduces one row (or element), the
+// copies of its next one are in flight.  The gather moves its scattered
+// 576..720-byte K slices with per-lane 16-byte asynchronous copies; the
+// atomic kernel moves each element's contiguous K with one bulk (TMA) copy
+// completed on an mbarrier, L2 evict-first so that values and maps stay
+// cached.  Shared memory per warp: two stages, then (gather) the row
+// accumulators, then (atomic) the per-element tables and two mbarriers.
+
+constexpr int GATHER_UMAX = 8;  // incidences staged per row (more are loaded directly)
+
+__host__ __device__ inline size_t gather_warp_bytes(int chk, int cap)
+{
+    const size_t b = ((size_t)2 * GATHER_UMAX * chk + (size_t)cap) * 8 + 16;
+    return (b + 127) & ~(size_t)127;
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(fe_smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Row gather with the K slices of the next row copied to shared memory by
+// per-lane 16-byte asynchronous copies while the current row is reduced.
+template <int NLN, int BB, typename MT, bool CRAC>
+__global__ void __launch_bounds__(128) k_gather_async(const double *__restrict__ K, int64_t n_nodes, Geo g,
+                                                      const MT *__restrict__ map, const MT *__restrict__ mapc, int cap,
+                                                      int accumulate, double *values)
+{
+    constexpr int NLOC = NLN * BB;
+    constexpr int NN = NLOC * NLOC;
+    constexpr int CHK = BB * NLOC;
+    constexpr int IT = (CHK + 31) / 32;
+    constexpr int Q16 = CHK / 2;  // 16-byte pieces per slice
+    constexpr int STAGE = GATHER_UMAX * CHK;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    double *stage0 = (double *)(smem_raw + (size_t)(threadIdx.x >> 5) * gather_warp_bytes(CHK, cap));
+    double *acc = stage0 + 2 * STAGE;
+    int jr_[IT], c_[IT], ku[IT], offu[IT];
+#pragma unroll
+    for (int j = 0; j < IT; ++j) {
+        const int q = lane + 32 * j;
+        const int qq = q < CHK ? q : 0;
+        jr_[j] = qq / NLOC;
+        c_[j] = qq % NLOC;
+        ku[j] = 0;
+        offu[j] = 0;
+        if (CRAC && g.uniform_R) run_of(g.run_mask[0], c_[j] / BB, ku[j], offu[j]);
+    }
+    // copy the first GATHER_UMAX slices of node row v into stage st (one commit group)
+    auto issue = [&](int64_t v, int st) -> int {
+        const int64_t a = g.adj_ptr[v];
+        const int n = (int)min((int64_t)GATHER_UMAX, g.adj_ptr[v + 1] - a);
+        const uint32_t t_l = lane < n ? g.adj[a + lane] : 0u;
+        for (int base = 0; base < n * Q16; base += 32) {  // same trip count on every lane
+            const int idx = base + lane;
+            const bool valid = idx < n * Q16;
+            const int u = valid ? idx / Q16 : 0, off = idx - u * Q16;
+            const uint32_t t = __shfl_sync(0xffffffffu, t_l, u);
+            const uint32_t e = t / NLN;
+            const uint32_t kr = t - e * NLN;
+            if (valid)
+                cp_async16(stage0 + st * STAGE + u * CHK + 2 * off, K + (int64_t)e * NN + (int64_t)kr * CHK + 2 * off);
+        }
+        cp_async_commit();
+        return n;
+    };
+    auto add = [&](uint32_t t, const double *src, bool from_global, int64_t RL) {
+        const uint32_t e = t / NLN;
+        const int kr = (int)(t - e * NLN);
+        int64_t rp = 0;
+        int nr = 0;
+        uint32_t m = 0;
+        if (CRAC) {
+            if (g.uniform_R) {
+                nr = g.uniform_R;
+                rp = (int64_t)e * nr;
+            } else {
+                rp = g.run_ptr[e];
+                nr = (int)(g.run_ptr[e + 1] - rp);
+                m = g.run_mask[e];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < IT; ++j) {
+            const int q = lane + 32 * j;
+            if (q < CHK) {
+                const int kc = c_[j] / BB;
+                int pos;
+                if (!CRAC) {
+                    pos = (int)map[(int64_t)t * NLN + kc];
+                } else {
+                    int k = ku[j], off = offu[j];
+                    if (!g.uniform_R) run_of(m, kc, k, off);
+                    pos = (int)mapc[rp * NLN + (int64_t)kr * nr + k] + off;
+                }
+                const double x = from_global ? __ldcs(src + q) : src[q];
+                acc[jr_[j] * (int)RL + BB * pos + c_[j] % BB] += x;
+            }
+        }
+        __syncwarp();
+    };
+    int64_t v = fe_warp_id();
+    int st = 0;
+    int n_cur = v < n_nodes ? issue(v, 0) : 0;
+    while (v < n_nodes) {
+        const int64_t vn = v + fe_warps();
+        const int n_next = vn < n_nodes ? issue(vn, st ^ 1) : (cp_async_commit(), 0);
+        const int64_t i0 = (int64_t)BB * v;
+        int64_t rb, RL;
+        if (!CRAC) {
+            rb = g.row_ptr[i0];
+            RL = g.row_ptr[i0 + 1] - rb;
+        } else {
+            rb = crac_row_base(g, i0);
+            RL = crac_row_base(g, i0 + 1) - rb;
+        }
+        const int total = (int)(BB * RL);
+        for (int k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
+        const int64_t a = g.adj_ptr[v], b = g.adj_ptr[v + 1];
+        const uint32_t t_l = lane < n_cur ? g.adj[a + lane] : 0u;
+        cp_async_wait<1>();  // this row's group has landed; the next row's may still fly
+        __syncwarp();
+        const double *stg = stage0 + st * STAGE;
+        for (int u = 0; u < n_cur; ++u) add(__shfl_sync(0xffffffffu, t_l, u), stg + u * CHK, false, RL);
+        for (int64_t s = a + n_cur; s < b; ++s) {
+            const uint32_t t = g.adj[s];
+            const uint32_t e = t / NLN;
+            const uint32_t kr = t - e * NLN;
+            add(t, K + (int64_t)e * NN + (int64_t)kr * CHK, true, RL);
+        }
+        for (int k = lane; k < total; k += 32) values[rb + k] = acc[k];
+        __syncwarp();
+        v = vn;
+        st ^= 1;
+        n_cur = n_next;
+    }
+    cp_async_wait<0>();
+}
+
+__host__ __device__ inline size_t atomic_warp_bytes(int nn, int nloc, int nln)
+{
+    const size_t b = (size_t)2 * nn * 8 + (size_t)nloc * 8 + (size_t)nln * nln * 4 + 2 * (size_t)nln * 4 + 24;
+    return (b + 127) & ~(size_t)127;
+}
+
+// One warp per element; the element's whole K (NN doubles, contiguous) is one
+// bulk copy.  Row starts and block positions are tabulated per element in
+// shared memory, then every entry is one atomic add.
+template <int NLN, int BB, typename MT, bool CRAC>
+__global__ void __launch_bounds__(128) k_atomic_tma(const double *__restrict__ K, int64_t n_e, Geo g,
+                                                    const MT *__restrict__ map, const MT *__restrict__ mapc,
+                                                    double *values, int *status)
+{
+    constexpr int NLOC = NLN * BB;
+    constexpr int NN = NLOC * NLOC;
+    constexpr int IT = (NN + 31) / 32;
+    constexpr uint32_t NNB = NN * 8;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    unsigned char *wbase = smem_raw + (size_t)(threadIdx.x >> 5) * atomic_warp_bytes(NN, NLOC, NLN);
+    double *stage0 = (double *)wbase;
+    int64_t *base_s = (int64_t *)(stage0 + 2 * NN);
+    int32_t *pos_s = (int32_t *)(base_s + NLOC);    // [NLN*NLN] block positions (CRAC: run starts)
+    int32_t *kk_s = pos_s + NLN * NLN;              // CRAC: run index per column block
+    int32_t *off_s = kk_s + NLN;                    // CRAC: offset inside the run
+    uint64_t *bar = (uint64_t *)(((uintptr_t)(off_s + NLN) + 7) & ~(uintptr_t)7);
+    if (lane == 0) {
+        fe_mbar_init(&bar[0], 1);
+        fe_mbar_init(&bar[1], 1);
+        fe_fence_mbar_init();
+    }
+    __syncwarp();
+    const uint64_t pol = fe_policy_evict_first();
+    auto issue = [&](int64_t e, int st) {
+        if (lane == 0) {
+            fe_fence_proxy_async();
+            fe_mbar_expect_tx(&bar[st], NNB);
+            fe_bulk_g2s(stage0 + st * NN, K + e * NN, NNB, &bar[st], pol);
+        }
+    };
+    int64_t e = fe_warp_id();
+    int st = 0;
+    uint32_t phase = 0;
+    if (e < n_e) issue(e, 0);
+    bool ok = true, next_issued = false;
+    while (e < n_e) {
+        const int64_t en = e + fe_warps();
+        next_issued = en < n_e;
+        if (next_issued) issue(en, st ^ 1);
+        // per-element tables
+        if (lane < NLOC) {
+            const int64_t row = (int64_t)BB * g.N[e * NLN + lane / BB] + lane % BB;
+            base_s[lane] = CRAC ? crac_row_base(g, row) : g.row_ptr[row];
+        }
+        if (!CRAC) {
+            for (int q = lane; q < NLN * NLN; q += 32) pos_s[q] = (int)map[e * NLN * NLN + q];
+        } else {
+            int64_t rp;
+            int nr;
+            if (g.uniform_R) {
+                nr = g.uniform_R;
+                rp = e * nr;
+            } else {
+                rp = g.run_ptr[e];
+                nr = (int)(g.run_ptr[e + 1] - rp);
+            }
+            const uint32_t m = g.uniform_R ? g.run_mask[0] : g.run_mask[e];
+            for (int q = lane; q < NLN * nr; q += 32) pos_s[q] = (int)mapc[rp * NLN + q];
+            if (lane < NLN) {
+                int k, off;
+                run_of(m, lane, k, off);
+                kk_s[lane] = k | (nr << 16);  // run index, and the run count as the table's row stride
+                off_s[lane] = off;
+            }
+        }
+        bool got = fe_mbar_wait(&bar[st], (phase >> st) & 1u);
+        got = __all_sync(0xffffffffu, got);
+        phase ^= 1u << st;
+        if (!got) {
+            ok = false;
+            break;
+        }
+        __syncwarp();
+        const double *stg = stage0 + st * NN;
+#pragma unroll 6
+        for (int j = 0; j < IT; ++j) {
+            const int q = lane + 32 * j;
+            if (q < NN) {
+                const int r = q / NLOC, c = q % NLOC;
+                const int kc = c / BB;
+                int pos;
+                if (!CRAC) {
+                    pos = pos_s[(r / BB) * NLN + kc];
+                } else {
+                    const int kw = kk_s[kc];
+                    pos = pos_s[(r / BB) * (kw >> 16) + (kw & 0xffff)] + off_s[kc];
+                }
+                atomicAdd(values + base_s[r] + BB * pos + c % BB, stg[q]);
+            }
+        }
+        __syncwarp();
+        e = en;
+        st ^= 1;
+    }
+    if (!ok) {
+        if (lane == 0) atomicCAS(status, 0, FE_ERR_TIMEOUT);
+        fe_mbar_wait(&bar[st], (phase >> st) & 1u);
+        if (next_issued) fe_mbar_wait(&bar[st ^ 1], (phase >> (st ^ 1)) & 1u);
+    }
+}
+
 template <typename KernelT>
 int configure_smem(KernelT kernel, size_t bytes)
 {
@@ -340,14 +598,45 @@ Geo geo_of(const fe_pattern *p)
                p->run_ptr,   p->adj_ptr, p->adj,      p->uniform_runs ? p->runs_per_elem : 0, p->mask_words};
 }
 
+template <typename KernelT>
+int grid_by_occupancy(KernelT kernel, int threads, size_t smem, int sms, int64_t warps_needed, int *grid)
+{
+    int per_sm = 0;
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
+    if (per_sm < 1) return FE_ERR_UNSUPPORTED;
+    const int64_t wpb = threads / 32;
+    *grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, (warps_needed + wpb - 1) / wpb));
+    return FE_OK;
+}
+
+// K slices are moved by bulk copies when their addresses are 16-byte aligned.
+inline bool tma_ok(const fe_pattern *p, const double *K, int chk_doubles)
+{
+    const int64_t nn = (int64_t)p->n_loc * p->n_loc;
+    return ((uintptr_t)K & 15u) == 0 && (nn * 8) % 16 == 0 && ((int64_t)chk_doubles * 8) % 16 == 0;
+}
+
 template <int NLN, int BB, typename MT, bool CRAC>
 int launch_atomic(const fe_pattern *p, const double *K, double *values, cudaStream_t s)
 {
     const Geo g = geo_of(p);
     const int sms = p->ctx->num_sms;
     if constexpr (NLN > 0) {
-        k_atomic_elem<NLN, BB, MT, CRAC><<<fe_grid_for(p->n_e * 32, 256, sms, 8), 256, 0, s>>>(
-            K, p->n_e, g, (const MT *)p->map_csr, (const MT *)p->map_crac, values);
+        constexpr int NLOC = NLN * BB;
+        if (p->ctx->knob[FE_KNOB_ATOMIC_KERNEL] != 1 && tma_ok(p, K, NLOC * NLOC)) {
+            const int W = (p->ctx->knob[FE_KNOB_ATOMIC_WARPS] > 0 && p->ctx->knob[FE_KNOB_ATOMIC_WARPS] <= 4)
+                              ? p->ctx->knob[FE_KNOB_ATOMIC_WARPS]
+                              : 4;  // launch bound: 128 threads
+            const size_t smem = W * atomic_warp_bytes(NLOC * NLOC, NLOC, NLN);
+            FE_TRY(configure_smem(k_atomic_tma<NLN, BB, MT, CRAC>, smem));
+            int grid;
+            FE_TRY(grid_by_occupancy(k_atomic_tma<NLN, BB, MT, CRAC>, W * 32, smem, sms, p->n_e, &grid));
+            k_atomic_tma<NLN, BB, MT, CRAC><<<grid, W * 32, smem, s>>>(
+                K, p->n_e, g, (const MT *)p->map_csr, (const MT *)p->map_crac, values, p->ctx->d_status);
+        } else {
+            k_atomic_elem<NLN, BB, MT, CRAC><<<fe_grid_for(p->n_e * 32, 256, sms, 8), 256, 0, s>>>(
+                K, p->n_e, g, (const MT *)p->map_csr, (const MT *)p->map_crac, values);
+        }
     } else {
         k_atomic_generic<MT, CRAC><<<fe_grid_for(p->n_e * 32, 256, sms, 8), 256, 0, s>>>(
             K, p->n_e, p->nln, p->B, g, (const MT *)p->map_csr, (const MT *)p->map_crac, values);
@@ -361,17 +650,43 @@ template <int NLN, int BB, typename MT, bool CRAC>
 int launch_gather(const fe_pattern *p, const double *K, double *values, int accumulate, cudaStream_t s)
 {
     const Geo g = geo_of(p);
-    const int sms = p->ctx->num_sms;
+    const fe_ctx *ctx = p->ctx;
+    const int sms = ctx->num_sms;
     const int cap = std::max(1, p->B * p->max_row_len);
-    int W = 8;
+    const int kind = ctx->knob[FE_KNOB_GATHER_KERNEL];
+    int W = ctx->knob[FE_KNOB_GATHER_WARPS];
+    if constexpr (NLN > 0) {
+        constexpr int CHK = BB * NLN * BB;
+        if (kind == 2 && tma_ok(p, K, CHK)) {
+            if (W <= 0 || W > 4) W = 4;  // launch bound of the staged kernel: 128 threads
+            const size_t tsmem = (size_t)W * gather_warp_bytes(CHK, cap);
+            if (tsmem <= 200 * 1024) {
+                FE_TRY(configure_smem(k_gather_async<NLN, BB, MT, CRAC>, tsmem));
+                int tgrid;
+                FE_TRY(grid_by_occupancy(k_gather_async<NLN, BB, MT, CRAC>, W * 32, tsmem, sms, p->n_nodes, &tgrid));
+                k_gather_async<NLN, BB, MT, CRAC><<<tgrid, W * 32, tsmem, s>>>(
+                    K, p->n_nodes, g, (const MT *)p->map_csr, (const MT *)p->map_crac, cap, accumulate, values);
+                fe_note_launch();
+                FE_CUDA(cudaGetLastError());
+                return FE_OK;
+            }
+        }
+    }
+    if (W <= 0) W = 8;
     while (W > 1 && (size_t)W * cap * 8 > 64 * 1024) W >>= 1;
     const size_t smem = (size_t)W * cap * 8;
     if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
     const int grid = fe_grid_for(p->n_nodes * 32, W * 32, sms, std::max(1, 64 / W));
     if constexpr (NLN > 0) {
-        FE_TRY(configure_smem(k_gather_node<NLN, BB, MT, CRAC>, smem));
-        k_gather_node<NLN, BB, MT, CRAC><<<grid, W * 32, smem, s>>>(
-            K, p->n_nodes, g, (const MT *)p->map_csr, (const MT *)p->map_crac, cap, accumulate, values);
+        if (ctx->knob[FE_KNOB_GATHER_BATCH] == 8) {
+            FE_TRY(configure_smem(k_gather_node<NLN, BB, MT, CRAC, 8>, smem));
+            k_gather_node<NLN, BB, MT, CRAC, 8><<<grid, W * 32, smem, s>>>(
+                K, p->n_nodes, g, (const MT *)p->map_csr, (const MT *)p->map_crac, cap, accumulate, values);
+        } else {
+            FE_TRY(configure_smem(k_gather_node<NLN, BB, MT, CRAC, 4>, smem));
+            k_gather_node<NLN, BB, MT, CRAC, 4><<<grid, W * 32, smem, s>>>(
+                K, p->n_nodes, g, (const MT *)p->map_csr, (const MT *)p->map_crac, cap, accumulate, values);
+        }
     } else {
         FE_TRY(configure_smem(k_gather_generic<MT, CRAC>, smem));
         k_gather_generic<MT, CRAC><<<grid, W * 32, smem, s>>>(K, p->n_nodes, p->nln, p->B, g,

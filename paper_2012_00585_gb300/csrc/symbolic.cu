@@ -17,6 +17,7 @@
 //      local node, run) the position of the run's first node, found by the
 //      linear block search of Listing 1 over the row's CRAC pairs.
 #include <climits>
+#include <utility>
 
 #include "internal.cuh"
 
@@ -40,32 +41,64 @@ __device__ __forceinline__ unsigned lanemask_lt()
 }
 
 // ---------------------------------------------------------------- A1 ---
-// One warp per element: DOF range, repeated DOFs, and the set of block sizes
-// b (bit b-1) for which the element lists whole aligned blocks.
-__global__ void k_validate(const int32_t *__restrict__ D, int64_t n_e, int32_t n_loc, int64_t n_dofs, int64_t *sc)
+// Block-size test for one compile-time b: every aligned group of b local
+// DOFs must be b consecutive indices starting at a multiple of b.
+template <int b>
+__device__ __forceinline__ void block_test(uint32_t cand, int c, int32_t d, bool is_start, bool valid, uint32_t &ok)
 {
+    if (cand & (1u << (b - 1))) {
+        const bool good = (c % b == 0) ? ((uint32_t)d % b == 0) : !is_start;
+        if (valid && !good) ok &= ~(1u << (b - 1));
+    }
+}
+
+template <int... Bs>
+__device__ __forceinline__ void block_tests(uint32_t cand, int c, int32_t d, bool is_start, bool valid, uint32_t &ok,
+                                            std::integer_sequence<int, Bs...>)
+{
+    (block_test<Bs + 2>(cand, c, d, is_start, valid, ok), ...);
+}
+
+// One warp per element: DOF range, repeated DOFs (by warp shuffles), and the
+// candidate block sizes b (bit b-1 of `cand`, the divisors of n_loc) for
+// which the element lists whole aligned blocks.
+__global__ void k_validate(const int32_t *__restrict__ D, int64_t n_e, int32_t n_loc, int64_t n_dofs, uint32_t cand,
+                           int64_t *sc)
+{
+    constexpr int MAXW = FE_MAX_NLOC / 32;
     const int lane = threadIdx.x & 31;
     uint32_t blocks_all = 0xffffffffu;
     bool bad_range = false, dup = false;
+    const int nw = (n_loc + 31) / 32;
     for (int64_t e = fe_warp_id(); e < n_e; e += fe_warps()) {
         const int32_t *De = D + e * n_loc;
+        int32_t dv[MAXW];
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w) {
+            const int c = 32 * w + lane;
+            dv[w] = (w < nw && c < n_loc) ? De[c] : INT32_MIN + w;
+        }
         uint32_t ok = 0xffffffffu;
-        for (int c0 = 0; c0 < n_loc; c0 += 32) {
-            const int c = c0 + lane;
-            if (c >= n_loc) continue;
-            const int32_t d = De[c];
-            const int32_t prev = c > 0 ? De[c - 1] : 0;
-            if (d < 0 || (int64_t)d >= n_dofs) bad_range = true;
-            for (int k = 0; k < c; ++k)
-                if (De[k] == d) {
-                    dup = true;
-                    break;
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w) {
+            if (w >= nw) break;
+            const int c = 32 * w + lane;
+            const bool valid = c < n_loc;
+            const int32_t d = dv[w];
+            if (valid && (d < 0 || (int64_t)d >= n_dofs)) bad_range = true;
+            // repeats: compare with every earlier local DOF
+#pragma unroll
+            for (int w2 = 0; w2 <= w; ++w2) {
+                for (int k = 0; k < 32; ++k) {
+                    const int32_t o = __shfl_sync(0xffffffffu, dv[w2], k);
+                    if (valid && 32 * w2 + k < c && o == d) dup = true;
                 }
-            for (int b = 2; b <= 32; ++b) {
-                const bool fits = (n_loc % b) == 0;
-                const bool good = (c % b == 0) ? (d % b == 0) : ((int64_t)d == (int64_t)prev + 1);
-                if (!fits || !good) ok &= ~(1u << (b - 1));
             }
+            int32_t prev = __shfl_up_sync(0xffffffffu, d, 1);
+            const int32_t last_prev_word = w > 0 ? __shfl_sync(0xffffffffu, dv[w > 0 ? w - 1 : 0], 31) : 0;
+            if (lane == 0) prev = last_prev_word;
+            const bool is_start = c == 0 || (int64_t)d != (int64_t)prev + 1;
+            block_tests(cand, c, d, is_start, valid, ok, std::make_integer_sequence<int, 31>{});
         }
         blocks_all &= ok;
     }
@@ -206,107 +239,74 @@ __device__ void warp_sort_smem(int32_t *buf, int n, int lane)
     }
 }
 
-struct RowOut {
-    // pass 1
-    int32_t *node_len;
-    int32_t *row_len;   // DOF level
-    int32_t *row_runs2; // DOF level, 2 * runs
-    // pass 2
-    const int64_t *node_row_ptr;
-    const int64_t *row_ptr;
-    const int64_t *crac_ptr;
-    int32_t *node_col;
-    int32_t *col_idx;
-    int32_t *col_align;
-};
-
-// Emit one kept key (node column m at rank rho; run rank rr if it starts a run).
-__device__ __forceinline__ void emit_pass2(const RowOut &o, int64_t v, int B, int32_t m, int rho, bool rs, int rr,
-                                           int64_t nbase)
+// One warp per node row v: gather the block ids of every element touching
+// v, sort (V keys per lane), keep the distinct ones.  Writes the row's
+// length L_v, 2 * (its runs of consecutive blocks) and the sorted distinct
+// blocks at keys + adj_ptr[v]*nln (the row's candidate range, an upper bound).
+template <int V>
+__global__ void __launch_bounds__(256) k_row_keys(const int32_t *__restrict__ N, int32_t nln, int64_t n_nodes,
+                                                  const int64_t *__restrict__ adj_ptr,
+                                                  const uint32_t *__restrict__ adj, int32_t *__restrict__ node_len,
+                                                  int32_t *__restrict__ node_runs2, int32_t *__restrict__ keys,
+                                                  int64_t *sc)
 {
-    o.node_col[nbase + rho] = m;
-    for (int j = 0; j < B; ++j) {
-        const int64_t i = (int64_t)B * v + j;
-        const int64_t rb = o.row_ptr[i];
-        for (int jj = 0; jj < B; ++jj) o.col_idx[rb + (int64_t)B * rho + jj] = B * m + jj;
-        if (rs && o.col_align) {
-            const int64_t cb = o.crac_ptr[i];
-            o.col_align[cb + 2 * rr] = B * m;
-            o.col_align[cb + 2 * rr + 1] = (int32_t)(rb + (int64_t)B * rho);
-        }
-    }
-}
-
-template <int PASS, int V>
-__device__ __forceinline__ void row_from_regs(const int32_t *__restrict__ N, int nln, const uint32_t *__restrict__ adj,
-                                              int64_t a, int n, int64_t v, int B, const RowOut &o, int64_t *sc,
-                                              int lane)
-{
-    int32_t x[V];
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-        const int g = lane * V + q;
-        x[q] = PAD;
-        if (g < n) {
-            const int s = g / nln;
-            const int c = g - s * nln;
-            const uint32_t t = adj[a + s];
-            x[q] = N[(int64_t)(t / (uint32_t)nln) * nln + c];
-        }
-    }
-    warp_sort_regs<V>(x, lane);
-    const int32_t up = __shfl_up_sync(0xffffffffu, x[V - 1], 1);
-    bool keep[V], rs[V];
-    int nk = 0, nrs = 0;
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-        const int g = lane * V + q;
-        const int32_t pv = q > 0 ? x[q - 1] : up;
-        keep[q] = g < n && (g == 0 || x[q] != pv);
-        rs[q] = keep[q] && (g == 0 || (int64_t)pv != (int64_t)x[q] - 1);
-        nk += keep[q];
-        nrs += rs[q];
-    }
-    int ik = nk, ir = nrs;  // inclusive warp scans
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int tk = __shfl_up_sync(0xffffffffu, ik, off);
-        const int tr = __shfl_up_sync(0xffffffffu, ir, off);
-        if (lane >= off) {
-            ik += tk;
-            ir += tr;
-        }
-    }
-    const int L = __shfl_sync(0xffffffffu, ik, 31);
-    const int R = __shfl_sync(0xffffffffu, ir, 31);
-    if (PASS == 1) {
-        if (lane == 0) {
-            o.node_len[v] = L;
-            atomicMax((long long *)&sc[S_MAX_NODE], (long long)L);
-        }
-        for (int j = lane; j < B; j += 32) {
-            o.row_len[(int64_t)B * v + j] = B * L;
-            o.row_runs2[(int64_t)B * v + j] = 2 * R;
-        }
-    } else {
-        int rho = ik - nk, rr = ir - nrs;
-        const int64_t nbase = o.node_row_ptr[v];
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
+        const int64_t a = adj_ptr[v];
+        const int n = (int)(adj_ptr[v + 1] - a) * nln;
+        int32_t x[V];
 #pragma unroll
         for (int q = 0; q < V; ++q) {
-            if (keep[q]) {
-                emit_pass2(o, v, B, x[q], rho, rs[q], rr, nbase);
-                ++rho;
-                rr += rs[q];
+            const int g = lane * V + q;
+            x[q] = PAD;
+            if (g < n) {
+                const int s = g / nln;
+                const int c = g - s * nln;
+                const uint32_t t = adj[a + s];
+                x[q] = N[(int64_t)(t / (uint32_t)nln) * nln + c];
             }
+        }
+        warp_sort_regs<V>(x, lane);
+        const int32_t up = __shfl_up_sync(0xffffffffu, x[V - 1], 1);
+        bool keep[V];
+        int nk = 0, nrs = 0;
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int g = lane * V + q;
+            const int32_t pv = q > 0 ? x[q - 1] : up;
+            keep[q] = g < n && (g == 0 || x[q] != pv);
+            nk += keep[q];
+            nrs += keep[q] && (g == 0 || (int64_t)pv != (int64_t)x[q] - 1);
+        }
+        int ik = nk, ir = nrs;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int tk = __shfl_up_sync(0xffffffffu, ik, off);
+            const int tr = __shfl_up_sync(0xffffffffu, ir, off);
+            if (lane >= off) {
+                ik += tk;
+                ir += tr;
+            }
+        }
+        int rho = ik - nk;
+        int32_t *kv = keys + a * nln;
+#pragma unroll
+        for (int q = 0; q < V; ++q)
+            if (keep[q]) kv[rho++] = x[q];
+        if (lane == 31) {
+            node_len[v] = ik;
+            node_runs2[v] = 2 * ir;
+            atomicMax((long long *)&sc[S_MAX_NODE], (long long)ik);
         }
     }
 }
 
-// One warp per node row v.
-template <int PASS>
-__global__ void k_node_rows(const int32_t *__restrict__ N, int32_t nln, int64_t n_nodes, int32_t B,
-                            const int64_t *__restrict__ adj_ptr, const uint32_t *__restrict__ adj, int P, RowOut o,
-                            int64_t *sc)
+// Rows with more than 256 candidates: the same with a bitonic sort in shared
+// memory (P keys per warp).
+__global__ void k_row_keys_smem(const int32_t *__restrict__ N, int32_t nln, int64_t n_nodes,
+                                const int64_t *__restrict__ adj_ptr, const uint32_t *__restrict__ adj, int P,
+                                int32_t *__restrict__ node_len, int32_t *__restrict__ node_runs2,
+                                int32_t *__restrict__ keys, int64_t *sc)
 {
     extern __shared__ int32_t sbuf[];
     const int lane = threadIdx.x & 31;
@@ -314,57 +314,98 @@ __global__ void k_node_rows(const int32_t *__restrict__ N, int32_t nln, int64_t 
     for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
         const int64_t a = adj_ptr[v];
         const int n = (int)(adj_ptr[v + 1] - a) * nln;
-        if (n <= 32) {
-            row_from_regs<PASS, 1>(N, nln, adj, a, n, v, B, o, sc, lane);
-        } else if (n <= 64) {
-            row_from_regs<PASS, 2>(N, nln, adj, a, n, v, B, o, sc, lane);
-        } else if (n <= 128) {
-            row_from_regs<PASS, 4>(N, nln, adj, a, n, v, B, o, sc, lane);
-        } else if (n <= REG_SORT_MAX) {
-            row_from_regs<PASS, 8>(N, nln, adj, a, n, v, B, o, sc, lane);
-        } else {
-            int Pn = 32;
-            while (Pn < n) Pn <<= 1;
-            for (int k = lane; k < Pn; k += 32) {
-                int32_t x = PAD;
-                if (k < n) {
-                    const int s = k / nln;
-                    const int c = k - s * nln;
-                    const uint32_t t = adj[a + s];
-                    x = N[(int64_t)(t / (uint32_t)nln) * nln + c];
-                }
-                buf[k] = x;
+        int Pn = 32;
+        while (Pn < n) Pn <<= 1;
+        for (int k = lane; k < Pn; k += 32) {
+            int32_t x = PAD;
+            if (k < n) {
+                const int s = k / nln;
+                const int c = k - s * nln;
+                const uint32_t t = adj[a + s];
+                x = N[(int64_t)(t / (uint32_t)nln) * nln + c];
             }
-            __syncwarp();
-            warp_sort_smem(buf, Pn, lane);
-            int L = 0, R = 0;
-            const int64_t nbase = PASS == 2 ? o.node_row_ptr[v] : 0;
-            for (int k0 = 0; k0 < n; k0 += 32) {
-                const int k = k0 + lane;
-                const int32_t x = k < n ? buf[k] : PAD;
-                const int32_t pv = (k > 0 && k < n) ? buf[k - 1] : PAD;
-                const bool keep = k < n && (k == 0 || x != pv);
-                const bool rs = keep && (k == 0 || (int64_t)pv != (int64_t)x - 1);
-                const unsigned mk = __ballot_sync(0xffffffffu, keep);
-                const unsigned mr = __ballot_sync(0xffffffffu, rs);
-                if (PASS == 2 && keep)
-                    emit_pass2(o, v, B, x, L + __popc(mk & lanemask_lt()), rs, R + __popc(mr & lanemask_lt()), nbase);
-                L += __popc(mk);
-                R += __popc(mr);
+            buf[k] = x;
+        }
+        __syncwarp();
+        warp_sort_smem(buf, Pn, lane);
+        int L = 0, R = 0;
+        int32_t *kv = keys + a * nln;
+        for (int k0 = 0; k0 < n; k0 += 32) {
+            const int k = k0 + lane;
+            const int32_t x = k < n ? buf[k] : PAD;
+            const int32_t pv = (k > 0 && k < n) ? buf[k - 1] : PAD;
+            const bool keep = k < n && (k == 0 || x != pv);
+            const bool rs = keep && (k == 0 || (int64_t)pv != (int64_t)x - 1);
+            const unsigned mk = __ballot_sync(0xffffffffu, keep);
+            const unsigned mr = __ballot_sync(0xffffffffu, rs);
+            if (keep) kv[L + __popc(mk & lanemask_lt())] = x;
+            L += __popc(mk);
+            R += __popc(mr);
+        }
+        if (lane == 0) {
+            node_len[v] = L;
+            node_runs2[v] = 2 * R;
+            atomicMax((long long *)&sc[S_MAX_NODE], (long long)L);
+        }
+        __syncwarp();
+    }
+}
+
+// One warp per node row v: the B DOF rows B*v+j get
+//   row_ptr  = B^2 * nrp[v] + j*B*L_v,   col_idx = B*key + comp (coalesced),
+//   crac_ptr = B * ncp[v] + j*2*R_v,     pairs (B*first key of a run, value position)
+// where nrp / ncp are the node-level scans of L and 2R.
+__global__ void __launch_bounds__(256) k_expand(int64_t n_nodes, int32_t B, int32_t nln,
+                                                const int64_t *__restrict__ adj_ptr,
+                                                const int32_t *__restrict__ keys, const int32_t *__restrict__ node_len,
+                                                const int32_t *__restrict__ node_runs2,
+                                                const int64_t *__restrict__ nrp, const int64_t *__restrict__ ncp,
+                                                int64_t *__restrict__ row_ptr, int64_t *__restrict__ crac_ptr,
+                                                int32_t *__restrict__ col_idx, int32_t *__restrict__ col_align)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
+        const int L = node_len[v];
+        const int R2 = node_runs2[v];
+        const int32_t *kv = keys + adj_ptr[v] * nln;
+        const int64_t rb0 = (int64_t)B * B * nrp[v];
+        const int64_t cb0 = (int64_t)B * ncp[v];
+        for (int j = lane; j < B; j += 32) {
+            row_ptr[(int64_t)B * v + j] = rb0 + (int64_t)j * B * L;
+            crac_ptr[(int64_t)B * v + j] = cb0 + (int64_t)j * R2;
+        }
+        for (int j = 0; j < B; ++j) {
+            const int64_t rb = rb0 + (int64_t)j * B * L;
+            for (int idx = lane; idx < B * L; idx += 32) {
+                const int rho = idx / B;
+                col_idx[rb + idx] = B * kv[rho] + (idx - rho * B);
             }
-            if (PASS == 1) {
-                if (lane == 0) {
-                    o.node_len[v] = L;
-                    atomicMax((long long *)&sc[S_MAX_NODE], (long long)L);
-                }
-                for (int j = lane; j < B; j += 32) {
-                    o.row_len[(int64_t)B * v + j] = B * L;
-                    o.row_runs2[(int64_t)B * v + j] = 2 * R;
+            if (col_align) {
+                const int64_t cb = cb0 + (int64_t)j * R2;
+                int rr = 0;
+                for (int k0 = 0; k0 < L; k0 += 32) {
+                    const int k = k0 + lane;
+                    const int32_t x = k < L ? kv[k] : 0;
+                    const int32_t pv = (k > 0 && k < L) ? kv[k - 1] : 0;
+                    const bool rs = k < L && (k == 0 || (int64_t)pv != (int64_t)x - 1);
+                    const unsigned mr = __ballot_sync(0xffffffffu, rs);
+                    if (rs) {
+                        const int r = rr + __popc(mr & lanemask_lt());
+                        col_align[cb + 2 * r] = B * x;
+                        col_align[cb + 2 * r + 1] = (int32_t)(rb + (int64_t)B * k);
+                    }
+                    rr += __popc(mr);
                 }
             }
-            __syncwarp();
         }
     }
+}
+
+__global__ void k_tail(int64_t *row_ptr, int64_t *crac_ptr, const int64_t *nrp, const int64_t *ncp, int64_t n_nodes,
+                       int64_t n_dofs, int32_t B)
+{
+    row_ptr[n_dofs] = (int64_t)B * B * nrp[n_nodes];
+    crac_ptr[n_dofs] = (int64_t)B * ncp[n_nodes];
 }
 
 __global__ void k_final_pair(int32_t *col_align, int64_t n_ca, int64_t n_dofs, int64_t nnz)
@@ -381,22 +422,22 @@ __global__ void k_final_pair(int32_t *col_align, int64_t n_ca, int64_t n_dofs, i
 template <typename MT>
 __global__ void k_map_node(const int32_t *__restrict__ N, int32_t nln, int64_t n_nodes,
                            const int64_t *__restrict__ adj_ptr, const uint32_t *__restrict__ adj,
-                           const int64_t *__restrict__ node_row_ptr, const int32_t *__restrict__ node_col, int cap,
+                           const int32_t *__restrict__ node_len, const int32_t *__restrict__ keys, int cap,
                            MT *__restrict__ map, int64_t *sc)
 {
     extern __shared__ int32_t sbuf[];
     const int lane = threadIdx.x & 31;
     int32_t *cols_s = sbuf + (size_t)(threadIdx.x >> 5) * cap;
     for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
-        const int64_t rb = node_row_ptr[v];
-        const int len = (int)(node_row_ptr[v + 1] - rb);
+        const int64_t a = adj_ptr[v], b = adj_ptr[v + 1];
+        const int len = node_len[v];
+        const int32_t *row = keys + a * nln;
         const bool in_smem = len <= cap;
-        const int32_t *cols = in_smem ? cols_s : node_col + rb;
+        const int32_t *cols = in_smem ? cols_s : row;
         if (in_smem) {
-            for (int k = lane; k < len; k += 32) cols_s[k] = node_col[rb + k];
+            for (int k = lane; k < len; k += 32) cols_s[k] = row[k];
             __syncwarp();
         }
-        const int64_t a = adj_ptr[v], b = adj_ptr[v + 1];
         // (incidence, local node) pairs of this row, spread over the lanes
         const int total = (int)(b - a) * nln;
         for (int q = lane; q < total; q += 32) {
@@ -443,34 +484,33 @@ __global__ void k_map_runs(const int32_t *__restrict__ N, int32_t nln, int64_t n
             __syncwarp();
         }
         const int32_t row_base = ca[1];
-        for (int64_t s = adj_ptr[v]; s < adj_ptr[v + 1]; ++s) {
-            const uint32_t t = adj[s];
+        const int64_t a = adj_ptr[v], b = adj_ptr[v + 1];
+        const int total = (int)(b - a) * nln;
+        for (int q = lane; q < total; q += 32) {
+            const int s = q / nln;
+            const int kc = q - s * nln;
+            const uint32_t t = adj[a + s];
             const int64_t e = t / (uint32_t)nln;
             const int k = (int)(t - (uint32_t)(e * nln));
+            const uint32_t *m = run_mask + e * mask_words;
+            if (!((m[kc >> 5] >> (kc & 31)) & 1u)) continue;  // not the first block of a run
+            int ri = __popc(m[kc >> 5] & ((1u << (kc & 31)) - 1u));
+            for (int w = 0; w < (kc >> 5); ++w) ri += __popc(m[w]);
             const int64_t rp = run_ptr[e];
             const int nr = (int)(run_ptr[e + 1] - rp);
-            int before = 0;
-            for (int c0 = 0; c0 < nln; c0 += 32) {
-                const uint32_t m = run_mask[e * mask_words + (c0 >> 5)];
-                const int kc = c0 + lane;
-                if (kc < nln && ((m >> lane) & 1u)) {
-                    const int ri = before + __popc(m & ((1u << lane) - 1u));
-                    const int32_t j = B * N[e * nln + kc];
-                    int p = 0;
-                    while (p + 2 < np) {
-                        if (ca[p + 2] > j) break;
-                        p += 2;
-                    }
-                    const int32_t col_start = ca[p];
-                    const int32_t val_start = ca[p + 1];
-                    const int32_t col_end = col_start + (ca[p + 3] - val_start);
-                    int32_t rel = 0;
-                    if (j >= col_start && j < col_end) rel = (val_start + (j - col_start) - row_base) / B;
-                    else set_err(sc, FE_ERR_DEVICE);
-                    mapc[rp * nln + (int64_t)k * nr + ri] = (MT)rel;
-                }
-                before += __popc(m);
+            const int32_t j = B * N[e * nln + kc];
+            int p = 0;
+            while (p + 2 < np) {
+                if (ca[p + 2] > j) break;
+                p += 2;
             }
+            const int32_t col_start = ca[p];
+            const int32_t val_start = ca[p + 1];
+            const int32_t col_end = col_start + (ca[p + 3] - val_start);
+            int32_t rel = 0;
+            if (j >= col_start && j < col_end) rel = (val_start + (j - col_start) - row_base) / B;
+            else set_err(sc, FE_ERR_DEVICE);
+            mapc[rp * nln + (int64_t)k * nr + ri] = (MT)rel;
         }
         __syncwarp();
     }
@@ -532,7 +572,11 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
 
     // A1: validation and block size
     if (n_e > 0) {
-        FE_LAUNCH((k_validate<<<fe_grid_for(n_e * 32, 256, sms, 16), 256, 0, s>>>(elem_dofs, n_e, n_loc, n_dofs, sc)));
+        uint32_t cand = 0;  // block sizes that divide both n_loc and n_dofs
+        for (int b = 2; b <= 32; ++b)
+            if (n_loc % b == 0 && n_dofs % b == 0) cand |= 1u << (b - 1);
+        FE_LAUNCH((k_validate<<<fe_grid_for(n_e * 32, 256, sms, 16), 256, 0, s>>>(elem_dofs, n_e, n_loc, n_dofs, cand,
+                                                                               sc)));
         FE_CUDA(cudaGetLastError());
     }
     int64_t h1[S_COUNT];
@@ -591,76 +635,73 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
     p->uniform_runs = (h2[S_NONUNIFORM] == 0) && n_e > 0;
     p->runs_per_elem = n_e > 0 ? (int32_t)(p->n_runs / n_e) : 0;
 
-    // A3 pass 1: node row lengths and runs
-    const int64_t cand = (int64_t)p->max_deg * nln;
-    int P = 0, W = 8;
-    if (cand > REG_SORT_MAX) {
-        P = 32;
-        while (P < cand) P <<= 1;
-        if ((int64_t)P * 4 > 128 * 1024) return FE_ERR_UNSUPPORTED;
-        W = (int)std::max<int64_t>(1, std::min<int64_t>(8, (64 * 1024) / ((int64_t)P * 4)));
-    }
-    const size_t smem_rows = (size_t)W * P * 4;
-    FE_TRY(configure_smem(k_node_rows<1>, smem_rows));
-    FE_TRY(configure_smem(k_node_rows<2>, smem_rows));
-    const int grid_rows = fe_grid_for(n_nodes * 32, W * 32, sms, std::max(1, 64 / W));
-    int32_t *node_len = nullptr, *row_len = nullptr, *row_runs2 = nullptr;
-    int64_t *node_row_ptr = nullptr;
+    // A3: sorted distinct blocks of every node row (kept in `keys` at the
+    // row's candidate offset adj_ptr[v]*nln), lengths and runs
+    int32_t *node_len = nullptr, *node_runs2 = nullptr, *keys = nullptr;
+    int64_t *nrp = nullptr, *ncp = nullptr;
     FE_TRY(fe_alloc(ctx, (void **)&node_len, sizeof(int32_t) * (size_t)(n_nodes + 1), s));
     tmp.add(node_len);
-    FE_TRY(fe_alloc(ctx, (void **)&row_len, sizeof(int32_t) * (size_t)(n_dofs + 1), s));
-    tmp.add(row_len);
-    FE_TRY(fe_alloc(ctx, (void **)&row_runs2, sizeof(int32_t) * (size_t)(n_dofs + 1), s));
-    tmp.add(row_runs2);
-    FE_TRY(fe_alloc(ctx, (void **)&node_row_ptr, sizeof(int64_t) * (size_t)(n_nodes + 1), s));
-    tmp.add(node_row_ptr);
-    RowOut o{};
-    o.node_len = node_len;
-    o.row_len = row_len;
-    o.row_runs2 = row_runs2;
+    FE_TRY(fe_alloc(ctx, (void **)&node_runs2, sizeof(int32_t) * (size_t)(n_nodes + 1), s));
+    tmp.add(node_runs2);
+    FE_TRY(fe_alloc(ctx, (void **)&keys, sizeof(int32_t) * (size_t)(n_ninc * nln + 1), s));
+    tmp.add(keys);
+    FE_TRY(fe_alloc(ctx, (void **)&nrp, sizeof(int64_t) * (size_t)(n_nodes + 1), s));
+    tmp.add(nrp);
+    FE_TRY(fe_alloc(ctx, (void **)&ncp, sizeof(int64_t) * (size_t)(n_nodes + 1), s));
+    tmp.add(ncp);
+    const int64_t cand = (int64_t)p->max_deg * nln;
     if (n_nodes > 0) {
-        FE_LAUNCH((k_node_rows<1><<<grid_rows, W * 32, smem_rows, s>>>(p->node_dofs, nln, n_nodes, B, p->adj_ptr,
-                                                                       p->adj, P, o, sc)));
+        const int grid = fe_grid_for(n_nodes * 32, 256, sms, 8);
+        if (cand <= 32) {
+            FE_LAUNCH((k_row_keys<1><<<grid, 256, 0, s>>>(p->node_dofs, nln, n_nodes, p->adj_ptr, p->adj, node_len,
+                                                           node_runs2, keys, sc)));
+        } else if (cand <= 64) {
+            FE_LAUNCH((k_row_keys<2><<<grid, 256, 0, s>>>(p->node_dofs, nln, n_nodes, p->adj_ptr, p->adj, node_len,
+                                                           node_runs2, keys, sc)));
+        } else if (cand <= 128) {
+            FE_LAUNCH((k_row_keys<4><<<grid, 256, 0, s>>>(p->node_dofs, nln, n_nodes, p->adj_ptr, p->adj, node_len,
+                                                           node_runs2, keys, sc)));
+        } else if (cand <= REG_SORT_MAX) {
+            FE_LAUNCH((k_row_keys<8><<<grid, 256, 0, s>>>(p->node_dofs, nln, n_nodes, p->adj_ptr, p->adj, node_len,
+                                                           node_runs2, keys, sc)));
+        } else {
+            int P = 32;
+            while (P < cand) P <<= 1;
+            if ((int64_t)P * 4 > 128 * 1024) return FE_ERR_UNSUPPORTED;
+            const int W = (int)std::max<int64_t>(1, std::min<int64_t>(8, (64 * 1024) / ((int64_t)P * 4)));
+            const size_t smem = (size_t)W * P * 4;
+            FE_TRY(configure_smem(k_row_keys_smem, smem));
+            FE_LAUNCH((k_row_keys_smem<<<fe_grid_for(n_nodes * 32, W * 32, sms, std::max(1, 64 / W)), W * 32, smem,
+                                         s>>>(p->node_dofs, nln, n_nodes, p->adj_ptr, p->adj, P, node_len, node_runs2,
+                                              keys, sc)));
+        }
         FE_CUDA(cudaGetLastError());
     }
-    FE_TRY(alloc_into(p, (void **)&p->row_ptr, sizeof(int64_t) * (size_t)(n_dofs + 1), s));
-    FE_TRY(alloc_into(p, (void **)&p->crac_ptr, sizeof(int64_t) * (size_t)(n_dofs + 1), s));
-    FE_TRY(fe_scan_i32_to_i64(ctx, node_len, node_row_ptr, n_nodes, s));
-    FE_TRY(fe_scan_i32_to_i64(ctx, row_len, p->row_ptr, n_dofs, s));
-    FE_TRY(fe_scan_i32_to_i64(ctx, row_runs2, p->crac_ptr, n_dofs, s));
-
-    int64_t h3[4];
-    FE_CUDA(cudaMemcpyAsync(&h3[0], p->row_ptr + n_dofs, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaMemcpyAsync(&h3[1], p->crac_ptr + n_dofs, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FE_TRY(fe_scan_i32_to_i64(ctx, node_len, nrp, n_nodes, s));
+    FE_TRY(fe_scan_i32_to_i64(ctx, node_runs2, ncp, n_nodes, s));
+    int64_t h3[3];
+    FE_CUDA(cudaMemcpyAsync(&h3[0], nrp + n_nodes, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaMemcpyAsync(&h3[1], ncp + n_nodes, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     FE_CUDA(cudaMemcpyAsync(&h3[2], sc + S_MAX_NODE, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaMemcpyAsync(&h3[3], node_row_ptr + n_nodes, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     FE_CUDA(cudaStreamSynchronize(s));  // sync 3: nnz, n_ca, longest row
-    p->nnz = h3[0];
-    p->n_ca = h3[1] + 2;
+    p->nnz = (int64_t)B * B * h3[0];
+    p->n_ca = (int64_t)B * h3[1] + 2;
     p->max_node_len = (int32_t)h3[2];
     p->max_row_len = B * p->max_node_len;
-    const int64_t node_nnz = h3[3];
     if (p->nnz >= INT32_MAX || p->n_ca >= INT32_MAX) return FE_ERR_OVERFLOW;
     p->map_bytes = p->max_node_len <= 256 ? 1 : 2;
     if (p->max_node_len > 65536) return FE_ERR_UNSUPPORTED;
 
-    // A3 pass 2 + CRAC pairs
-    int32_t *node_col = nullptr;
-    FE_TRY(fe_alloc(ctx, (void **)&node_col, sizeof(int32_t) * (size_t)(node_nnz + 1), s));
-    tmp.add(node_col);
+    // expansion to DOF rows: row_ptr, col_idx, CRAC row pointers and pairs
+    FE_TRY(alloc_into(p, (void **)&p->row_ptr, sizeof(int64_t) * (size_t)(n_dofs + 1), s));
+    FE_TRY(alloc_into(p, (void **)&p->crac_ptr, sizeof(int64_t) * (size_t)(n_dofs + 1), s));
     FE_TRY(alloc_into(p, (void **)&p->col_idx, sizeof(int32_t) * (size_t)(p->nnz + 1), s));
     FE_TRY(alloc_into(p, (void **)&p->col_align, sizeof(int32_t) * (size_t)p->n_ca, s));
-    o.node_row_ptr = node_row_ptr;
-    o.row_ptr = p->row_ptr;
-    o.crac_ptr = p->crac_ptr;
-    o.node_col = node_col;
-    o.col_idx = p->col_idx;
-    o.col_align = p->col_align;
-    if (n_nodes > 0) {
-        FE_LAUNCH((k_node_rows<2><<<grid_rows, W * 32, smem_rows, s>>>(p->node_dofs, nln, n_nodes, B, p->adj_ptr,
-                                                                       p->adj, P, o, sc)));
-        FE_CUDA(cudaGetLastError());
-    }
+    if (n_nodes > 0)
+        FE_LAUNCH((k_expand<<<fe_grid_for(n_nodes * 32, 256, sms, 8), 256, 0, s>>>(
+            n_nodes, B, nln, p->adj_ptr, keys, node_len, node_runs2, nrp, ncp, p->row_ptr, p->crac_ptr, p->col_idx,
+            p->col_align)));
+    FE_LAUNCH((k_tail<<<1, 1, 0, s>>>(p->row_ptr, p->crac_ptr, nrp, ncp, n_nodes, n_dofs, B)));
     FE_LAUNCH((k_final_pair<<<1, 1, 0, s>>>(p->col_align, p->n_ca, n_dofs, p->nnz)));
     FE_CUDA(cudaGetLastError());
 
@@ -674,13 +715,13 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
             if (p->map_bytes == 1) {
                 FE_TRY(configure_smem(k_map_node<uint8_t>, smem));
                 FE_LAUNCH((k_map_node<uint8_t><<<fe_grid_for(n_nodes * 32, WM * 32, sms, 8), WM * 32, smem, s>>>(
-                    p->node_dofs, nln, n_nodes, p->adj_ptr, p->adj, node_row_ptr, node_col, cap,
-                    (uint8_t *)p->map_csr, sc)));
+                    p->node_dofs, nln, n_nodes, p->adj_ptr, p->adj, node_len, keys, cap, (uint8_t *)p->map_csr,
+                    sc)));
             } else {
                 FE_TRY(configure_smem(k_map_node<uint16_t>, smem));
                 FE_LAUNCH((k_map_node<uint16_t><<<fe_grid_for(n_nodes * 32, WM * 32, sms, 8), WM * 32, smem, s>>>(
-                    p->node_dofs, nln, n_nodes, p->adj_ptr, p->adj, node_row_ptr, node_col, cap,
-                    (uint16_t *)p->map_csr, sc)));
+                    p->node_dofs, nln, n_nodes, p->adj_ptr, p->adj, node_len, keys, cap, (uint16_t *)p->map_csr,
+                    sc)));
             }
             FE_CUDA(cudaGetLastError());
         }

@@ -38,6 +38,13 @@ FE_PATTERN_ALL = 0x1F
 FE_ATOMIC = 0
 FE_DETERMINISTIC = 1
 
+FE_KNOB_GATHER_KERNEL = 0
+FE_KNOB_GATHER_BATCH = 1
+FE_KNOB_GATHER_WARPS = 2
+FE_KNOB_ATOMIC_KERNEL = 3
+FE_KNOB_ATOMIC_WARPS = 4
+FE_KNOB_COUNT = 8
+
 _lib = None
 _lock = threading.Lock()
 
@@ -93,6 +100,9 @@ def load():
             "fe_strerror": (ctypes.c_char_p, [i]),
             "fe_last_cuda_error": (ctypes.c_char_p, []),
             "fe_kernel_launches": (ctypes.c_uint64, []),
+            "fe_device_status": (i, [vp, vp]),
+            "fe_tune_set": (i, [vp, i, i]),
+            "fe_tune_get": (i, [vp, i, ctypes.POINTER(i)]),
             "fe_pattern_build": (i, [vp, i64, i32, i64, vp, u32, vp, pp]),
             "fe_pattern_free": (i, [vp]),
             "fe_pattern_csr": (i, [vp, pp, pp, ctypes.POINTER(i64)]),
@@ -148,6 +158,21 @@ def fe_last_cuda_error() -> str:
 
 def fe_kernel_launches() -> int:
     return int(load().fe_kernel_launches())
+
+
+def fe_device_status(ctx, stream=None) -> int:
+    """First error recorded by a kernel since the last call (0 = none); clears it."""
+    return int(load().fe_device_status(ctx, _stream(stream)))
+
+
+def fe_tune_set(ctx, knob: int, value: int):
+    _check(load().fe_tune_set(ctx, int(knob), int(value)), "fe_tune_set")
+
+
+def fe_tune_get(ctx, knob: int) -> int:
+    out = ctypes.c_int()
+    _check(load().fe_tune_get(ctx, int(knob), ctypes.byref(out)), "fe_tune_get")
+    return out.value
 
 
 def fe_create(device: int = 0, hbm_budget_bytes: int = 0):
