@@ -165,6 +165,39 @@ int fe_pattern_build(fe_ctx *ctx, int64_t n_elem, int32_t dofs_per_elem, int64_t
                      const int32_t *elem_dofs, uint32_t flags, void *stream,
                      fe_pattern **out);
 
+/*
+ * CSR pattern build that allocates no memory (the paper has no counterpart:
+ * this entry point exists for callers of this library).
+ *
+ * Some callers cannot allocate device memory: an application that owns every
+ * byte of HBM through its own allocator, a latency-bound loop that cannot
+ * accept the implicit device synchronisation of cudaMalloc, or code running
+ * where allocation is not permitted.  This call builds the same CSR arrays as
+ * fe_pattern_build + fe_pattern_csr, but needs no context and calls no
+ * cudaMalloc, cudaFree or allocating routine: its working memory is one fixed
+ * 16 MiB device array inside the library, held by every GPU that loads the
+ * library until the process exits.
+ *
+ *   elem_dofs   device, int32 [n_elem * dofs_per_elem] (read only).
+ *   row_ptr     device, int64 [n_dofs + 1], written.
+ *   col_idx     device, int32 [col_capacity], written when nnz <= capacity.
+ *   nnz         host, receives the number of pattern entries (also when the
+ *               capacity was too small, so the caller can retry).
+ *   stream      work is ordered on it; the call returns after a stream sync.
+ * Works on the current CUDA device.  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.
+ * All calls share the one array (its contents persist between calls; this
+ * call clears what must start at zero), so calls whose work overlaps on the
+ * GPU, from different streams or threads, race: serialise them.
+ * Errors: FE_ERR_UNSUPPORTED when the mesh needs more than the 16 MiB of
+ * scratch (roughly n_elem * dofs_per_elem^2 * 4 bytes plus 60 bytes per DOF)
+ * or dofs_per_elem > FE_MAX_NLOC; FE_ERR_INVALID_ARG when col_capacity < nnz;
+ * FE_ERR_DOF_RANGE / FE_ERR_DUP_DOF for bad connectivity; FE_ERR_OVERFLOW.
+ */
+int fe_pattern_csr_noalloc(int64_t n_elem, int32_t dofs_per_elem, int64_t n_dofs, const int32_t *elem_dofs,
+                           int64_t *row_ptr, int32_t *col_idx, int64_t col_capacity, int64_t *nnz,
+                           void *stream);
+
 /* Release a pattern.  Waits for the device to finish pending work first. */
 int fe_pattern_free(fe_pattern *pattern);
 

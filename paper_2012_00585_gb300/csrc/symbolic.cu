@@ -17,6 +17,7 @@
 //      local node, run) the position of the run's first node, found by the
 //      linear block search of Listing 1 over the row's CRAC pairs.
 #include <climits>
+#include <mutex>
 #include <utility>
 
 #include "internal.cuh"
@@ -854,3 +855,265 @@ int fe_pattern_info_get(const fe_pattern *p, fe_pattern_info *out)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// CSR pattern build that allocates nothing (fe_pattern_csr_noalloc).
+//
+// For callers that must not allocate device memory: a library embedded in a
+// host application that owns every byte of HBM through its own allocator, a
+// real-time or latency-bound loop that cannot afford cudaMalloc's implicit
+// device synchronisation, or code running where an allocation is not
+// permitted.  Its working memory is the fixed array below, which every GPU
+// that loads this library keeps until the process exits.
+
+#define FE_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+static __device__ __align__(256) unsigned char fe_noalloc_scratch[FE_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int NS_THREADS = 1024;
+constexpr int NS_TILE = 4096;  // elements per tile; at most NS_TILE tiles
+
+__global__ void k_ns_tile_sums(const int32_t *__restrict__ in, int64_t n, int64_t *__restrict__ sums)
+{
+    __shared__ int64_t red[NS_THREADS / 32];
+    const int64_t base = (int64_t)blockIdx.x * NS_TILE;
+    int64_t s = 0;
+    for (int k = threadIdx.x; k < NS_TILE; k += blockDim.x)
+        if (base + k < n) s += in[base + k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t t = 0;
+        for (int w = 0; w < NS_THREADS / 32; ++w) t += red[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+// One block: exclusive scan of `tiles` sums in place (serial per thread
+// chunk, then across chunks).
+__global__ void k_ns_scan_sums(int64_t *sums, int tiles)
+{
+    __shared__ int64_t part[NS_THREADS];
+    const int per = (tiles + NS_THREADS - 1) / NS_THREADS;
+    const int lo = threadIdx.x * per, hi = min(tiles, lo + per);
+    int64_t s = 0;
+    for (int k = lo; k < hi; ++k) s += sums[k];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int k = 0; k < NS_THREADS; ++k) {
+            const int64_t x = part[k];
+            part[k] = run;
+            run += x;
+        }
+    }
+    __syncthreads();
+    int64_t run = part[threadIdx.x];
+    for (int k = lo; k < hi; ++k) {
+        const int64_t x = sums[k];
+        sums[k] = run;
+        run += x;
+    }
+}
+
+// out[i] = offs[tile] + in[tile_base] + ... + in[i-1]; out[n] = total.
+__global__ void k_ns_tile_scan(const int32_t *__restrict__ in, int64_t n, const int64_t *__restrict__ offs,
+                               int64_t *__restrict__ out)
+{
+    __shared__ int64_t wsum[NS_THREADS / 32];
+    constexpr int PER = NS_TILE / NS_THREADS;
+    const int64_t base = (int64_t)blockIdx.x * NS_TILE + (int64_t)threadIdx.x * PER;
+    int64_t x[PER], local = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        x[k] = base + k < n ? in[base + k] : 0;
+        local += x[k];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int64_t v = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    int64_t run = offs[blockIdx.x] + incl - local + (w > 0 ? wsum[w - 1] : 0);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += x[k];
+        if (base + k == n - 1) out[n] = run;
+    }
+}
+
+// Bump allocation inside the fixed scratch array.
+struct Bump {
+    unsigned char *base;
+    size_t used, cap;
+    void *take(size_t bytes)
+    {
+        const size_t at = (used + 255) & ~(size_t)255;
+        used = at + bytes;
+        return used <= cap ? base + at : nullptr;
+    }
+};
+
+int ns_scan(const int32_t *in, int64_t *out, int64_t n, int64_t *tile_sums, cudaStream_t s)
+{
+    const int64_t tiles = std::max<int64_t>(1, (n + NS_TILE - 1) / NS_TILE);
+    if (tiles > NS_TILE) return FE_ERR_UNSUPPORTED;
+    if (n == 0) return cudaMemsetAsync(out, 0, sizeof(int64_t), s) == cudaSuccess ? FE_OK : FE_ERR_DEVICE;
+    FE_LAUNCH((k_ns_tile_sums<<<(unsigned)tiles, NS_THREADS, 0, s>>>(in, n, tile_sums)));
+    FE_LAUNCH((k_ns_scan_sums<<<1, NS_THREADS, 0, s>>>(tile_sums, (int)tiles)));
+    FE_LAUNCH((k_ns_tile_scan<<<(unsigned)tiles, NS_THREADS, 0, s>>>(in, n, tile_sums, out)));
+    FE_CUDA(cudaGetLastError());
+    return FE_OK;
+}
+
+int noalloc_impl(unsigned char *scratch, int64_t n_e, int32_t n_loc, int64_t n_dofs, const int32_t *elem_dofs,
+                 int64_t *row_ptr, int32_t *col_idx, int64_t col_capacity, int64_t *nnz_out, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    FE_CUDA(cudaGetDevice(&dev));
+    FE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // layout for the largest case (block size 1): every array sized by DOFs
+    Bump bump{scratch, 0, FE_NOALLOC_SCRATCH_BYTES};
+    const int64_t n_inc = n_e * n_loc;
+    int64_t *sc = (int64_t *)bump.take(sizeof(int64_t) * S_COUNT);
+    int32_t *deg = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_dofs + 1));
+    int32_t *runs = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_e + 1));
+    int32_t *N = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_inc + 1));
+    uint32_t *run_mask = (uint32_t *)bump.take(sizeof(uint32_t) * (size_t)(n_e * ((n_loc + 31) / 32) + 1));
+    int64_t *adj_ptr = (int64_t *)bump.take(sizeof(int64_t) * (size_t)(n_dofs + 1));
+    uint32_t *adj = (uint32_t *)bump.take(sizeof(uint32_t) * (size_t)(n_inc + 1));
+    int32_t *node_len = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_dofs + 1));
+    int32_t *node_runs2 = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_dofs + 1));
+    int32_t *keys = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_inc * n_loc + 1));
+    int64_t *nrp = (int64_t *)bump.take(sizeof(int64_t) * (size_t)(n_dofs + 1));
+    int64_t *ncp = (int64_t *)bump.take(sizeof(int64_t) * (size_t)(n_dofs + 1));
+    int64_t *crac_ptr = (int64_t *)bump.take(sizeof(int64_t) * (size_t)(n_dofs + 1));
+    int64_t *tile_sums = (int64_t *)bump.take(sizeof(int64_t) * (size_t)NS_TILE);
+    if (!tile_sums) return FE_ERR_UNSUPPORTED;  // mesh too large for the fixed scratch
+
+    // everything that must start at zero (the array keeps the last call's data)
+    FE_CUDA(cudaMemsetAsync(sc, 0, sizeof(int64_t) * S_COUNT, s));
+    FE_CUDA(cudaMemsetAsync(sc + S_BLOCKS, 0xff, sizeof(int64_t), s));
+    FE_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)(n_dofs + 1), s));
+
+    int64_t h[S_COUNT];
+    if (n_e > 0) {
+        uint32_t cand = 0;
+        for (int b = 2; b <= 32; ++b)
+            if (n_loc % b == 0 && n_dofs % b == 0) cand |= 1u << (b - 1);
+        FE_LAUNCH((k_validate<<<fe_grid_for(n_e * 32, 256, sms, 16), 256, 0, s>>>(elem_dofs, n_e, n_loc, n_dofs, cand,
+                                                                               sc)));
+        FE_CUDA(cudaGetLastError());
+    }
+    FE_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    if (h[S_ERR] != 0) return (int)h[S_ERR];
+    int B = 1;
+    for (int b = 32; b >= 2 && n_e > 0; --b)
+        if ((((uint32_t)h[S_BLOCKS] >> (b - 1)) & 1u) && n_loc % b == 0 && n_dofs % b == 0) {
+            B = b;
+            break;
+        }
+    const int32_t nln = n_loc / B;
+    const int64_t n_nodes = n_dofs / B, n_ninc = n_e * nln;
+    const int mw = (nln + 31) / 32;
+    if (n_e > 0) {
+        FE_LAUNCH((k_node_conn<<<fe_grid_for(n_e * 32, 256, sms, 16), 256, 0, s>>>(elem_dofs, n_e, n_loc, B, nln, mw, N,
+                                                                                run_mask, runs, deg, sc)));
+        FE_LAUNCH((k_max_i32<<<fe_grid_for(n_nodes, 256, sms, 8), 256, 0, s>>>(deg, n_nodes, sc + S_MAX_DEG)));
+        FE_CUDA(cudaGetLastError());
+    }
+    FE_TRY(ns_scan(deg, adj_ptr, n_nodes, tile_sums, s));
+    FE_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)(n_nodes + 1), s));
+    if (n_ninc > 0) {
+        FE_LAUNCH((k_fill_adj<<<fe_grid_for(n_ninc, 256, sms, 16), 256, 0, s>>>(N, n_ninc, n_nodes, adj_ptr, deg, adj)));
+        FE_LAUNCH((k_sort_adj<<<fe_grid_for(n_nodes, 128, sms, 16), 128, 0, s>>>(adj_ptr, n_nodes, adj)));
+        FE_CUDA(cudaGetLastError());
+    }
+    FE_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    const int64_t cand = h[S_MAX_DEG] * nln;
+    if (n_nodes > 0) {
+        const int grid = fe_grid_for(n_nodes * 32, 256, sms, 8);
+        if (cand <= 32) {
+            FE_LAUNCH((k_row_keys<1><<<grid, 256, 0, s>>>(N, nln, n_nodes, adj_ptr, adj, node_len, node_runs2, keys, sc)));
+        } else if (cand <= 64) {
+            FE_LAUNCH((k_row_keys<2><<<grid, 256, 0, s>>>(N, nln, n_nodes, adj_ptr, adj, node_len, node_runs2, keys, sc)));
+        } else if (cand <= 128) {
+            FE_LAUNCH((k_row_keys<4><<<grid, 256, 0, s>>>(N, nln, n_nodes, adj_ptr, adj, node_len, node_runs2, keys, sc)));
+        } else if (cand <= REG_SORT_MAX) {
+            FE_LAUNCH((k_row_keys<8><<<grid, 256, 0, s>>>(N, nln, n_nodes, adj_ptr, adj, node_len, node_runs2, keys, sc)));
+        } else {
+            int P = 32;
+            while (P < cand) P <<= 1;
+            if ((int64_t)P * 4 > 128 * 1024) return FE_ERR_UNSUPPORTED;
+            const int W = (int)std::max<int64_t>(1, std::min<int64_t>(8, (64 * 1024) / ((int64_t)P * 4)));
+            const size_t smem = (size_t)W * P * 4;
+            FE_TRY(configure_smem(k_row_keys_smem, smem));
+            FE_LAUNCH((k_row_keys_smem<<<fe_grid_for(n_nodes * 32, W * 32, sms, std::max(1, 64 / W)), W * 32, smem,
+                                         s>>>(N, nln, n_nodes, adj_ptr, adj, P, node_len, node_runs2, keys, sc)));
+        }
+        FE_CUDA(cudaGetLastError());
+    }
+    FE_TRY(ns_scan(node_len, nrp, n_nodes, tile_sums, s));
+    FE_TRY(ns_scan(node_runs2, ncp, n_nodes, tile_sums, s));
+    int64_t node_nnz = 0;
+    FE_CUDA(cudaMemcpyAsync(&node_nnz, nrp + n_nodes, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    const int64_t nnz = (int64_t)B * B * node_nnz;
+    if (nnz_out) *nnz_out = nnz;
+    if (nnz >= INT32_MAX) return FE_ERR_OVERFLOW;
+    if (col_capacity < nnz) return FE_ERR_INVALID_ARG;  // *nnz_out tells the caller how much to provide
+    if (n_nodes > 0)
+        FE_LAUNCH((k_expand<<<fe_grid_for(n_nodes * 32, 256, sms, 8), 256, 0, s>>>(
+            n_nodes, B, nln, adj_ptr, keys, node_len, node_runs2, nrp, ncp, row_ptr, crac_ptr, col_idx, nullptr)));
+    FE_LAUNCH((k_tail<<<1, 1, 0, s>>>(row_ptr, crac_ptr, nrp, ncp, n_nodes, n_dofs, B)));
+    FE_CUDA(cudaGetLastError());
+    FE_CUDA(cudaStreamSynchronize(s));
+    return FE_OK;
+}
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[256] = {};
+
+}  // namespace
+
+extern "C" int fe_pattern_csr_noalloc(int64_t n_elem, int32_t dofs_per_elem, int64_t n_dofs, const int32_t *elem_dofs,
+                                      int64_t *row_ptr, int32_t *col_idx, int64_t col_capacity, int64_t *nnz,
+                                      void *stream)
+{
+    if (nnz) *nnz = 0;
+    if (n_elem < 0 || dofs_per_elem <= 0 || n_dofs < 0 || !row_ptr || col_capacity < 0) return FE_ERR_INVALID_ARG;
+    if (n_elem > 0 && (!elem_dofs || !col_idx)) return FE_ERR_INVALID_ARG;
+    if (dofs_per_elem > FE_MAX_NLOC) return FE_ERR_UNSUPPORTED;
+    if (n_dofs >= INT32_MAX || n_elem * (int64_t)dofs_per_elem >= (int64_t)UINT32_MAX) return FE_ERR_OVERFLOW;
+    int dev = 0;
+    FE_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return FE_ERR_UNSUPPORTED;
+    void *scratch = nullptr;
+    {
+        // first call on a device: look up the device address of the array
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) FE_CUDA(cudaGetSymbolAddress(&g_noalloc_addr[dev], fe_noalloc_scratch));
+        scratch = g_noalloc_addr[dev];
+    }
+    return noalloc_impl((unsigned char *)scratch, n_elem, dofs_per_elem, n_dofs, elem_dofs, row_ptr, col_idx,
+                        col_capacity, nnz, (cudaStream_t)stream);
+}

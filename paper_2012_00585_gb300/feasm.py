@@ -105,6 +105,7 @@ def load():
             "fe_tune_get": (i, [vp, i, ctypes.POINTER(i)]),
             "fe_pattern_build": (i, [vp, i64, i32, i64, vp, u32, vp, pp]),
             "fe_pattern_free": (i, [vp]),
+            "fe_pattern_csr_noalloc": (i, [i64, i32, i64, vp, vp, vp, i64, ctypes.POINTER(i64), vp]),
             "fe_pattern_csr": (i, [vp, pp, pp, ctypes.POINTER(i64)]),
             "fe_pattern_crac": (i, [vp, pp, pp, ctypes.POINTER(i64)]),
             "fe_pattern_adjacency": (i, [vp, ctypes.POINTER(i32), pp, pp]),
@@ -194,6 +195,22 @@ def fe_pattern_build(ctx, n_elem, dofs_per_elem, n_dofs, elem_dofs, flags=FE_PAT
     _check(load().fe_pattern_build(ctx, int(n_elem), int(dofs_per_elem), int(n_dofs), _addr(elem_dofs),
                                    int(flags), _stream(stream), ctypes.byref(out)), "fe_pattern_build")
     return out
+
+
+def fe_pattern_csr_noalloc(n_elem, dofs_per_elem, n_dofs, elem_dofs, row_ptr, col_idx, col_capacity,
+                           stream=None):
+    """CSR pattern into caller-provided device buffers without allocating;
+    returns nnz.  Raises FeError (code FE_ERR_INVALID_ARG) when col_capacity
+    is below nnz; the error's .nnz then holds the size needed."""
+    nnz = ctypes.c_int64()
+    rc = load().fe_pattern_csr_noalloc(int(n_elem), int(dofs_per_elem), int(n_dofs), _addr(elem_dofs),
+                                       _addr(row_ptr), _addr(col_idx), int(col_capacity), ctypes.byref(nnz),
+                                       _stream(stream))
+    if rc != FE_OK:
+        err = FeError(rc, "fe_pattern_csr_noalloc")
+        err.nnz = nnz.value
+        raise err
+    return nnz.value
 
 
 def fe_pattern_free(pattern):
