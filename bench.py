@@ -56,6 +56,22 @@ def b_alg(n_e, n_loc, nnz):
     return 8 * n_e * n_loc * n_loc + 4 * n_e * n_loc + 8 * nnz
 
 
+def reduce_max_over_ranks(x, device):
+    """Max of a per-rank scalar over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_units(units_per_rank, world):
+    """Replicas: every rank assembles its own copy of the workload."""
+    return units_per_rank * world
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -210,13 +226,9 @@ def run_gpu(args, rank, world, local_rank):
     if dist:
         tdist.barrier()
     clk = clocks.stop()
-    ms = t0.elapsed_time(t1) / args.steps
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max_over_ranks(t0.elapsed_time(t1) / args.steps, dev)
     kern_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-    value = world * N_ASSEMBLIES * N_ent / (ms * 1e-3)
+    value = whole_job_units(N_ASSEMBLIES * N_ent, world) / (ms * 1e-3)
 
     # per-variant numeric times and the pattern build on its own
     extra = {}
@@ -326,15 +338,10 @@ def run_e2e(args, ctx, feasm, D, Kd, n_dofs, nnz, mode, assemble, stream, dev, w
     for _ in range(steps):
         step()
     torch.cuda.synchronize()
-    sec = (time.perf_counter() - t0) / steps
-    if dist:
-        import torch.distributed as tdist
-        t = torch.tensor([sec], dtype=torch.float64, device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        sec = float(t.item())
+    sec = reduce_max_over_ranks((time.perf_counter() - t0) / steps, dev)
     h2d = D_h.numel() * 4 + K_h.numel() * 8
     d2h = v_h.numel() * 8 + rp_h.numel() * 8 + ci_h.numel() * 4
-    return {"value": world * N_ASSEMBLIES * n_e * n_loc * n_loc / sec, "unit": UNIT, "h2d_bytes_per_step": h2d,
+    return {"value": whole_job_units(N_ASSEMBLIES * n_e * n_loc * n_loc, world) / sec, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": round(sec * 1e3, 3)}
 
 

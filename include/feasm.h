@@ -256,6 +256,55 @@ int fe_assemble_csr(fe_ctx *ctx, const fe_pattern *pattern, const double *elem_m
 int fe_assemble_crac(fe_ctx *ctx, const fe_pattern *pattern, const double *elem_mats,
                      double *values, int mode, int accumulate, void *stream);
 
+/* ---- batched assembly (many independent meshes, one launch) --------------
+ * Not in the paper: a GPU runs thousands of small assemblies at once when
+ * they share one persistent launch.  Every mesh keeps its own pattern, K and
+ * values; the result of each is the single-mesh result (bit-identical in
+ * FE_DETERMINISTIC). */
+#define FE_FORMAT_CSR 0
+#define FE_FORMAT_CRAC 1
+
+#define FE_SCHED_WARP_PER_ELEMENT 1  /* FE_ATOMIC: a warp per element          */
+#define FE_SCHED_THREAD_PER_ENTRY 2  /* FE_ATOMIC: a thread per K entry        */
+#define FE_SCHED_BLOCK_PER_ELEMENT 3 /* FE_ATOMIC: a thread block per element  */
+#define FE_SCHED_WARP_PER_ROW 4      /* FE_DETERMINISTIC: a warp per node row  */
+
+typedef struct fe_schedule {
+    int32_t kind;  /* FE_SCHED_*                                               */
+    int32_t tile;  /* elements (atomic) or node rows (deterministic) per tile  */
+} fe_schedule;
+
+typedef struct fe_batch_item {
+    const fe_pattern *pattern;  /* built on the same context                     */
+    const double *elem_mats;    /* device, [n_elem * n_loc * n_loc], read only    */
+    double *values;             /* device, [nnz], written (or added to)           */
+} fe_batch_item;
+
+/* Assemble n_items meshes in one persistent launch on `stream` (plus one
+ * zeroing launch in FE_ATOMIC without accumulation).  format: FE_FORMAT_CSR /
+ * FE_FORMAT_CRAC; mode, accumulate as in fe_assemble_csr.  sched = NULL uses
+ * the schedule fe_batch_autotune found for a batch of this signature (element
+ * shapes, format, mode, size class), else a default.  The item array is read
+ * during the call only.  Asynchronous. */
+int fe_assemble_batch(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
+                      int32_t accumulate, const fe_schedule *sched, void *stream);
+
+/* Time every candidate schedule (kind x tile) on this batch and remember the
+ * fastest for batches of the same signature.  Runs the assemblies (values
+ * are overwritten).  Synchronous on `stream`.  *best / *best_ms may be NULL. */
+int fe_batch_autotune(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
+                      void *stream, fe_schedule *best, float *best_ms);
+
+/* Capture one batched assembly into a CUDA graph (item table copied to the
+ * device once); fe_batch_graph_launch replays it on any stream, e.g. after
+ * new element values were written into the same K buffers.  The patterns and
+ * buffers must outlive the graph. */
+typedef struct fe_batch_graph fe_batch_graph;
+int fe_batch_graph_create(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
+                          int32_t accumulate, const fe_schedule *sched, void *stream, fe_batch_graph **out);
+int fe_batch_graph_launch(fe_batch_graph *graph, void *stream);
+int fe_batch_graph_destroy(fe_batch_graph *graph);
+
 #ifdef __cplusplus
 }
 #endif

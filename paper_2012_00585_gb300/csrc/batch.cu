@@ -1,4 +1,604 @@
-// Batching and serving scheduler state (filled in by the batch/serve layer).
+// Batched assembly: many independent meshes (patterns + element matrices +
+// values) in ONE persistent kernel launch.  The launch walks a work list of
+// tiles (a tile = `tile` consecutive elements in FE_ATOMIC, `tile`
+// consecutive node rows in FE_DETERMINISTIC) of every mesh; warps (or blocks)
+// take the next tile from an atomic counter, so meshes of very different
+// sizes share the GPU without per-mesh launches or tail effects.  The
+// arithmetic per element / node row is the single-mesh one
+// (assemble_body.cuh), so a batched result equals the per-mesh result: bit
+// for bit in FE_DETERMINISTIC.
+//
+// Schedules: FE_ATOMIC  -- warp per element, thread per entry, block per element
+//            FE_DETERMINISTIC -- warp per node row
+// An autotuner times the candidates on the caller's batch and caches the
+// fastest per batch signature in the context; a batch can also be captured
+// once into a CUDA graph and replayed.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "assemble_body.cuh"
 #include "internal.cuh"
 
-void fe_batch_state_destroy(fe_ctx *ctx) { (void)ctx; }
+using namespace fe_dev;
+
+namespace {
+
+enum Shape { SH_GENERIC = 0, SH_4_1 = 1, SH_8_1 = 2, SH_8_3 = 3, SH_10_3 = 4 };
+
+struct BatchItemDev {
+    Geo g;
+    const double *K;
+    double *values;
+    const void *map;
+    const void *mapc;
+    int64_t units;       // elements (atomic) or node rows (deterministic)
+    int64_t nnz;
+    int64_t tile_begin;  // first global tile of this item
+    int32_t nln, B, shape, map_bytes;
+};
+
+int shape_of(const fe_pattern *p)
+{
+    if (p->nln == 4 && p->B == 1) return SH_4_1;
+    if (p->nln == 8 && p->B == 1) return SH_8_1;
+    if (p->nln == 8 && p->B == 3) return SH_8_3;
+    if (p->nln == 10 && p->B == 3) return SH_10_3;
+    return SH_GENERIC;
+}
+
+__device__ __forceinline__ int find_item(const BatchItemDev *__restrict__ items, int n_items, int64_t t)
+{
+    int lo = 0, hi = n_items - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One non-inlined function per element shape, so that the batched kernel
+// needs the registers of its largest body, not of all bodies together.
+template <int NLN, int BB, typename MT, bool CRAC>
+__device__ __noinline__ void atomic_elem_call(const BatchItemDev *__restrict__ it, int64_t e, int lane)
+{
+    const Geo g = it->g;
+    atomic_element<NLN, BB, MT, CRAC>(it->K, e, g, (const MT *)it->map, (const MT *)it->mapc, it->values, lane);
+}
+
+template <typename MT, bool CRAC>
+__device__ __noinline__ void atomic_elem_generic_call(const BatchItemDev *__restrict__ it, int64_t e, int lane,
+                                                      int64_t *base_s, int32_t *k_s, int32_t *off_s)
+{
+    const Geo g = it->g;
+    atomic_element_generic<MT, CRAC>(it->K, e, it->nln, it->B, g, (const MT *)it->map, (const MT *)it->mapc,
+                                     it->values, base_s, k_s, off_s, lane);
+}
+
+template <int NLN, int BB, typename MT, bool CRAC>
+__device__ __noinline__ void gather_row_call(const BatchItemDev *__restrict__ it, int64_t v, double *acc,
+                                             int accumulate, int lane)
+{
+    const Geo g = it->g;
+    gather_row<NLN, BB, MT, CRAC, 4>(it->K, v, g, (const MT *)it->map, (const MT *)it->mapc, acc, accumulate,
+                                     it->values, lane);
+}
+
+template <typename MT, bool CRAC>
+__device__ __noinline__ void gather_row_generic_call(const BatchItemDev *__restrict__ it, int64_t v, double *acc,
+                                                     int accumulate, int lane)
+{
+    const Geo g = it->g;
+    gather_row_generic<MT, CRAC>(it->K, v, it->nln, it->B, g, (const MT *)it->map, (const MT *)it->mapc, acc,
+                                 accumulate, it->values, lane);
+}
+
+template <typename MT, bool CRAC>
+__device__ __forceinline__ void atomic_elem_any(const BatchItemDev *it, int shape, int64_t e, int lane,
+                                                int64_t *base_s, int32_t *k_s, int32_t *off_s)
+{
+    switch (shape) {
+    case SH_4_1: atomic_elem_call<4, 1, MT, CRAC>(it, e, lane); break;
+    case SH_8_1: atomic_elem_call<8, 1, MT, CRAC>(it, e, lane); break;
+    case SH_8_3: atomic_elem_call<8, 3, MT, CRAC>(it, e, lane); break;
+    case SH_10_3: atomic_elem_call<10, 3, MT, CRAC>(it, e, lane); break;
+    default: atomic_elem_generic_call<MT, CRAC>(it, e, lane, base_s, k_s, off_s);
+    }
+}
+
+template <typename MT, bool CRAC>
+__device__ __forceinline__ void gather_row_any(const BatchItemDev *it, int shape, int64_t v, double *acc,
+                                               int accumulate, int lane)
+{
+    switch (shape) {
+    case SH_4_1: gather_row_call<4, 1, MT, CRAC>(it, v, acc, accumulate, lane); break;
+    case SH_8_1: gather_row_call<8, 1, MT, CRAC>(it, v, acc, accumulate, lane); break;
+    case SH_8_3: gather_row_call<8, 3, MT, CRAC>(it, v, acc, accumulate, lane); break;
+    case SH_10_3: gather_row_call<10, 3, MT, CRAC>(it, v, acc, accumulate, lane); break;
+    default: gather_row_generic_call<MT, CRAC>(it, v, acc, accumulate, lane);
+    }
+}
+
+// Slot of entry q of element e for any shape (thread-per-entry schedule).
+template <typename MT, bool CRAC>
+__device__ __forceinline__ int64_t entry_slot(const BatchItemDev &it, int64_t e, int q)
+{
+    const int B = it.B, nln = it.nln, n_loc = nln * B;
+    const int r = q / n_loc, c = q - r * n_loc;
+    const int kc = c / B;
+    const int64_t row = (int64_t)B * it.g.N[e * nln + r / B] + r % B;
+    int pos;
+    int64_t base;
+    if (!CRAC) {
+        base = it.g.row_ptr[row];
+        pos = (int)((const MT *)it.map)[(e * nln + r / B) * nln + kc];
+    } else {
+        base = crac_row_base(it.g, row);
+        const int64_t rp = it.g.run_ptr[e];
+        const int nr = (int)(it.g.run_ptr[e + 1] - rp);
+        int k, off;
+        run_of_multi(it.g.run_mask + e * it.g.mask_words, kc, k, off);
+        pos = (int)((const MT *)it.mapc)[rp * nln + (int64_t)(r / B) * nr + k] + off;
+    }
+    return base + (int64_t)B * pos + c % B;
+}
+
+constexpr int SCHED_THREADS = 256;
+
+template <bool CRAC, int SCHED>
+__global__ void __launch_bounds__(SCHED_THREADS) k_batch(const BatchItemDev *__restrict__ items, int n_items,
+                                                         int64_t total_tiles, int tile, int cap, int accumulate,
+                                                         unsigned long long *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long block_tile;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (SCHED == FE_SCHED_BLOCK_PER_ELEMENT) {
+        int64_t *base_s = (int64_t *)smem_raw;            // [FE_MAX_NLOC] row starts
+        int32_t *k_s = (int32_t *)(base_s + FE_MAX_NLOC);  // [FE_MAX_NLOC] run index (CRAC)
+        int32_t *off_s = k_s + FE_MAX_NLOC;                // [FE_MAX_NLOC] offset in run (CRAC)
+        for (;;) {
+            if (threadIdx.x == 0) block_tile = atomicAdd(counter, 1ull);
+            __syncthreads();
+            const unsigned long long t = block_tile;
+            __syncthreads();
+            if (t >= (unsigned long long)total_tiles) break;
+            const BatchItemDev &it = items[find_item(items, n_items, (int64_t)t)];
+            const int64_t u0 = ((int64_t)t - it.tile_begin) * tile, u1 = min(u0 + tile, it.units);
+            const int B = it.B, nln = it.nln, n_loc = nln * B;
+            const int NN = n_loc * n_loc;
+            for (int64_t e = u0; e < u1; ++e) {
+                int64_t rp = 0;
+                int nr = 0;
+                if (CRAC) {
+                    rp = it.g.run_ptr[e];
+                    nr = (int)(it.g.run_ptr[e + 1] - rp);
+                }
+                for (int r = threadIdx.x; r < n_loc; r += blockDim.x) {
+                    const int64_t row = (int64_t)B * it.g.N[e * nln + r / B] + r % B;
+                    base_s[r] = CRAC ? crac_row_base(it.g, row) : it.g.row_ptr[row];
+                }
+                if (CRAC)
+                    for (int kc = threadIdx.x; kc < nln; kc += blockDim.x)
+                        run_of_multi(it.g.run_mask + e * it.g.mask_words, kc, k_s[kc], off_s[kc]);
+                __syncthreads();
+                for (int q = threadIdx.x; q < NN; q += blockDim.x) {
+                    const int r = q / n_loc, c = q - r * n_loc;
+                    const int kc = c / B;
+                    int pos;
+                    if (!CRAC) {
+                        const int64_t mi = (e * nln + r / B) * nln + kc;
+                        pos = it.map_bytes == 1 ? (int)((const uint8_t *)it.map)[mi] : (int)((const uint16_t *)it.map)[mi];
+                    } else {
+                        const int64_t mi = rp * nln + (int64_t)(r / B) * nr + k_s[kc];
+                        pos = (it.map_bytes == 1 ? (int)((const uint8_t *)it.mapc)[mi]
+                                                 : (int)((const uint16_t *)it.mapc)[mi]) + off_s[kc];
+                    }
+                    atomicAdd(it.values + base_s[r] + (int64_t)B * pos + c % B, __ldcs(it.K + e * NN + q));
+                }
+                __syncthreads();
+            }
+        }
+        return;
+    }
+    // warp-level schedules
+    double *acc = (double *)smem_raw + (size_t)wib * cap;                       // deterministic
+    int64_t *base_s = (int64_t *)smem_raw + (size_t)wib * FE_MAX_NLOC;          // atomic, generic shapes
+    int32_t *k_s = (int32_t *)((int64_t *)smem_raw + (size_t)(SCHED_THREADS / 32) * FE_MAX_NLOC) +
+                   (size_t)wib * 2 * FE_MAX_NLOC;
+    int32_t *off_s = k_s + FE_MAX_NLOC;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= (unsigned long long)total_tiles) break;
+        const BatchItemDev &it = items[find_item(items, n_items, (int64_t)t)];
+        const int64_t u0 = ((int64_t)t - it.tile_begin) * tile, u1 = min(u0 + tile, it.units);
+        if (SCHED == FE_SCHED_WARP_PER_ROW) {
+            for (int64_t v = u0; v < u1; ++v) {
+                if (it.map_bytes == 1) gather_row_any<uint8_t, CRAC>(&it, it.shape, v, acc, accumulate, lane);
+                else gather_row_any<uint16_t, CRAC>(&it, it.shape, v, acc, accumulate, lane);
+            }
+        } else if (SCHED == FE_SCHED_WARP_PER_ELEMENT) {
+            for (int64_t e = u0; e < u1; ++e) {
+                if (it.map_bytes == 1) atomic_elem_any<uint8_t, CRAC>(&it, it.shape, e, lane, base_s, k_s, off_s);
+                else atomic_elem_any<uint16_t, CRAC>(&it, it.shape, e, lane, base_s, k_s, off_s);
+            }
+        } else {  // thread per entry: the tile's entries spread over the lanes
+            const int n_loc = it.nln * it.B;
+            const int64_t NN = (int64_t)n_loc * n_loc;
+            for (int64_t x = u0 * NN + lane; x < u1 * NN; x += 32) {
+                const int64_t e = x / NN;
+                const int q = (int)(x - e * NN);
+                const int64_t slot = it.map_bytes == 1 ? entry_slot<uint8_t, CRAC>(it, e, q)
+                                                       : entry_slot<uint16_t, CRAC>(it, e, q);
+                atomicAdd(it.values + slot, __ldcs(it.K + x));
+            }
+        }
+    }
+}
+
+// Zero every item's values (FE_ATOMIC without accumulation) in one launch.
+__global__ void k_batch_zero(const BatchItemDev *__restrict__ items, int n_items)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int i = 0; i < n_items; ++i) {
+        double *v = items[i].values;
+        const int64_t n = items[i].nnz;
+        for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) v[k] = 0.0;
+    }
+}
+
+struct Plan {
+    std::vector<BatchItemDev> host;
+    int64_t total_tiles = 0;
+    int cap = 1;  // doubles of accumulator per warp (deterministic)
+};
+
+int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mode, int tile, Plan &plan)
+{
+    plan.host.resize(n);
+    plan.total_tiles = 0;
+    plan.cap = 1;
+    for (int i = 0; i < n; ++i) {
+        const fe_pattern *p = items[i].pattern;
+        if (!p || p->ctx != ctx) return FE_ERR_INVALID_ARG;
+        if ((p->n_e > 0 && !items[i].elem_mats) || (p->nnz > 0 && !items[i].values)) return FE_ERR_INVALID_ARG;
+        if (((uintptr_t)items[i].elem_mats & 7u) || ((uintptr_t)items[i].values & 7u)) return FE_ERR_INVALID_ARG;
+        if (format == FE_FORMAT_CSR && !p->map_csr) return FE_ERR_NOT_BUILT;
+        if (format == FE_FORMAT_CRAC && (!p->map_crac || !p->col_align)) return FE_ERR_NOT_BUILT;
+        if (mode == FE_DETERMINISTIC && !p->adj) return FE_ERR_NOT_BUILT;
+        BatchItemDev &d = plan.host[i];
+        d.g = geo_of(p);
+        d.K = items[i].elem_mats;
+        d.values = items[i].values;
+        d.map = p->map_csr;
+        d.mapc = p->map_crac;
+        d.units = mode == FE_ATOMIC ? p->n_e : p->n_nodes;
+        d.nnz = p->nnz;
+        d.tile_begin = plan.total_tiles;
+        d.nln = p->nln;
+        d.B = p->B;
+        d.shape = shape_of(p);
+        d.map_bytes = p->map_bytes;
+        plan.total_tiles += (d.units + tile - 1) / tile;
+        plan.cap = std::max(plan.cap, p->B * p->max_row_len);
+    }
+    return FE_OK;
+}
+
+size_t batch_smem(int mode, int sched, int cap)
+{
+    const int W = SCHED_THREADS / 32;
+    if (mode == FE_DETERMINISTIC) return (size_t)W * cap * 8;
+    if (sched == FE_SCHED_BLOCK_PER_ELEMENT) return (size_t)FE_MAX_NLOC * 16;
+    return (size_t)W * FE_MAX_NLOC * 8 + (size_t)W * 2 * FE_MAX_NLOC * 4;
+}
+
+template <bool CRAC, int SCHED>
+int launch_batch_t(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t total, int tile, int cap, int acc,
+                   unsigned long long *counter, size_t smem, cudaStream_t s)
+{
+    auto kern = k_batch<CRAC, SCHED>;
+    if (smem > 48 * 1024) FE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SCHED_THREADS, smem));
+    if (per_sm < 1) return FE_ERR_UNSUPPORTED;
+    const int64_t want = SCHED == FE_SCHED_BLOCK_PER_ELEMENT ? total : (total + 7) / 8;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * per_sm, want));
+    kern<<<grid, SCHED_THREADS, smem, s>>>(d_items, n, total, tile, cap, acc, counter);
+    fe_note_launch();
+    FE_CUDA(cudaGetLastError());
+    return FE_OK;
+}
+
+int launch_batch(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t total, int format, int mode, int acc,
+                 int sched, int tile, int cap, unsigned long long *counter, cudaStream_t s)
+{
+    const size_t smem = batch_smem(mode, sched, cap);
+    if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
+    const bool crac = format == FE_FORMAT_CRAC;
+    if (mode == FE_DETERMINISTIC)
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s);
+    switch (sched) {
+    case FE_SCHED_THREAD_PER_ENTRY:
+        return crac ? launch_batch_t<true, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s)
+                    : launch_batch_t<false, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s);
+    case FE_SCHED_BLOCK_PER_ELEMENT:
+        return crac ? launch_batch_t<true, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s)
+                    : launch_batch_t<false, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s);
+    default:
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s);
+    }
+}
+
+bool sched_valid(int mode, const fe_schedule &sc)
+{
+    if (sc.tile < 1 || sc.tile > (1 << 20)) return false;
+    if (mode == FE_DETERMINISTIC) return sc.kind == FE_SCHED_WARP_PER_ROW;
+    return sc.kind == FE_SCHED_WARP_PER_ELEMENT || sc.kind == FE_SCHED_THREAD_PER_ENTRY ||
+           sc.kind == FE_SCHED_BLOCK_PER_ELEMENT;
+}
+
+}  // namespace
+
+// ---- per-context state: tuned schedules ----------------------------------
+
+struct fe_batch_state {
+    std::mutex mu;
+    std::map<std::tuple<int, int, uint64_t, int>, fe_schedule> tuned;  // (format, mode, shapes, size bucket)
+};
+
+void fe_batch_state_destroy(fe_ctx *ctx)
+{
+    delete ctx->batch;
+    ctx->batch = nullptr;
+}
+
+namespace {
+
+fe_batch_state *state_of(fe_ctx *ctx)
+{
+    static std::mutex create_mu;
+    std::lock_guard<std::mutex> lk(create_mu);
+    if (!ctx->batch) ctx->batch = new fe_batch_state();
+    return ctx->batch;
+}
+
+std::tuple<int, int, uint64_t, int> signature(const fe_batch_item *items, int n, int format, int mode)
+{
+    uint64_t shapes = 0;
+    int64_t units = 0;
+    for (int i = 0; i < n; ++i) {
+        const fe_pattern *p = items[i].pattern;
+        shapes |= 1ull << (shape_of(p) * 8 + std::min(p->map_bytes, 2));
+        units += (int64_t)p->n_e * p->n_loc * p->n_loc;
+    }
+    int bucket = 0;
+    while ((1ll << bucket) < units && bucket < 62) ++bucket;
+    return std::make_tuple(format, mode, shapes, bucket / 2);
+}
+
+fe_schedule default_schedule(int mode)
+{
+    return mode == FE_DETERMINISTIC ? fe_schedule{FE_SCHED_WARP_PER_ROW, 16} : fe_schedule{FE_SCHED_WARP_PER_ELEMENT, 16};
+}
+
+struct DeviceScope {
+    int prev = -1, dev;
+    explicit DeviceScope(int d) : dev(d)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceScope()
+    {
+        if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    }
+};
+
+// Plan upload + launch on stream s.  The item table and the tile counter are
+// stream-ordered allocations freed after the launch.
+int run_batch(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mode, int acc, fe_schedule sc,
+              cudaStream_t s)
+{
+    Plan plan;
+    FE_TRY(make_plan(ctx, items, n, format, mode, sc.tile, plan));
+    BatchItemDev *d_items = nullptr;
+    unsigned long long *counter = nullptr;
+    FE_TRY(fe_alloc(ctx, (void **)&d_items, sizeof(BatchItemDev) * n, s));
+    int rc = fe_alloc(ctx, (void **)&counter, sizeof(unsigned long long), s);
+    if (rc == FE_OK && cudaMemcpyAsync(d_items, plan.host.data(), sizeof(BatchItemDev) * n, cudaMemcpyHostToDevice,
+                                       s) != cudaSuccess)
+        rc = FE_ERR_DEVICE;
+    if (rc == FE_OK && cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s) != cudaSuccess) rc = FE_ERR_DEVICE;
+    if (rc == FE_OK && mode == FE_ATOMIC && !acc) {
+        k_batch_zero<<<ctx->num_sms * 4, 256, 0, s>>>(d_items, n);
+        fe_note_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = FE_ERR_DEVICE;
+    }
+    if (rc == FE_OK && plan.total_tiles > 0)
+        rc = launch_batch(ctx, d_items, n, plan.total_tiles, format, mode, acc, sc.kind, sc.tile, plan.cap, counter, s);
+    fe_free_async(d_items, s);
+    fe_free_async(counter, s);
+    return rc;
+}
+
+}  // namespace
+
+struct fe_batch_graph {
+    fe_ctx *ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    BatchItemDev *d_items = nullptr;
+    unsigned long long *counter = nullptr;
+};
+
+extern "C" {
+
+int fe_assemble_batch(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
+                      int32_t accumulate, const fe_schedule *sched, void *stream)
+{
+    if (!ctx || n_items < 0 || (n_items > 0 && !items)) return FE_ERR_INVALID_ARG;
+    if ((format != FE_FORMAT_CSR && format != FE_FORMAT_CRAC) || (mode != FE_ATOMIC && mode != FE_DETERMINISTIC) ||
+        (accumulate != 0 && accumulate != 1))
+        return FE_ERR_INVALID_ARG;
+    if (n_items == 0) return FE_OK;
+    DeviceScope ds(ctx->device);
+    fe_schedule sc = default_schedule(mode);
+    if (sched) {
+        sc = *sched;
+        if (!sched_valid(mode, sc)) return FE_ERR_INVALID_ARG;
+    } else {
+        fe_batch_state *st = state_of(ctx);
+        std::lock_guard<std::mutex> lk(st->mu);
+        auto it = st->tuned.find(signature(items, n_items, format, mode));
+        if (it != st->tuned.end()) sc = it->second;
+    }
+    return run_batch(ctx, items, n_items, format, mode, accumulate, sc, (cudaStream_t)stream);
+}
+
+int fe_batch_autotune(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
+                      void *stream, fe_schedule *best, float *best_ms)
+{
+    if (!ctx || n_items <= 0 || !items) return FE_ERR_INVALID_ARG;
+    if ((format != FE_FORMAT_CSR && format != FE_FORMAT_CRAC) || (mode != FE_ATOMIC && mode != FE_DETERMINISTIC))
+        return FE_ERR_INVALID_ARG;
+    DeviceScope ds(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<fe_schedule> cands;
+    if (mode == FE_DETERMINISTIC) {
+        for (int t : {1, 4, 16, 64}) cands.push_back({FE_SCHED_WARP_PER_ROW, t});
+    } else {
+        for (int t : {1, 4, 16, 64}) cands.push_back({FE_SCHED_WARP_PER_ELEMENT, t});
+        for (int t : {1, 4}) cands.push_back({FE_SCHED_THREAD_PER_ENTRY, t});
+        for (int t : {1, 4}) cands.push_back({FE_SCHED_BLOCK_PER_ELEMENT, t});
+    }
+    cudaEvent_t e0, e1;
+    FE_CUDA(cudaEventCreate(&e0));
+    FE_CUDA(cudaEventCreate(&e1));
+    fe_schedule win = cands[0];
+    float win_ms = 1e30f;
+    int rc = FE_OK;
+    for (const fe_schedule &sc : cands) {
+        rc = run_batch(ctx, items, n_items, format, mode, 0, sc, s);  // warm-up
+        if (rc == FE_ERR_UNSUPPORTED) continue;
+        if (rc != FE_OK) break;
+        float best_rep = 1e30f;
+        for (int rep = 0; rep < 3 && rc == FE_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            rc = run_batch(ctx, items, n_items, format, mode, 0, sc, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = FE_ERR_DEVICE;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best_rep = std::min(best_rep, ms);
+        }
+        if (rc != FE_OK) break;
+        if (best_rep < win_ms) {
+            win_ms = best_rep;
+            win = sc;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != FE_OK) return rc;
+    {
+        fe_batch_state *st = state_of(ctx);
+        std::lock_guard<std::mutex> lk(st->mu);
+        st->tuned[signature(items, n_items, format, mode)] = win;
+    }
+    if (best) *best = win;
+    if (best_ms) *best_ms = win_ms;
+    return FE_OK;
+}
+
+int fe_batch_graph_create(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
+                          int32_t accumulate, const fe_schedule *sched, void *stream, fe_batch_graph **out)
+{
+    if (!ctx || !out || n_items <= 0 || !items) return FE_ERR_INVALID_ARG;
+    if ((format != FE_FORMAT_CSR && format != FE_FORMAT_CRAC) || (mode != FE_ATOMIC && mode != FE_DETERMINISTIC) ||
+        (accumulate != 0 && accumulate != 1))
+        return FE_ERR_INVALID_ARG;
+    *out = nullptr;
+    DeviceScope ds(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    fe_schedule sc = default_schedule(mode);
+    if (sched) {
+        sc = *sched;
+        if (!sched_valid(mode, sc)) return FE_ERR_INVALID_ARG;
+    } else {
+        fe_batch_state *st = state_of(ctx);
+        std::lock_guard<std::mutex> lk(st->mu);
+        auto it = st->tuned.find(signature(items, n_items, format, mode));
+        if (it != st->tuned.end()) sc = it->second;
+    }
+    Plan plan;
+    FE_TRY(make_plan(ctx, items, n_items, format, mode, sc.tile, plan));
+    fe_batch_graph *g = new fe_batch_graph();
+    g->ctx = ctx;
+    int rc = FE_OK;
+    // the graph's own item table and counter live as long as the graph
+    if (cudaMalloc((void **)&g->d_items, sizeof(BatchItemDev) * n_items) != cudaSuccess ||
+        cudaMalloc((void **)&g->counter, sizeof(unsigned long long)) != cudaSuccess)
+        rc = FE_ERR_OOM;
+    if (rc == FE_OK && cudaMemcpy(g->d_items, plan.host.data(), sizeof(BatchItemDev) * n_items,
+                                  cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = FE_ERR_DEVICE;
+    cudaStream_t cs = nullptr;
+    if (rc == FE_OK && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = FE_ERR_DEVICE;
+    if (rc == FE_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = FE_ERR_DEVICE;
+    if (rc == FE_OK) {
+        int lrc = cudaMemsetAsync(g->counter, 0, sizeof(unsigned long long), cs) == cudaSuccess ? FE_OK : FE_ERR_DEVICE;
+        if (lrc == FE_OK && mode == FE_ATOMIC && !accumulate) {
+            k_batch_zero<<<ctx->num_sms * 4, 256, 0, cs>>>(g->d_items, n_items);
+            if (cudaGetLastError() != cudaSuccess) lrc = FE_ERR_DEVICE;
+        }
+        if (lrc == FE_OK && plan.total_tiles > 0)
+            lrc = launch_batch(ctx, g->d_items, n_items, plan.total_tiles, format, mode, accumulate, sc.kind, sc.tile,
+                               plan.cap, g->counter, cs);
+        const cudaError_t ec = cudaStreamEndCapture(cs, &g->graph);
+        rc = lrc != FE_OK ? lrc : (ec == cudaSuccess ? FE_OK : FE_ERR_DEVICE);
+    }
+    if (rc == FE_OK && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) rc = FE_ERR_DEVICE;
+    if (cs) cudaStreamDestroy(cs);
+    (void)s;
+    if (rc != FE_OK) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        if (g->d_items) cudaFree(g->d_items);
+        if (g->counter) cudaFree(g->counter);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return FE_OK;
+}
+
+int fe_batch_graph_launch(fe_batch_graph *g, void *stream)
+{
+    if (!g) return FE_ERR_INVALID_ARG;
+    DeviceScope ds(g->ctx->device);
+    FE_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    fe_note_launch();
+    return FE_OK;
+}
+
+int fe_batch_graph_destroy(fe_batch_graph *g)
+{
+    if (!g) return FE_ERR_INVALID_ARG;
+    DeviceScope ds(g->ctx->device);
+    cudaDeviceSynchronize();
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->d_items) cudaFree(g->d_items);
+    if (g->counter) cudaFree(g->counter);
+    delete g;
+    return FE_OK;
+}
+
+}  // extern "C"

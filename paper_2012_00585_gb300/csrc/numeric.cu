@@ -18,49 +18,13 @@
 // each element (the compressed DOF array of §2.1): one map entry per
 // (element, row block, run), the column's offset inside its run, and the
 // row start read from the CRAC pairs (Listing 5's contiguous slices).
+#include "assemble_body.cuh"
 #include "internal.cuh"
 #include "tma.cuh"
 
 namespace {
 
-struct Geo {
-    const int32_t *N;        // block ids per element
-    const int64_t *row_ptr;  // CSR
-    const int64_t *crac_ptr; // CRAC
-    const int32_t *col_align;
-    const uint32_t *run_mask;
-    const int64_t *run_ptr;
-    const int64_t *adj_ptr;
-    const uint32_t *adj;
-    int uniform_R;  // > 0 when every element has this many runs and the same mask
-    int mask_words;
-};
-
-__device__ __forceinline__ int64_t crac_row_base(const Geo &g, int64_t i) { return g.col_align[g.crac_ptr[i] + 1]; }
-
-// Run index of block kc and kc's offset inside that run, for run-start bits m
-// (kc < 32, bit 0 always set).
-__device__ __forceinline__ void run_of(uint32_t m, int kc, int &k, int &off)
-{
-    const uint32_t le = m & (0xffffffffu >> (31 - kc));
-    k = __popc(le) - 1;
-    off = kc - (31 - __clz(le));
-}
-
-// The same for any number of 32-bit mask words.
-__device__ __forceinline__ void run_of_multi(const uint32_t *m, int kc, int &k, int &off)
-{
-    int before = 0, last = 0;
-    const int w_end = kc >> 5;
-    for (int w = 0; w < w_end; ++w) {
-        before += __popc(m[w]);
-        if (m[w]) last = 32 * w + 31 - __clz(m[w]);
-    }
-    const uint32_t le = m[w_end] & (0xffffffffu >> (31 - (kc & 31)));
-    k = before + __popc(le) - 1;
-    const int start = le ? 32 * w_end + 31 - __clz(le) : last;
-    off = kc - start;
-}
+using namespace fe_dev;
 
 // ------------------------------------------------------------ atomic ---
 // One warp per element; NLN blocks of BB DOFs, NLN*BB <= 32.
@@ -592,11 +556,6 @@ int configure_smem(KernelT kernel, size_t bytes)
     return FE_OK;
 }
 
-Geo geo_of(const fe_pattern *p)
-{
-    return Geo{p->node_dofs, p->row_ptr,  p->crac_ptr, p->col_align, p->run_mask,
-               p->run_ptr,   p->adj_ptr, p->adj,      p->uniform_runs ? p->runs_per_elem : 0, p->mask_words};
-}
 
 template <typename KernelT>
 int grid_by_occupancy(KernelT kernel, int threads, size_t smem, int sms, int64_t warps_needed, int *grid)

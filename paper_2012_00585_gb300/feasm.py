@@ -45,6 +45,13 @@ FE_KNOB_ATOMIC_KERNEL = 3
 FE_KNOB_ATOMIC_WARPS = 4
 FE_KNOB_COUNT = 8
 
+FE_FORMAT_CSR = 0
+FE_FORMAT_CRAC = 1
+FE_SCHED_WARP_PER_ELEMENT = 1
+FE_SCHED_THREAD_PER_ENTRY = 2
+FE_SCHED_BLOCK_PER_ELEMENT = 3
+FE_SCHED_WARP_PER_ROW = 4
+
 _lib = None
 _lock = threading.Lock()
 
@@ -76,6 +83,14 @@ class fe_pattern_info(ctypes.Structure):
         ("reserved", ctypes.c_int32),
         ("device_bytes", ctypes.c_int64),
     ]
+
+
+class fe_schedule(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("tile", ctypes.c_int32)]
+
+
+class fe_batch_item(ctypes.Structure):
+    _fields_ = [("pattern", ctypes.c_void_p), ("elem_mats", ctypes.c_void_p), ("values", ctypes.c_void_p)]
 
 
 def library_path() -> str:
@@ -112,6 +127,14 @@ def load():
             "fe_pattern_info_get": (i, [vp, ctypes.POINTER(fe_pattern_info)]),
             "fe_assemble_csr": (i, [vp, vp, vp, vp, i, i, vp]),
             "fe_assemble_crac": (i, [vp, vp, vp, vp, i, i, vp]),
+            "fe_assemble_batch": (i, [vp, ctypes.POINTER(fe_batch_item), i32, i32, i32, i32,
+                                      ctypes.POINTER(fe_schedule), vp]),
+            "fe_batch_autotune": (i, [vp, ctypes.POINTER(fe_batch_item), i32, i32, i32, vp,
+                                      ctypes.POINTER(fe_schedule), ctypes.POINTER(ctypes.c_float)]),
+            "fe_batch_graph_create": (i, [vp, ctypes.POINTER(fe_batch_item), i32, i32, i32, i32,
+                                          ctypes.POINTER(fe_schedule), vp, pp]),
+            "fe_batch_graph_launch": (i, [vp, vp]),
+            "fe_batch_graph_destroy": (i, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -250,6 +273,55 @@ def fe_assemble_csr(ctx, pattern, elem_mats, values, mode=FE_ATOMIC, accumulate=
 def fe_assemble_crac(ctx, pattern, elem_mats, values, mode=FE_ATOMIC, accumulate=0, stream=None):
     _check(load().fe_assemble_crac(ctx, pattern, _addr(elem_mats), _addr(values), int(mode), int(accumulate),
                                    _stream(stream)), "fe_assemble_crac")
+
+
+def _items(items):
+    """items: sequence of (pattern handle or Pattern, K tensor/addr, values tensor/addr)."""
+    arr = (fe_batch_item * max(len(items), 1))()
+    for k, (pat, K, v) in enumerate(items):
+        h = pat.handle if isinstance(pat, Pattern) else pat
+        arr[k].pattern = h.value if isinstance(h, ctypes.c_void_p) else h
+        arr[k].elem_mats = _addr(K)
+        arr[k].values = _addr(v)
+    return arr
+
+
+def _sched(sched):
+    if sched is None:
+        return None
+    kind, tile = sched
+    return ctypes.byref(fe_schedule(int(kind), int(tile)))
+
+
+def fe_assemble_batch(ctx, items, fmt=FE_FORMAT_CSR, mode=FE_ATOMIC, accumulate=0, sched=None, stream=None):
+    arr = _items(items)
+    _check(load().fe_assemble_batch(ctx, arr, len(items), int(fmt), int(mode), int(accumulate), _sched(sched),
+                                    _stream(stream)), "fe_assemble_batch")
+
+
+def fe_batch_autotune(ctx, items, fmt=FE_FORMAT_CSR, mode=FE_ATOMIC, stream=None):
+    """-> (kind, tile, ms) of the fastest schedule; remembered for this batch signature."""
+    arr = _items(items)
+    best, ms = fe_schedule(), ctypes.c_float()
+    _check(load().fe_batch_autotune(ctx, arr, len(items), int(fmt), int(mode), _stream(stream), ctypes.byref(best),
+                                    ctypes.byref(ms)), "fe_batch_autotune")
+    return best.kind, best.tile, ms.value
+
+
+def fe_batch_graph_create(ctx, items, fmt=FE_FORMAT_CSR, mode=FE_ATOMIC, accumulate=0, sched=None, stream=None):
+    arr = _items(items)
+    out = ctypes.c_void_p()
+    _check(load().fe_batch_graph_create(ctx, arr, len(items), int(fmt), int(mode), int(accumulate), _sched(sched),
+                                        _stream(stream), ctypes.byref(out)), "fe_batch_graph_create")
+    return out
+
+
+def fe_batch_graph_launch(graph, stream=None):
+    _check(load().fe_batch_graph_launch(graph, _stream(stream)), "fe_batch_graph_launch")
+
+
+def fe_batch_graph_destroy(graph):
+    _check(load().fe_batch_graph_destroy(graph), "fe_batch_graph_destroy")
 
 
 # ---- views of library-owned device arrays --------------------------------

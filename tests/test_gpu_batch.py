@@ -1,0 +1,154 @@
+"""Batched assembly (one persistent launch over many meshes) against the
+per-mesh path and the oracle: every schedule, both formats, both modes;
+the autotuner; CUDA-graph replay with new element values."""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2012_00585_gb300 import feasm
+    c = feasm.fe_create(0)
+    yield c
+    feasm.fe_destroy(c)
+
+
+def _meshes():
+    out = []
+    for n in (3, 5, 8):
+        out.append(wl.hex_q1_grid(n, 1) + (wl.laplace_q1_hex(1.0 / n),))
+    for n in (2, 4, 6):
+        out.append(wl.hex_q1_grid(n, 3) + (wl.elasticity_q1_hex(1.0 / n),))
+    out.append(wl.tet_p2_kuhn(2, d=3, seed=3) + (None,))     # 30 x 30, runs vary per element
+    out.append(wl.quad_qp_grid(3, 3, 1) + (None,))           # 16 x 16, no specialised kernel
+    out.append(wl.quad_q1_grid(5, 1) + (wl.laplace_q1_quad(),))
+    out.append(wl.quad_qp_grid(2, 8, 1) + (None,))           # rows over 256: 16-bit maps
+    return out
+
+
+@pytest.fixture(scope="module")
+def batch(ctx):
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    rows = []
+    for k, (D, n_dofs, Kr) in enumerate(_meshes()):
+        if Kr is None:
+            K = wl.random_matrices(D.shape[0], D.shape[1], seed=k)
+        else:
+            K = wl.scaled_matrices(Kr, D.shape[0], seed=k)
+        pat = feasm.Pattern(ctx, torch.from_numpy(D).cuda(), n_dofs)
+        rp, ci = oracle.csr_pattern(D, n_dofs)
+        v_o = oracle.assemble_csr(D, K, rp, ci)
+        tau = gu.row_tolerance(rp, v_o, gu.contribution_abs_row_sums(D, K, n_dofs))
+        rows.append(dict(D=D, n_dofs=n_dofs, K=K, Kd=torch.from_numpy(K).cuda(), pat=pat, rp=rp, v_o=v_o, tau=tau,
+                         v=torch.empty(pat.info["nnz"], dtype=torch.float64, device="cuda")))
+    yield rows
+    for r in rows:
+        r["pat"].free()
+
+
+def _items(rows):
+    return [(r["pat"], r["Kd"], r["v"]) for r in rows]
+
+
+def _check(rows, mode):
+    from paper_2012_00585_gb300 import feasm
+    for r in rows:
+        got = r["v"].cpu().numpy()
+        if mode == feasm.FE_DETERMINISTIC:
+            assert np.array_equal(got.view(np.uint64), r["v_o"].view(np.uint64))
+        else:
+            gu.assert_within_row_tol(r["rp"], got, r["v_o"], r["tau"])
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+@pytest.mark.parametrize("sched", [(4, 1), (4, 16), (4, 64)])
+def test_batch_deterministic_bit_exact(ctx, batch, fmt, sched):
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    for r in batch:
+        r["v"].fill_(float("nan"))
+    feasm.fe_assemble_batch(ctx, _items(batch), fmt, feasm.FE_DETERMINISTIC, 0, sched)
+    torch.cuda.synchronize()
+    _check(batch, feasm.FE_DETERMINISTIC)
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+@pytest.mark.parametrize("sched", [(1, 1), (1, 16), (2, 1), (2, 4), (3, 1), (3, 4)])
+def test_batch_atomic_schedules(ctx, batch, fmt, sched):
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    for r in batch:
+        r["v"].fill_(float("nan"))
+    feasm.fe_assemble_batch(ctx, _items(batch), fmt, feasm.FE_ATOMIC, 0, sched)
+    torch.cuda.synchronize()
+    _check(batch, feasm.FE_ATOMIC)
+
+
+def test_batch_accumulate_and_bad_schedule(ctx, batch):
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    feasm.fe_assemble_batch(ctx, _items(batch), 0, feasm.FE_DETERMINISTIC)
+    feasm.fe_assemble_batch(ctx, _items(batch), 0, feasm.FE_DETERMINISTIC, accumulate=1)
+    torch.cuda.synchronize()
+    for r in batch:
+        exp = oracle.assemble_csr(r["D"], r["K"], r["rp"], oracle.csr_pattern(r["D"], r["n_dofs"])[1], values=r["v_o"])
+        assert np.array_equal(r["v"].cpu().numpy(), exp)
+    with pytest.raises(feasm.FeError):
+        feasm.fe_assemble_batch(ctx, _items(batch), 0, feasm.FE_DETERMINISTIC, 0, (1, 16))  # atomic-only kind
+    with pytest.raises(feasm.FeError):
+        feasm.fe_assemble_batch(ctx, _items(batch), 0, feasm.FE_ATOMIC, 0, (1, 0))  # tile 0
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_autotune_then_default_uses_it(ctx, batch, mode):
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    kind, tile, ms = feasm.fe_batch_autotune(ctx, _items(batch), 0, mode)
+    assert ms > 0 and tile >= 1
+    assert kind == feasm.FE_SCHED_WARP_PER_ROW if mode == 1 else kind in (1, 2, 3)
+    for r in batch:
+        r["v"].fill_(float("nan"))
+    feasm.fe_assemble_batch(ctx, _items(batch), 0, mode)
+    torch.cuda.synchronize()
+    _check(batch, mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_graph_replay_with_new_values(ctx, batch, mode):
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    g = feasm.fe_batch_graph_create(ctx, _items(batch), 1, mode)
+    try:
+        for rep in range(2):
+            # new element values in the same buffers, then replay
+            for k, r in enumerate(batch):
+                K2 = wl.random_matrices(r["D"].shape[0], r["D"].shape[1], seed=100 + 10 * rep + k)
+                r["Kd"].copy_(torch.from_numpy(K2))
+                r["K2"] = K2
+                r["v"].fill_(float("nan"))
+            feasm.fe_batch_graph_launch(g)
+            torch.cuda.synchronize()
+            for r in batch:
+                rp, ci = oracle.csr_pattern(r["D"], r["n_dofs"])
+                exp = oracle.assemble_csr(r["D"], r["K2"], rp, ci)
+                got = r["v"].cpu().numpy()
+                if mode == 1:
+                    assert np.array_equal(got, exp)
+                else:
+                    tau = gu.row_tolerance(rp, exp, gu.contribution_abs_row_sums(r["D"], r["K2"], r["n_dofs"]))
+                    gu.assert_within_row_tol(rp, got, exp, tau)
+    finally:
+        feasm.fe_batch_graph_destroy(g)
+        for r in batch:  # restore the module's K for other tests
+            r["Kd"].copy_(torch.from_numpy(r["K"]))

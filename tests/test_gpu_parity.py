@@ -303,3 +303,60 @@ def test_invalid_connectivity_reports_errors(ctx):
     assert v.cpu().tolist() == [1.0] * 9
     p.free()
     p2.free()
+
+
+@pytest.mark.slow
+def test_c3_full_size_sampled_rows(ctx):
+    """Config 3 at full size: 96^3 hexes -> 5,308,416 permuted P2 tets,
+    21,567,171 DOFs, random SPD 30x30 K drawn on the device (38 GB).  The
+    whole pattern is checked by properties that hold at any size (nnz is
+    permutation invariant and equals the natural-numbering count); sampled
+    rows are checked entry by entry against the oracle run on the sub-mesh of
+    the elements that touch them (in ascending element order, which leaves
+    those rows' sums unchanged)."""
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    n = 96
+    D, n_dofs = wl.tet_p2_kuhn(n, d=3, seed=2012)
+    assert D.shape == (5_308_416, 30) and n_dofs == 21_567_171
+    g = gu.GpuAssembly(ctx, D, n_dofs)
+    info = g.pattern.info
+    assert info["nnz"] == 1_842_870_537 and info["block"] == 3
+    rp_d, ci_d = g.pattern.csr()
+    crp_d, ca_d = g.pattern.crac()
+    Kd = wl.random_spd_matrices(D.shape[0], 30, seed=7, device="cuda", chunk=1 << 18)
+    rng = np.random.default_rng(0)
+    rows = np.unique(np.concatenate([rng.choice(n_dofs, 60, replace=False), [0, n_dofs - 1]]))
+    # elements touching the sampled rows, ascending
+    hit = np.isin(D, rows).any(axis=1)
+    els = np.nonzero(hit)[0]
+    Dsub = D[els]
+    Ksub = Kd[torch.from_numpy(els).cuda()].cpu().numpy()
+    rp_o, ci_o = oracle.csr_pattern(Dsub, n_dofs)
+    v_o = oracle.assemble_csr(Dsub, Ksub, rp_o, ci_o)
+    crp_o, ca_o = oracle.crac_from_csr(rp_o, ci_o, n_dofs)
+    rp_h = rp_d.cpu().numpy()
+    crp_h = crp_d.cpu().numpy()
+    assert np.all(np.diff(rp_h) >= 0) and rp_h[-1] == info["nnz"]
+    for fmt in ("csr", "crac"):
+        for mode in (feasm.FE_DETERMINISTIC, feasm.FE_ATOMIC):
+            v = g.assemble(Kd, fmt, mode)
+            for i in rows:
+                a, b = int(rp_h[i]), int(rp_h[i + 1])
+                ao, bo = int(rp_o[i]), int(rp_o[i + 1])
+                assert np.array_equal(ci_d[a:b].cpu().numpy(), ci_o[ao:bo])
+                ca_row = ca_d[int(crp_h[i]):int(crp_h[i + 1])].cpu().numpy()
+                ca_row_o = ca_o[int(crp_o[i]):int(crp_o[i + 1])].copy()
+                ca_row_o[1::2] += a - ao  # value positions are relative to the row's start
+                assert np.array_equal(ca_row, ca_row_o)
+                got = v[a:b].cpu().numpy()
+                exp = v_o[ao:bo]
+                if mode == feasm.FE_DETERMINISTIC:
+                    assert np.array_equal(got.view(np.uint64), exp.view(np.uint64))
+                else:
+                    assert np.all(np.abs(got - exp) <= 1e-12 * np.abs(exp).sum())
+            del v
+    assert feasm.fe_device_status(ctx) == 0
+    del Kd
+    torch.cuda.empty_cache()
+    g.free()
