@@ -305,6 +305,84 @@ int fe_batch_graph_create(fe_ctx *ctx, const fe_batch_item *items, int32_t n_ite
 int fe_batch_graph_launch(fe_batch_graph *graph, void *stream);
 int fe_batch_graph_destroy(fe_batch_graph *graph);
 
+/* ---- serving: requests admitted by HBM footprint, continuous batching ------
+ * Not in the paper.  A server owns a scheduler thread (admission, launches,
+ * completions) and a pattern-builder thread.  Patterns are cached by
+ * `pattern_key`; a request for a cached key is numeric-only.  Admitted
+ * requests are assembled together (fe_assemble_batch) on one of n_streams
+ * streams, so new requests are admitted and run while others are in flight. */
+#define FE_STATE_PENDING 0    /* submitted, waiting for admission            */
+#define FE_STATE_ADMITTED 1   /* memory reserved, pattern being built/looked up */
+#define FE_STATE_RUNNING 2    /* launched                                     */
+#define FE_STATE_DONE 3
+#define FE_STATE_FAILED 4
+#define FE_STATE_CANCELLED 5
+
+typedef struct fe_request {
+    uint64_t pattern_key;      /* identity of the mesh for the pattern cache            */
+    int64_t n_elem;
+    int32_t dofs_per_elem;
+    int32_t format;            /* FE_FORMAT_CSR / FE_FORMAT_CRAC                        */
+    int64_t n_dofs;
+    const int32_t *elem_dofs;  /* device; read when the key is not cached; must stay
+                                  valid until the request completes                    */
+    const double *elem_mats;   /* device K, or NULL: generate K_e = alpha_e * K_ref   */
+    const double *k_ref;       /* device [n_loc*n_loc], used when elem_mats is NULL     */
+    uint64_t seed;             /* alpha_e = 0.5 + (splitmix64(seed + e) >> 44) / 2^20   */
+    int32_t mode;              /* FE_ATOMIC / FE_DETERMINISTIC                          */
+    int32_t reserved;
+    void *ready_event;         /* cudaEvent_t the assembly waits for (NULL = none)     */
+} fe_request;
+
+typedef struct fe_result {
+    int32_t status;            /* FE_OK or the error of the request                    */
+    int32_t state;             /* FE_STATE_*                                           */
+    int32_t cold;              /* 1 when the pattern was built for this request        */
+    int32_t reserved;
+    int64_t nnz;
+    const int64_t *row_ptr;    /* device, borrowed from the cached pattern             */
+    const int32_t *col_idx;    /* device, borrowed                                     */
+    const double *values;      /* device, library-owned until fe_release               */
+    double t_submit_us, t_admit_us, t_start_us, t_done_us;  /* host steady clock       */
+} fe_result;
+
+typedef struct fe_server_stats {
+    int64_t submitted, admitted, completed, failed, cancelled;
+    int64_t launches, batched_requests, patterns_built, evictions;
+    int64_t bytes_in_use, budget_bytes, cached_patterns;
+} fe_server_stats;
+
+typedef struct fe_server fe_server;
+
+/* Start a server on ctx: n_streams launch streams (1..64), at most max_batch
+ * requests per launch, hbm_budget_bytes of device memory for admitted
+ * requests and cached patterns (0 = the context's budget).  n_streams = 1
+ * with max_batch = 1 is a strict FIFO: one request at a time from admission
+ * to completion (the one-launch-per-request baseline). */
+int fe_server_start(fe_ctx *ctx, int32_t n_streams, int32_t max_batch, size_t hbm_budget_bytes,
+                    fe_server **out);
+/* Stop the threads, wait for the device, free everything the server owns. */
+int fe_server_stop(fe_server *server);
+/* Enqueue n requests (thread-safe); tickets[k] identifies request k.  A
+ * request whose footprint exceeds the whole budget fails with
+ * FE_ERR_ADMISSION; otherwise it waits until memory frees up. */
+int fe_batch_submit(fe_server *server, const fe_request *reqs, int32_t n, uint64_t *tickets);
+/* Current state of a ticket (never blocks). */
+int fe_poll(fe_server *server, uint64_t ticket, fe_result *out);
+/* Block until the ticket is done, failed or cancelled, or timeout_s passes
+ * (FE_ERR_TIMEOUT). */
+int fe_wait(fe_server *server, uint64_t ticket, double timeout_s, fe_result *out);
+/* Cancel a request that was not admitted yet. */
+int fe_cancel(fe_server *server, uint64_t ticket);
+/* Free a finished ticket's values and unpin its pattern. */
+int fe_release(fe_server *server, uint64_t ticket);
+int fe_server_stats_get(fe_server *server, fe_server_stats *out);
+
+/* K_e = alpha_e * K_ref for n_elem elements (the generator the server uses
+ * for requests without elem_mats), on `stream`. */
+int fe_generate_scaled(fe_ctx *ctx, const double *k_ref, int32_t n_loc, int64_t n_elem, uint64_t seed,
+                       double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

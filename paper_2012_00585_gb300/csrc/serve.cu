@@ -1,0 +1,590 @@
+// Serving loop: assembly requests arrive at any time; the library admits
+// them by HBM footprint, keeps their patterns (and slot maps) resident in a
+// cache keyed by mesh, builds missing patterns on a separate thread, and
+// launches the ready requests together as batched assemblies on several
+// streams, so that requests arriving while others run are admitted as memory
+// frees up and their work overlaps on the GPU (continuous batching).
+//
+// Element values of a request are either given (device K) or generated on
+// the device after admission as K_e = alpha_e * K_ref, with alpha_e = 0.5 +
+// u_e and u_e the top 20 bits of splitmix64(seed + e) / 2^20 (Steele, Lea,
+// Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014; the
+// 64-bit finaliser of Vigna's splitmix64), one exact IEEE multiply per entry.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <list>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace {
+
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// K_e = alpha_e * K_ref for every element; one thread per entry.
+__global__ void k_generate_scaled(const double *__restrict__ k_ref, int32_t nn, int64_t n_e, uint64_t seed,
+                                  double *__restrict__ K)
+{
+    const int64_t total = n_e * nn;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = x / nn;
+        const int q = (int)(x - e * nn);
+        const double alpha = 0.5 + (double)(splitmix64(seed + (uint64_t)e) >> 44) * (1.0 / 1048576.0);
+        K[x] = alpha * k_ref[q];
+    }
+}
+
+int launch_generate(const double *k_ref, int32_t n_loc, int64_t n_e, uint64_t seed, double *K, int sms,
+                    cudaStream_t s)
+{
+    if (n_e == 0) return FE_OK;
+    const int64_t total = n_e * n_loc * n_loc;
+    k_generate_scaled<<<fe_grid_for(total, 256, sms, 16), 256, 0, s>>>(k_ref, n_loc * n_loc, n_e, seed, K);
+    fe_note_launch();
+    FE_CUDA(cudaGetLastError());
+    return FE_OK;
+}
+
+double now_us()
+{
+    using namespace std::chrono;
+    return (double)duration_cast<nanoseconds>(steady_clock::now().time_since_epoch()).count() * 1e-3;
+}
+
+struct Ticket {
+    fe_request req{};
+    int state = FE_STATE_PENDING;
+    int status = FE_OK;
+    int cold = 0;
+    fe_pattern *pattern = nullptr;
+    double *values = nullptr;  // library-owned until fe_release
+    double *K = nullptr;       // generated element matrices, freed at completion
+    size_t foot = 0;           // bytes charged against the budget
+    size_t k_bytes = 0, v_bytes = 0, v_charged = 0;
+    double t_submit = 0, t_admit = 0, t_start = 0, t_done = 0;
+    int stream = -1;
+};
+
+struct CacheEntry {
+    fe_pattern *p = nullptr;
+    size_t bytes = 0;
+    int refs = 0;
+    uint64_t last_use = 0;
+    bool building = false;
+};
+
+struct Group {
+    std::vector<uint64_t> ids;
+    cudaEvent_t done = nullptr;
+    int stream = 0;
+};
+
+}  // namespace
+
+struct fe_server {
+    fe_ctx *ctx = nullptr;
+    std::mutex mu;
+    std::condition_variable cv, cv_build, cv_done;
+    std::deque<uint64_t> pending, to_build, ready;
+    std::list<Group> inflight;
+    std::unordered_map<uint64_t, Ticket> tickets;
+    std::unordered_map<uint64_t, CacheEntry> cache;
+    size_t budget = 0, in_use = 0;
+    std::vector<cudaStream_t> streams;
+    cudaStream_t build_stream = nullptr;
+    int next_stream = 0, max_batch = 64;
+    uint64_t next_id = 1, clock = 0;
+    int active = 0;            // admitted and not finished
+    bool strict_fifo = false;  // one request at a time, end to end
+    bool stop = false;
+    std::thread sched, builder;
+    fe_server_stats stats{};
+};
+
+namespace {
+
+size_t pattern_estimate(const fe_request &r)
+{
+    // generous upper bound of a pattern built from n_e elements of n_loc DOFs
+    const size_t ninc = (size_t)r.n_elem * r.dofs_per_elem;
+    return ninc * r.dofs_per_elem * 6 + (size_t)r.n_dofs * 64 + ((size_t)1 << 20);
+}
+
+size_t values_estimate(const fe_request &r, const fe_pattern *p)
+{
+    if (p) return (size_t)p->nnz * 8;
+    return (size_t)r.n_elem * r.dofs_per_elem * r.dofs_per_elem * 8;  // nnz <= entries
+}
+
+// Evict unreferenced cached patterns, least recently used first, until
+// `need` more bytes fit.  Caller holds the lock.
+void evict_for(fe_server *sv, size_t need)
+{
+    while (sv->in_use + need > sv->budget) {
+        uint64_t victim = 0;
+        uint64_t oldest = UINT64_MAX;
+        for (auto &kv : sv->cache)
+            if (kv.second.refs == 0 && !kv.second.building && kv.second.last_use < oldest) {
+                oldest = kv.second.last_use;
+                victim = kv.first;
+            }
+        if (oldest == UINT64_MAX) return;
+        CacheEntry ce = sv->cache[victim];
+        sv->cache.erase(victim);
+        sv->in_use -= ce.bytes;
+        ++sv->stats.evictions;
+        cudaStreamSynchronize(sv->build_stream);
+        for (cudaStream_t s : sv->streams) cudaStreamSynchronize(s);
+        fe_pattern_free(ce.p);
+    }
+}
+
+void finish(fe_server *sv, Ticket &t, int status)
+{
+    if (t.t_admit > 0 && sv->active > 0) --sv->active;
+    t.status = status;
+    t.state = status == FE_OK ? FE_STATE_DONE : FE_STATE_FAILED;
+    t.t_done = now_us();
+    if (status == FE_OK) ++sv->stats.completed; else ++sv->stats.failed;
+}
+
+// Admission, launches and completions; runs on the scheduler thread.
+void scheduler_loop(fe_server *sv)
+{
+    cudaSetDevice(sv->ctx->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    while (!sv->stop) {
+        bool progress = false;
+        // completions
+        for (auto it = sv->inflight.begin(); it != sv->inflight.end();) {
+            const cudaError_t q = cudaEventQuery(it->done);
+            if (q == cudaErrorNotReady) {
+                ++it;
+                continue;
+            }
+            const int st = q == cudaSuccess ? FE_OK : FE_ERR_DEVICE;
+            for (uint64_t id : it->ids) {
+                Ticket &t = sv->tickets[id];
+                if (t.K) {
+                    fe_free_async(t.K, sv->streams[it->stream]);
+                    t.K = nullptr;
+                    sv->in_use -= t.k_bytes;
+                    t.foot -= t.k_bytes;
+                }
+                finish(sv, t, st);
+            }
+            cudaEventDestroy(it->done);
+            it = sv->inflight.erase(it);
+            progress = true;
+            sv->cv_done.notify_all();
+        }
+        // admission (arrival order)
+        while (!sv->pending.empty()) {
+            const uint64_t id = sv->pending.front();
+            Ticket &t = sv->tickets[id];
+            if (t.state == FE_STATE_CANCELLED) {
+                sv->pending.pop_front();
+                continue;
+            }
+            auto ce = sv->cache.find(t.req.pattern_key);
+            const bool cached = ce != sv->cache.end();
+            const fe_pattern *p = cached && !ce->second.building ? ce->second.p : nullptr;
+            const size_t k_bytes = t.req.elem_mats ? 0 : (size_t)t.req.n_elem * t.req.dofs_per_elem * t.req.dofs_per_elem * 8;
+            const size_t v_est = values_estimate(t.req, p);
+            const size_t need = k_bytes + v_est + (cached ? 0 : pattern_estimate(t.req));
+            if (need > sv->budget) {
+                sv->pending.pop_front();
+                finish(sv, t, FE_ERR_ADMISSION);
+                progress = true;
+                continue;
+            }
+            if (sv->strict_fifo && sv->active > 0) break;
+            if (sv->in_use + need > sv->budget) evict_for(sv, need);
+            if (sv->in_use + need > sv->budget) break;  // wait for memory to free up
+            sv->pending.pop_front();
+            sv->in_use += need;
+            t.foot = need;
+            t.k_bytes = k_bytes;
+            t.v_charged = v_est;
+            t.t_admit = now_us();
+            t.state = FE_STATE_ADMITTED;
+            ++sv->active;
+            ++sv->stats.admitted;
+            progress = true;
+            if (cached) {
+                ce->second.refs++;
+                ce->second.last_use = ++sv->clock;
+                if (ce->second.building) {
+                    sv->to_build.push_back(id);  // the builder hands it on when the pattern exists
+                } else {
+                    t.pattern = ce->second.p;
+                    sv->ready.push_back(id);
+                }
+            } else {
+                CacheEntry &ne = sv->cache[t.req.pattern_key];
+                ne.building = true;
+                ne.refs = 1;
+                ne.last_use = ++sv->clock;
+                t.cold = 1;
+                sv->to_build.push_back(id);
+                sv->cv_build.notify_one();
+            }
+        }
+        // launches: ready requests grouped by (format, mode)
+        while (!sv->ready.empty()) {
+            const uint64_t id0 = sv->ready.front();
+            const int fmt = sv->tickets[id0].req.format, mode = sv->tickets[id0].req.mode;
+            Group g;
+            g.stream = sv->next_stream;
+            sv->next_stream = (sv->next_stream + 1) % (int)sv->streams.size();
+            cudaStream_t s = sv->streams[g.stream];
+            std::vector<fe_batch_item> items;
+            for (auto it = sv->ready.begin(); it != sv->ready.end() && (int)items.size() < sv->max_batch;) {
+                Ticket &t = sv->tickets[*it];
+                if (t.req.format != fmt || t.req.mode != mode) {
+                    ++it;
+                    continue;
+                }
+                if (t.state == FE_STATE_CANCELLED) {
+                    it = sv->ready.erase(it);
+                    continue;
+                }
+                int rc = FE_OK;
+                t.v_bytes = (size_t)t.pattern->nnz * 8;
+                rc = fe_alloc(sv->ctx, (void **)&t.values, t.v_bytes, s);
+                if (rc == FE_OK && !t.req.elem_mats) {
+                    rc = fe_alloc(sv->ctx, (void **)&t.K, t.k_bytes, s);
+                    if (rc == FE_OK)
+                        rc = launch_generate(t.req.k_ref, t.req.dofs_per_elem, t.req.n_elem, t.req.seed, t.K,
+                                             sv->ctx->num_sms, s);
+                }
+                if (rc == FE_OK && t.req.ready_event) cudaStreamWaitEvent(s, (cudaEvent_t)t.req.ready_event, 0);
+                if (rc != FE_OK) {
+                    finish(sv, t, rc);
+                    it = sv->ready.erase(it);
+                    continue;
+                }
+                // footprint: the values charge becomes exact
+                if (t.v_charged > t.v_bytes) {
+                    const size_t drop = t.v_charged - t.v_bytes;
+                    t.foot -= std::min(drop, t.foot);
+                    sv->in_use -= std::min(drop, sv->in_use);
+                    t.v_charged = t.v_bytes;
+                }
+                t.state = FE_STATE_RUNNING;
+                t.t_start = now_us();
+                t.stream = g.stream;
+                items.push_back(fe_batch_item{t.pattern, t.K ? t.K : t.req.elem_mats, t.values});
+                g.ids.push_back(*it);
+                it = sv->ready.erase(it);
+            }
+            if (items.empty()) continue;
+            int rc = fe_assemble_batch(sv->ctx, items.data(), (int32_t)items.size(), fmt, mode, 0, nullptr, s);
+            if (rc == FE_OK && cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess) rc = FE_ERR_DEVICE;
+            if (rc == FE_OK && cudaEventRecord(g.done, s) != cudaSuccess) rc = FE_ERR_DEVICE;
+            if (rc != FE_OK) {
+                for (uint64_t id : g.ids) finish(sv, sv->tickets[id], rc);
+                if (g.done) cudaEventDestroy(g.done);
+                continue;
+            }
+            ++sv->stats.launches;
+            sv->stats.batched_requests += g.ids.size();
+            sv->inflight.push_back(std::move(g));
+            progress = true;
+        }
+        if (!progress) sv->cv.wait_for(lk, std::chrono::microseconds(sv->inflight.empty() ? 2000 : 20));
+    }
+}
+
+// Cold requests: build the pattern, publish it in the cache, pass the
+// request (and any that waited for the same key) on to the ready queue.
+void builder_loop(fe_server *sv)
+{
+    cudaSetDevice(sv->ctx->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    while (!sv->stop) {
+        uint64_t id = 0;
+        for (auto it = sv->to_build.begin(); it != sv->to_build.end(); ++it) {
+            Ticket &t = sv->tickets[*it];
+            CacheEntry &ce = sv->cache[t.req.pattern_key];
+            if (!ce.building) {  // built meanwhile by another request
+                t.pattern = ce.p;
+                sv->ready.push_back(*it);
+                sv->to_build.erase(it);
+                sv->cv.notify_one();
+                id = UINT64_MAX;
+                break;
+            }
+            if (t.cold) {
+                id = *it;
+                sv->to_build.erase(it);
+                break;
+            }
+        }
+        if (id == UINT64_MAX) continue;
+        if (id == 0) {
+            sv->cv_build.wait_for(lk, std::chrono::milliseconds(2));
+            continue;
+        }
+        const fe_request req = sv->tickets[id].req;
+        lk.unlock();
+        fe_pattern *p = nullptr;
+        int rc = fe_pattern_build(sv->ctx, req.n_elem, req.dofs_per_elem, req.n_dofs, req.elem_dofs, FE_PATTERN_ALL,
+                                  sv->build_stream, &p);
+        if (rc == FE_OK) rc = cudaStreamSynchronize(sv->build_stream) == cudaSuccess ? FE_OK : FE_ERR_DEVICE;
+        lk.lock();
+        Ticket &t = sv->tickets[id];
+        CacheEntry &ce = sv->cache[req.pattern_key];
+        ++sv->stats.patterns_built;
+        if (rc != FE_OK) {
+            sv->in_use -= std::min(t.foot, sv->in_use);
+            t.foot = 0;
+            finish(sv, t, rc);
+            sv->cache.erase(req.pattern_key);
+            // requests that waited for this key fail with it
+            for (auto it = sv->to_build.begin(); it != sv->to_build.end();) {
+                Ticket &w = sv->tickets[*it];
+                if (w.req.pattern_key == req.pattern_key) {
+                    sv->in_use -= std::min(w.foot, sv->in_use);
+                    w.foot = 0;
+                    finish(sv, w, rc);
+                    it = sv->to_build.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+            sv->cv_done.notify_all();
+            continue;
+        }
+        ce.p = p;
+        ce.bytes = (size_t)p->device_bytes;
+        ce.building = false;
+        // the estimate charged to this request becomes the pattern's real size
+        const size_t est = pattern_estimate(req);
+        sv->in_use = sv->in_use - std::min(est, sv->in_use) + ce.bytes;
+        t.foot = t.foot - std::min(est, t.foot);
+        t.pattern = p;
+        sv->ready.push_back(id);
+        sv->cv.notify_one();
+    }
+}
+
+int release_ticket(fe_server *sv, uint64_t id)
+{
+    auto it = sv->tickets.find(id);
+    if (it == sv->tickets.end()) return FE_ERR_NOT_FOUND;
+    Ticket &t = it->second;
+    if (t.state == FE_STATE_RUNNING || t.state == FE_STATE_ADMITTED) return FE_ERR_INVALID_ARG;
+    cudaStream_t s = t.stream >= 0 ? sv->streams[t.stream] : sv->streams[0];
+    if (t.values) fe_free_async(t.values, s);
+    if (t.K) fe_free_async(t.K, s);
+    sv->in_use -= std::min(t.foot, sv->in_use);
+    if (t.pattern) {
+        auto ce = sv->cache.find(t.req.pattern_key);
+        if (ce != sv->cache.end() && ce->second.refs > 0) ce->second.refs--;
+    }
+    sv->tickets.erase(it);
+    return FE_OK;
+}
+
+void fill_result(const Ticket &t, fe_result *out)
+{
+    out->status = t.status;
+    out->state = t.state;
+    out->cold = t.cold;
+    out->nnz = t.pattern ? t.pattern->nnz : 0;
+    out->row_ptr = t.pattern ? t.pattern->row_ptr : nullptr;
+    out->col_idx = t.pattern ? t.pattern->col_idx : nullptr;
+    out->values = t.state == FE_STATE_DONE ? t.values : nullptr;
+    out->t_submit_us = t.t_submit;
+    out->t_admit_us = t.t_admit;
+    out->t_start_us = t.t_start;
+    out->t_done_us = t.t_done;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fe_server_start(fe_ctx *ctx, int32_t n_streams, int32_t max_batch, size_t hbm_budget_bytes, fe_server **out)
+{
+    if (!ctx || !out || n_streams < 1 || n_streams > 64 || max_batch < 1) return FE_ERR_INVALID_ARG;
+    *out = nullptr;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    fe_server *sv = new fe_server();
+    sv->ctx = ctx;
+    sv->budget = hbm_budget_bytes ? hbm_budget_bytes : ctx->hbm_budget;
+    sv->max_batch = max_batch;
+    sv->strict_fifo = n_streams == 1 && max_batch == 1;
+    int rc = FE_OK;
+    for (int k = 0; k < n_streams && rc == FE_OK; ++k) {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) rc = FE_ERR_DEVICE;
+        else sv->streams.push_back(s);
+    }
+    if (rc == FE_OK && cudaStreamCreateWithFlags(&sv->build_stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = FE_ERR_DEVICE;
+    if (rc != FE_OK) {
+        for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
+        delete sv;
+        if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+        return rc;
+    }
+    sv->sched = std::thread(scheduler_loop, sv);
+    sv->builder = std::thread(builder_loop, sv);
+    *out = sv;
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    return FE_OK;
+}
+
+int fe_server_stop(fe_server *sv)
+{
+    if (!sv) return FE_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv.notify_all();
+    sv->cv_build.notify_all();
+    sv->sched.join();
+    sv->builder.join();
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != sv->ctx->device) cudaSetDevice(sv->ctx->device);
+    for (cudaStream_t s : sv->streams) cudaStreamSynchronize(s);
+    cudaStreamSynchronize(sv->build_stream);
+    for (auto &g : sv->inflight) cudaEventDestroy(g.done);
+    for (auto &kv : sv->tickets) {
+        if (kv.second.values) cudaFreeAsync(kv.second.values, sv->streams[0]);
+        if (kv.second.K) cudaFreeAsync(kv.second.K, sv->streams[0]);
+    }
+    cudaStreamSynchronize(sv->streams[0]);
+    for (auto &kv : sv->cache)
+        if (kv.second.p) fe_pattern_free(kv.second.p);
+    for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
+    cudaStreamDestroy(sv->build_stream);
+    const int dev = sv->ctx->device;
+    delete sv;
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    return FE_OK;
+}
+
+int fe_batch_submit(fe_server *sv, const fe_request *reqs, int32_t n, uint64_t *tickets)
+{
+    if (!sv || n < 0 || (n > 0 && (!reqs || !tickets))) return FE_ERR_INVALID_ARG;
+    for (int k = 0; k < n; ++k) {
+        const fe_request &r = reqs[k];
+        if (r.n_elem < 0 || r.dofs_per_elem <= 0 || r.n_dofs < 0 || (!r.elem_mats && !r.k_ref) ||
+            (r.format != FE_FORMAT_CSR && r.format != FE_FORMAT_CRAC) ||
+            (r.mode != FE_ATOMIC && r.mode != FE_DETERMINISTIC))
+            return FE_ERR_INVALID_ARG;
+    }
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        const double t0 = now_us();
+        for (int k = 0; k < n; ++k) {
+            const uint64_t id = sv->next_id++;
+            Ticket &t = sv->tickets[id];
+            t.req = reqs[k];
+            t.t_submit = t0;
+            sv->pending.push_back(id);
+            tickets[k] = id;
+            ++sv->stats.submitted;
+        }
+    }
+    sv->cv.notify_one();
+    return FE_OK;
+}
+
+int fe_poll(fe_server *sv, uint64_t ticket, fe_result *out)
+{
+    if (!sv || !out) return FE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->tickets.find(ticket);
+    if (it == sv->tickets.end()) return FE_ERR_NOT_FOUND;
+    fill_result(it->second, out);
+    return FE_OK;
+}
+
+int fe_wait(fe_server *sv, uint64_t ticket, double timeout_s, fe_result *out)
+{
+    if (!sv || !out) return FE_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds((int64_t)(timeout_s * 1e6));
+    for (;;) {
+        auto it = sv->tickets.find(ticket);
+        if (it == sv->tickets.end()) return FE_ERR_NOT_FOUND;
+        const int st = it->second.state;
+        if (st == FE_STATE_DONE || st == FE_STATE_FAILED || st == FE_STATE_CANCELLED) {
+            fill_result(it->second, out);
+            return FE_OK;
+        }
+        if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+            fill_result(it->second, out);
+            return FE_ERR_TIMEOUT;
+        }
+    }
+}
+
+int fe_cancel(fe_server *sv, uint64_t ticket)
+{
+    if (!sv) return FE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->tickets.find(ticket);
+    if (it == sv->tickets.end()) return FE_ERR_NOT_FOUND;
+    Ticket &t = it->second;
+    if (t.state != FE_STATE_PENDING) return FE_ERR_INVALID_ARG;  // only requests not yet admitted
+    t.state = FE_STATE_CANCELLED;
+    t.status = FE_ERR_CANCELLED;
+    t.t_done = now_us();
+    ++sv->stats.cancelled;
+    sv->cv_done.notify_all();
+    return FE_OK;
+}
+
+int fe_release(fe_server *sv, uint64_t ticket)
+{
+    if (!sv) return FE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    const int rc = release_ticket(sv, ticket);
+    sv->cv.notify_one();
+    return rc;
+}
+
+int fe_server_stats_get(fe_server *sv, fe_server_stats *out)
+{
+    if (!sv || !out) return FE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    *out = sv->stats;
+    out->bytes_in_use = (int64_t)sv->in_use;
+    out->budget_bytes = (int64_t)sv->budget;
+    out->cached_patterns = (int64_t)sv->cache.size();
+    return FE_OK;
+}
+
+int fe_generate_scaled(fe_ctx *ctx, const double *k_ref, int32_t n_loc, int64_t n_elem, uint64_t seed, double *out,
+                       void *stream)
+{
+    if (!ctx || !out || (n_elem > 0 && !k_ref) || n_loc <= 0 || n_elem < 0) return FE_ERR_INVALID_ARG;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    const int rc = launch_generate(k_ref, n_loc, n_elem, seed, out, ctx->num_sms, (cudaStream_t)stream);
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    return rc;
+}
+
+}  // extern "C"

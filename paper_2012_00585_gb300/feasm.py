@@ -93,6 +93,34 @@ class fe_batch_item(ctypes.Structure):
     _fields_ = [("pattern", ctypes.c_void_p), ("elem_mats", ctypes.c_void_p), ("values", ctypes.c_void_p)]
 
 
+FE_STATE_PENDING = 0
+FE_STATE_ADMITTED = 1
+FE_STATE_RUNNING = 2
+FE_STATE_DONE = 3
+FE_STATE_FAILED = 4
+FE_STATE_CANCELLED = 5
+
+
+class fe_request(ctypes.Structure):
+    _fields_ = [("pattern_key", ctypes.c_uint64), ("n_elem", ctypes.c_int64), ("dofs_per_elem", ctypes.c_int32),
+                ("format", ctypes.c_int32), ("n_dofs", ctypes.c_int64), ("elem_dofs", ctypes.c_void_p),
+                ("elem_mats", ctypes.c_void_p), ("k_ref", ctypes.c_void_p), ("seed", ctypes.c_uint64),
+                ("mode", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ready_event", ctypes.c_void_p)]
+
+
+class fe_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("state", ctypes.c_int32), ("cold", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("values", ctypes.c_void_p), ("t_submit_us", ctypes.c_double),
+                ("t_admit_us", ctypes.c_double), ("t_start_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+
+
+class fe_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "admitted", "completed", "failed", "cancelled",
+                                              "launches", "batched_requests", "patterns_built", "evictions",
+                                              "bytes_in_use", "budget_bytes", "cached_patterns")]
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -135,6 +163,15 @@ def load():
                                           ctypes.POINTER(fe_schedule), vp, pp]),
             "fe_batch_graph_launch": (i, [vp, vp]),
             "fe_batch_graph_destroy": (i, [vp]),
+            "fe_server_start": (i, [vp, i32, i32, ctypes.c_size_t, pp]),
+            "fe_server_stop": (i, [vp]),
+            "fe_batch_submit": (i, [vp, ctypes.POINTER(fe_request), i32, ctypes.POINTER(ctypes.c_uint64)]),
+            "fe_poll": (i, [vp, ctypes.c_uint64, ctypes.POINTER(fe_result)]),
+            "fe_wait": (i, [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(fe_result)]),
+            "fe_cancel": (i, [vp, ctypes.c_uint64]),
+            "fe_release": (i, [vp, ctypes.c_uint64]),
+            "fe_server_stats_get": (i, [vp, ctypes.POINTER(fe_server_stats)]),
+            "fe_generate_scaled": (i, [vp, vp, i32, i64, ctypes.c_uint64, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -322,6 +359,77 @@ def fe_batch_graph_launch(graph, stream=None):
 
 def fe_batch_graph_destroy(graph):
     _check(load().fe_batch_graph_destroy(graph), "fe_batch_graph_destroy")
+
+
+def fe_server_start(ctx, n_streams=4, max_batch=64, hbm_budget_bytes=0):
+    out = ctypes.c_void_p()
+    _check(load().fe_server_start(ctx, int(n_streams), int(max_batch), int(hbm_budget_bytes), ctypes.byref(out)),
+           "fe_server_start")
+    return out
+
+
+def fe_server_stop(server):
+    _check(load().fe_server_stop(server), "fe_server_stop")
+
+
+def make_request(pattern_key, elem_dofs, n_dofs, *, elem_mats=None, k_ref=None, seed=0, fmt=FE_FORMAT_CSR,
+                 mode=FE_DETERMINISTIC, ready_event=None):
+    """An fe_request for a device connectivity tensor [n_elem, n_loc]."""
+    r = fe_request()
+    r.pattern_key = int(pattern_key)
+    r.n_elem = int(elem_dofs.shape[0])
+    r.dofs_per_elem = int(elem_dofs.shape[1])
+    r.format = int(fmt)
+    r.n_dofs = int(n_dofs)
+    r.elem_dofs = _addr(elem_dofs)
+    r.elem_mats = _addr(elem_mats)
+    r.k_ref = _addr(k_ref)
+    r.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    r.mode = int(mode)
+    r.ready_event = None if ready_event is None else int(ready_event.cuda_event)
+    return r
+
+
+def fe_batch_submit(server, requests):
+    arr = (fe_request * max(len(requests), 1))(*requests)
+    tickets = (ctypes.c_uint64 * max(len(requests), 1))()
+    _check(load().fe_batch_submit(server, arr, len(requests), tickets), "fe_batch_submit")
+    return [int(tickets[k]) for k in range(len(requests))]
+
+
+def _result_dict(res):
+    return {name: getattr(res, name) for name, _ in fe_result._fields_}
+
+
+def fe_poll(server, ticket):
+    res = fe_result()
+    _check(load().fe_poll(server, int(ticket), ctypes.byref(res)), "fe_poll")
+    return _result_dict(res)
+
+
+def fe_wait(server, ticket, timeout_s=60.0):
+    res = fe_result()
+    _check(load().fe_wait(server, int(ticket), float(timeout_s), ctypes.byref(res)), "fe_wait")
+    return _result_dict(res)
+
+
+def fe_cancel(server, ticket):
+    _check(load().fe_cancel(server, int(ticket)), "fe_cancel")
+
+
+def fe_release(server, ticket):
+    _check(load().fe_release(server, int(ticket)), "fe_release")
+
+
+def fe_server_stats_get(server):
+    st = fe_server_stats()
+    _check(load().fe_server_stats_get(server, ctypes.byref(st)), "fe_server_stats_get")
+    return {name: getattr(st, name) for name, _ in fe_server_stats._fields_}
+
+
+def fe_generate_scaled(ctx, k_ref, n_loc, n_elem, seed, out, stream=None):
+    _check(load().fe_generate_scaled(ctx, _addr(k_ref), int(n_loc), int(n_elem), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                     _addr(out), _stream(stream)), "fe_generate_scaled")
 
 
 # ---- views of library-owned device arrays --------------------------------
