@@ -117,6 +117,12 @@ const char *fe_last_cuda_error(void);
  * incomplete. */
 int fe_device_status(fe_ctx *ctx, void *stream);
 
+/* HBM calibration (not part of the method): stream n doubles of device
+ * memory `src` (16-byte aligned) on `stream`, read only (dst = NULL) or copied
+ * into dst.  Callers time it to get the read-only and copy bandwidth that
+ * bound a read-dominated or a balanced kernel. */
+int fe_hbm_probe(fe_ctx *ctx, const double *src, double *dst, int64_t n, void *stream);
+
 /* Number of kernels this library has launched in this process so far (all
  * contexts and threads); a caller brackets a region with two reads to count
  * the launches inside it. */
@@ -126,8 +132,9 @@ uint64_t fe_kernel_launches(void);
  * Kernel and launch-shape choices of the numeric phase, per context.  0 means
  * the library's default; an autotuner may set them.  Results do not depend on
  * them (FE_DETERMINISTIC stays bit-identical), only speed does. */
-#define FE_KNOB_GATHER_KERNEL 0  /* FE_DETERMINISTIC: 1 register-batched row gather,
-                                    2 shared-memory-staged row gather        */
+#define FE_KNOB_GATHER_KERNEL 0  /* FE_DETERMINISTIC: 1 register-batched row gather
+                                    (default), 2 shared-memory-staged row
+                                    gather, 3 pipelined staged gather        */
 #define FE_KNOB_GATHER_BATCH 1   /* incidences per register batch: 4 or 8   */
 #define FE_KNOB_GATHER_WARPS 2   /* warps per block of the gather: 1..8      */
 #define FE_KNOB_ATOMIC_KERNEL 3  /* FE_ATOMIC: 1 register warp-per-element,

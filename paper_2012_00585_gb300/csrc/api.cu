@@ -85,6 +85,28 @@ __global__ void k_tile_scan(const T *__restrict__ in, int64_t *__restrict__ out,
 
 __global__ void k_set_zero_i64(int64_t *p) { *p = 0; }
 
+// HBM calibration: stream n doubles (read only, or copy to dst), 8
+// independent 16-byte accesses in flight per thread.
+__global__ void k_hbm_probe(const double2 *__restrict__ src, double2 *__restrict__ dst, int64_t n2, double *sink)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += 8 * stride) {
+        double2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = i + u * stride < n2 ? __ldcs(src + i + u * stride) : make_double2(0.0, 0.0);
+        if (dst) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i + u * stride < n2) __stcs(dst + i + u * stride, v[u]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += v[u].x + v[u].y;
+        }
+    }
+    if (s == 1.2345e300) *sink = s;  // keeps the loads alive
+}
+
 template <typename T>
 int scan_impl(fe_ctx *ctx, const T *in, int64_t *out, int64_t n, cudaStream_t s)
 {
@@ -254,7 +276,7 @@ int fe_tune_set(fe_ctx *ctx, int knob, int value)
     if (!ctx || knob < 0 || knob >= FE_KNOB_COUNT) return FE_ERR_INVALID_ARG;
     int lo = 0, hi = 0;
     switch (knob) {
-    case FE_KNOB_GATHER_KERNEL: hi = 2; break;
+    case FE_KNOB_GATHER_KERNEL: hi = 3; break;
     case FE_KNOB_GATHER_BATCH: hi = 8; break;
     case FE_KNOB_GATHER_WARPS: hi = 8; break;
     case FE_KNOB_ATOMIC_KERNEL: hi = 2; break;
@@ -271,6 +293,17 @@ int fe_tune_get(const fe_ctx *ctx, int knob, int *value)
 {
     if (!ctx || !value || knob < 0 || knob >= FE_KNOB_COUNT) return FE_ERR_INVALID_ARG;
     *value = ctx->knob[knob];
+    return FE_OK;
+}
+
+int fe_hbm_probe(fe_ctx *ctx, const double *src, double *dst, int64_t n, void *stream)
+{
+    if (!ctx || !src || n < 2 || ((uintptr_t)src & 15u) || ((uintptr_t)dst & 15u)) return FE_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    k_hbm_probe<<<ctx->num_sms * 8, 256, 0, s>>>((const double2 *)src, (double2 *)dst, n / 2, (double *)ctx->d_status + 1);
+    fe_note_launch();
+    FE_CUDA(cudaGetLastError());
     return FE_OK;
 }
 

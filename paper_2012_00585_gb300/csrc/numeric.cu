@@ -437,6 +437,170 @@ __global__ void __launch_bounds__(128) k_gather_async(const double *__restrict__
     cp_async_wait<0>();
 }
 
+__host__ __device__ inline size_t pipe_warp_bytes(int chk, int cap)
+{
+    const size_t b = ((size_t)2 * GATHER_UMAX * chk + (size_t)cap) * 8 + (size_t)2 * GATHER_UMAX * 8;
+    return (b + 127) & ~(size_t)127;
+}
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(fe_smem_u32(dst)), "l"(src) : "memory");
+}
+
+// Row gather as a software pipeline over the rows of a warp (stride W):
+//   iteration i issues the K slices (and 8-byte CSR map rows) of row v+W by
+//   per-lane asynchronous copies, loads the incidence ids of row v+2W and the
+//   adjacency pointers of row v+3W, then reduces row v from shared memory.
+// No dependent global load stays on the critical path of a row.
+template <int NLN, int BB, typename MT, bool CRAC>
+__global__ void __launch_bounds__(128) k_gather_pipe(const double *__restrict__ K, int64_t n_nodes, Geo g,
+                                                     const MT *__restrict__ map, const MT *__restrict__ mapc, int cap,
+                                                     int accumulate, double *values)
+{
+    constexpr int NLOC = NLN * BB;
+    constexpr int NN = NLOC * NLOC;
+    constexpr int CHK = BB * NLOC;
+    constexpr int IT = (CHK + 31) / 32;
+    constexpr int Q16 = CHK / 2;
+    constexpr int STAGE = GATHER_UMAX * CHK;
+    constexpr bool MAPSTAGE = !CRAC && NLN * sizeof(MT) == 8;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    double *kst = (double *)(smem_raw + (size_t)(threadIdx.x >> 5) * pipe_warp_bytes(CHK, cap));
+    uint64_t *mst = (uint64_t *)(kst + 2 * STAGE);  // [2][GATHER_UMAX] map rows
+    double *acc = (double *)(mst + 2 * GATHER_UMAX);
+    int jr_[IT], c_[IT], ku[IT], offu[IT];
+#pragma unroll
+    for (int j = 0; j < IT; ++j) {
+        const int q = lane + 32 * j;
+        const int qq = q < CHK ? q : 0;
+        jr_[j] = qq / NLOC;
+        c_[j] = qq % NLOC;
+        ku[j] = 0;
+        offu[j] = 0;
+        if (CRAC && g.uniform_R) run_of(g.run_mask[0], c_[j] / BB, ku[j], offu[j]);
+    }
+    const int64_t W = fe_warps();
+    auto nstaged = [&](int64_t a, int64_t b) { return (int)min((int64_t)GATHER_UMAX, b - a); };
+    // copy the staged slices of a row (ids held by lanes 0..n-1) into stage st
+    auto issue = [&](uint32_t t_l, int n, int st) {
+        for (int base = 0; base < n * Q16; base += 32) {
+            const int idx = base + lane;
+            const bool valid = idx < n * Q16;
+            const int u = valid ? idx / Q16 : 0, off = idx - u * Q16;
+            const uint32_t t = __shfl_sync(0xffffffffu, t_l, u);
+            const uint32_t e = t / NLN;
+            const uint32_t kr = t - e * NLN;
+            if (valid)
+                cp_async16(kst + st * STAGE + u * CHK + 2 * off, K + (int64_t)e * NN + (int64_t)kr * CHK + 2 * off);
+        }
+        if (MAPSTAGE && lane < n) cp_async8(mst + st * GATHER_UMAX + lane, map + (int64_t)t_l * NLN);
+        cp_async_commit();
+    };
+    int64_t v = fe_warp_id();
+    if (v >= n_nodes) return;
+    // prologue: row v (ids + copies), row v+W (ids), row v+2W (pointers)
+    int64_t a0 = g.adj_ptr[v], b0 = g.adj_ptr[v + 1];
+    int n0 = nstaged(a0, b0);
+    uint32_t t0 = lane < n0 ? g.adj[a0 + lane] : 0u;
+    issue(t0, n0, 0);
+    int64_t a1 = 0, b1 = 0, a2 = 0, b2 = 0;
+    uint32_t t1 = 0;
+    if (v + W < n_nodes) {
+        a1 = g.adj_ptr[v + W];
+        b1 = g.adj_ptr[v + W + 1];
+        t1 = lane < nstaged(a1, b1) ? g.adj[a1 + lane] : 0u;
+    }
+    if (v + 2 * W < n_nodes) {
+        a2 = g.adj_ptr[v + 2 * W];
+        b2 = g.adj_ptr[v + 2 * W + 1];
+    }
+    int st = 0;
+    while (v < n_nodes) {
+        // next row's copies, then the geometry two and three rows ahead
+        const int n1 = v + W < n_nodes ? nstaged(a1, b1) : 0;
+        issue(t1, n1, st ^ 1);
+        const int n2 = v + 2 * W < n_nodes ? nstaged(a2, b2) : 0;
+        const uint32_t t2 = lane < n2 ? g.adj[a2 + lane] : 0u;
+        int64_t a3 = 0, b3 = 0;
+        if (v + 3 * W < n_nodes) {
+            a3 = g.adj_ptr[v + 3 * W];
+            b3 = g.adj_ptr[v + 3 * W + 1];
+        }
+        const int64_t i0 = (int64_t)BB * v;
+        int64_t rb, RL;
+        if (!CRAC) {
+            rb = g.row_ptr[i0];
+            RL = g.row_ptr[i0 + 1] - rb;
+        } else {
+            rb = crac_row_base(g, i0);
+            RL = crac_row_base(g, i0 + 1) - rb;
+        }
+        const int total = (int)(BB * RL);
+        for (int k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
+        cp_async_wait<1>();  // row v's copies have landed
+        __syncwarp();
+        const double *stg = kst + st * STAGE;
+        for (int s = 0; s < (int)(b0 - a0); ++s) {
+            const bool staged = s < n0;
+            const uint32_t t = staged ? __shfl_sync(0xffffffffu, t0, s) : g.adj[a0 + s];
+            const uint32_t e = t / NLN;
+            const int kr = (int)(t - e * NLN);
+            const double *src = staged ? stg + s * CHK : K + (int64_t)e * NN + (int64_t)kr * CHK;
+            uint64_t mrow = 0;
+            if (MAPSTAGE) mrow = staged ? mst[st * GATHER_UMAX + s] : *(const uint64_t *)(map + (int64_t)t * NLN);
+            int64_t rp = 0;
+            int nr = 0;
+            uint32_t m = 0;
+            if (CRAC) {
+                if (g.uniform_R) {
+                    nr = g.uniform_R;
+                    rp = (int64_t)e * nr;
+                } else {
+                    rp = g.run_ptr[e];
+                    nr = (int)(g.run_ptr[e + 1] - rp);
+                    m = g.run_mask[e];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < IT; ++j) {
+                const int q = lane + 32 * j;
+                if (q < CHK) {
+                    const int kc = c_[j] / BB;
+                    int pos;
+                    if (MAPSTAGE) {
+                        pos = (int)((mrow >> (8 * sizeof(MT) * kc)) & ((1ull << (8 * sizeof(MT))) - 1));
+                    } else if (!CRAC) {
+                        pos = (int)map[(int64_t)t * NLN + kc];
+                    } else {
+                        int k = ku[j], off = offu[j];
+                        if (!g.uniform_R) run_of(m, kc, k, off);
+                        pos = (int)mapc[rp * NLN + (int64_t)kr * nr + k] + off;
+                    }
+                    acc[jr_[j] * (int)RL + BB * pos + c_[j] % BB] += staged ? src[q] : __ldcs(src + q);
+                }
+            }
+            __syncwarp();
+        }
+        for (int k = lane; k < total; k += 32) values[rb + k] = acc[k];
+        __syncwarp();
+        // rotate the pipeline
+        v += W;
+        st ^= 1;
+        a0 = a1;
+        b0 = b1;
+        n0 = n1;
+        t0 = t1;
+        a1 = a2;
+        b1 = b2;
+        t1 = t2;
+        a2 = a3;
+        b2 = b3;
+    }
+    cp_async_wait<0>();
+}
+
 __host__ __device__ inline size_t atomic_warp_bytes(int nn, int nloc, int nln)
 {
     const size_t b = (size_t)2 * nn * 8 + (size_t)nloc * 8 + (size_t)nln * nln * 4 + 2 * (size_t)nln * 4 + 24;
@@ -616,6 +780,21 @@ int launch_gather(const fe_pattern *p, const double *K, double *values, int accu
     int W = ctx->knob[FE_KNOB_GATHER_WARPS];
     if constexpr (NLN > 0) {
         constexpr int CHK = BB * NLN * BB;
+        if (kind == 3 && tma_ok(p, K, CHK)) {
+            if (W <= 0 || W > 4) W = 4;
+            const size_t psmem = (size_t)W * pipe_warp_bytes(CHK, cap);
+            if (psmem <= 200 * 1024) {
+                FE_TRY(configure_smem(k_gather_pipe<NLN, BB, MT, CRAC>, psmem));
+                int pgrid;
+                FE_TRY(grid_by_occupancy(k_gather_pipe<NLN, BB, MT, CRAC>, W * 32, psmem, sms, p->n_nodes, &pgrid));
+                k_gather_pipe<NLN, BB, MT, CRAC><<<pgrid, W * 32, psmem, s>>>(
+                    K, p->n_nodes, g, (const MT *)p->map_csr, (const MT *)p->map_crac, cap, accumulate, values);
+                fe_note_launch();
+                FE_CUDA(cudaGetLastError());
+                return FE_OK;
+            }
+            W = ctx->knob[FE_KNOB_GATHER_WARPS];
+        }
         if (kind == 2 && tma_ok(p, K, CHK)) {
             if (W <= 0 || W > 4) W = 4;  // launch bound of the staged kernel: 128 threads
             const size_t tsmem = (size_t)W * gather_warp_bytes(CHK, cap);
@@ -631,7 +810,7 @@ int launch_gather(const fe_pattern *p, const double *K, double *values, int accu
             }
         }
     }
-    if (W <= 0) W = 8;
+    if (W <= 0) W = 2;  // fastest in sweeps of 1..8 warps per block on the 64^3 elasticity mesh
     while (W > 1 && (size_t)W * cap * 8 > 64 * 1024) W >>= 1;
     const size_t smem = (size_t)W * cap * 8;
     if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;

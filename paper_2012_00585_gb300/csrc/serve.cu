@@ -157,6 +157,7 @@ void finish(fe_server *sv, Ticket &t, int status)
     t.state = status == FE_OK ? FE_STATE_DONE : FE_STATE_FAILED;
     t.t_done = now_us();
     if (status == FE_OK) ++sv->stats.completed; else ++sv->stats.failed;
+    sv->cv_done.notify_all();
 }
 
 // Admission, launches and completions; runs on the scheduler thread.
@@ -533,8 +534,11 @@ int fe_wait(fe_server *sv, uint64_t ticket, double timeout_s, fe_result *out)
             return FE_OK;
         }
         if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
-            fill_result(it->second, out);
-            return FE_ERR_TIMEOUT;
+            auto again = sv->tickets.find(ticket);
+            if (again == sv->tickets.end()) return FE_ERR_NOT_FOUND;
+            fill_result(again->second, out);
+            const int s2 = again->second.state;
+            return (s2 == FE_STATE_DONE || s2 == FE_STATE_FAILED || s2 == FE_STATE_CANCELLED) ? FE_OK : FE_ERR_TIMEOUT;
         }
     }
 }

@@ -145,6 +145,7 @@ def load():
             "fe_kernel_launches": (ctypes.c_uint64, []),
             "fe_device_status": (i, [vp, vp]),
             "fe_tune_set": (i, [vp, i, i]),
+            "fe_hbm_probe": (i, [vp, vp, vp, i64, vp]),
             "fe_tune_get": (i, [vp, i, ctypes.POINTER(i)]),
             "fe_pattern_build": (i, [vp, i64, i32, i64, vp, u32, vp, pp]),
             "fe_pattern_free": (i, [vp]),
@@ -224,6 +225,11 @@ def fe_kernel_launches() -> int:
 def fe_device_status(ctx, stream=None) -> int:
     """First error recorded by a kernel since the last call (0 = none); clears it."""
     return int(load().fe_device_status(ctx, _stream(stream)))
+
+
+def fe_hbm_probe(ctx, src, dst=None, n=None, stream=None):
+    n = src.numel() if n is None else n
+    _check(load().fe_hbm_probe(ctx, _addr(src), _addr(dst), int(n), _stream(stream)), "fe_hbm_probe")
 
 
 def fe_tune_set(ctx, knob: int, value: int):

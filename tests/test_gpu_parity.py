@@ -360,3 +360,29 @@ def test_c3_full_size_sampled_rows(ctx):
     del Kd
     torch.cuda.empty_cache()
     g.free()
+
+
+@pytest.mark.parametrize("gkind", [1, 2, 3])
+@pytest.mark.parametrize("akind", [1, 2])
+def test_every_kernel_variant(ctx, gkind, akind):
+    """Each schedule knob value gives the same results: deterministic
+    variants bit-exact, atomic variants within the row tolerance; meshes with
+    rows of more than 8 incidences (tets) exercise the unstaged remainder."""
+    from paper_2012_00585_gb300 import feasm
+    feasm.fe_tune_set(ctx, feasm.FE_KNOB_GATHER_KERNEL, gkind)
+    feasm.fe_tune_set(ctx, feasm.FE_KNOB_ATOMIC_KERNEL, akind)
+    try:
+        for D, n_dofs, K in [
+            (*wl.hex_q1_grid(5, 3), None),
+            (*wl.tet_p2_kuhn(3, d=3, seed=8), None),
+            (*wl.hex_q1_grid(6, 1), None),
+            (*wl.quad_q1_grid(9, 2), None),
+        ]:
+            K = wl.random_matrices(D.shape[0], D.shape[1], seed=gkind * 10 + akind)
+            g = gu.GpuAssembly(ctx, D, n_dofs)
+            pat = _check_pattern(g, D, n_dofs)
+            _run_all_modes(g, D, K, n_dofs, *pat)
+            g.free()
+    finally:
+        feasm.fe_tune_set(ctx, feasm.FE_KNOB_GATHER_KERNEL, 0)
+        feasm.fe_tune_set(ctx, feasm.FE_KNOB_ATOMIC_KERNEL, 0)
