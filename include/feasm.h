@@ -68,6 +68,11 @@ extern "C" {
 #define FE_DETERMINISTIC 1  /* row-parallel gather, no atomics; every value is
                                summed in ascending element order from +0.0
                                (Listing 2's order), bit-reproducible          */
+#define FE_COLOURED 2       /* colour after colour, elements of one colour in
+                               parallel with plain adds (Listing 6); needs
+                               fe_pattern_colour; every value is summed in
+                               colour order (ascending element within a
+                               colour), bit-reproducible                      */
 
 typedef struct fe_ctx fe_ctx;
 typedef struct fe_pattern fe_pattern;
@@ -230,6 +235,20 @@ int fe_pattern_crac(const fe_pattern *pattern, const int64_t **row_ptr, const in
  * row) adjacency.  Always built. */
 int fe_pattern_adjacency(const fe_pattern *pattern, int32_t *block, const int64_t **adj_ptr,
                          const uint32_t **adj);
+
+/*
+ * Greedy colouring of the elements (the colouring of Listing 6): elements in
+ * ascending order each take the smallest colour not used by an earlier
+ * element sharing a DOF, so that elements of one colour share no DOF.
+ * Computed on the device in dependency waves; the result equals the
+ * sequential first-fit colouring.  Enables mode FE_COLOURED.  Synchronous on
+ * `stream`.  *n_colours (may be NULL) receives the number of colours.
+ * FE_ERR_UNSUPPORTED beyond 256 colours.
+ */
+int fe_pattern_colour(fe_ctx *ctx, fe_pattern *pattern, void *stream, int32_t *n_colours);
+
+/* Borrowed device pointer to the colours, int32 [n_elem]. */
+int fe_pattern_colours(const fe_pattern *pattern, int32_t *n_colours, const int32_t **colour);
 
 /* Sizes and parts of a pattern. */
 int fe_pattern_info_get(const fe_pattern *pattern, fe_pattern_info *out);

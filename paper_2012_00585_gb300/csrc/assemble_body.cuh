@@ -54,8 +54,10 @@ inline Geo geo_of(const fe_pattern *p)
 }
 
 // One element of NLN blocks of BB DOFs (NLN*BB <= 32), the warp cooperating:
-// every entry of K_e is added into its slot with one FP64 atomic add.
-template <int NLN, int BB, typename MT, bool CRAC>
+// every entry of K_e is added into its slot with one FP64 atomic add, or with
+// a plain read-modify-write when PLAIN (no other element touching the same
+// slots runs concurrently, as within one colour).
+template <int NLN, int BB, typename MT, bool CRAC, bool PLAIN = false>
 __device__ __forceinline__ void atomic_element(const double *__restrict__ K, int64_t e, const Geo &g,
                                                const MT *__restrict__ map, const MT *__restrict__ mapc,
                                                double *values, int lane)
@@ -110,7 +112,11 @@ __device__ __forceinline__ void atomic_element(const double *__restrict__ K, int
                     const int off = __shfl_sync(0xffffffffu, koff, kc);
                     pos = (int)mapc[rp * NLN + (r / BB) * nr + k] + off;
                 }
-                if (q < NN) atomicAdd(values + b + (int64_t)BB * pos + c % BB, kv[u]);
+                if (q < NN) {
+                    double *dst = values + b + (int64_t)BB * pos + c % BB;
+                    if (PLAIN) *dst = *dst + kv[u];
+                    else atomicAdd(dst, kv[u]);
+                }
             }
         }
     }
@@ -118,7 +124,7 @@ __device__ __forceinline__ void atomic_element(const double *__restrict__ K, int
 
 // Any element size, the warp cooperating; base_s / k_s / off_s are this
 // warp's shared tables of at least n_loc and nln entries.
-template <typename MT, bool CRAC>
+template <typename MT, bool CRAC, bool PLAIN = false>
 __device__ __forceinline__ void atomic_element_generic(const double *__restrict__ K, int64_t e, int32_t nln,
                                                        int32_t B, const Geo &g, const MT *__restrict__ map,
                                                        const MT *__restrict__ mapc, double *values, int64_t *base_s,
@@ -146,7 +152,9 @@ __device__ __forceinline__ void atomic_element_generic(const double *__restrict_
         int pos;
         if (!CRAC) pos = (int)map[(e * nln + r / B) * nln + kc];
         else pos = (int)mapc[rp * nln + (int64_t)(r / B) * nr + k_s[kc]] + off_s[kc];
-        atomicAdd(values + base_s[r] + (int64_t)B * pos + c % B, __ldcs(Ke + q));
+        double *dst = values + base_s[r] + (int64_t)B * pos + c % B;
+        if (PLAIN) *dst = *dst + __ldcs(Ke + q);
+        else atomicAdd(dst, __ldcs(Ke + q));
     }
     __syncwarp();
 }

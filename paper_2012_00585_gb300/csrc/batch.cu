@@ -385,7 +385,7 @@ std::tuple<int, int, uint64_t, int> signature(const fe_batch_item *items, int n,
 
 fe_schedule default_schedule(int mode)
 {
-    return mode == FE_DETERMINISTIC ? fe_schedule{FE_SCHED_WARP_PER_ROW, 16} : fe_schedule{FE_SCHED_WARP_PER_ELEMENT, 16};
+    return mode == FE_DETERMINISTIC ? fe_schedule{FE_SCHED_WARP_PER_ROW, 64} : fe_schedule{FE_SCHED_WARP_PER_ELEMENT, 64};
 }
 
 struct DeviceScope {
@@ -471,12 +471,14 @@ int fe_batch_autotune(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, 
     DeviceScope ds(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<fe_schedule> cands;
+    // one atomic tile fetch per warp (or block) per tile: larger tiles mean
+    // fewer same-address atomics on the work counter
     if (mode == FE_DETERMINISTIC) {
-        for (int t : {1, 4, 16, 64}) cands.push_back({FE_SCHED_WARP_PER_ROW, t});
+        for (int t : {4, 16, 64, 256, 1024}) cands.push_back({FE_SCHED_WARP_PER_ROW, t});
     } else {
-        for (int t : {1, 4, 16, 64}) cands.push_back({FE_SCHED_WARP_PER_ELEMENT, t});
-        for (int t : {1, 4}) cands.push_back({FE_SCHED_THREAD_PER_ENTRY, t});
-        for (int t : {1, 4}) cands.push_back({FE_SCHED_BLOCK_PER_ELEMENT, t});
+        for (int t : {4, 16, 64, 256, 1024}) cands.push_back({FE_SCHED_WARP_PER_ELEMENT, t});
+        for (int t : {4, 32}) cands.push_back({FE_SCHED_THREAD_PER_ENTRY, t});
+        for (int t : {1, 8}) cands.push_back({FE_SCHED_BLOCK_PER_ELEMENT, t});
     }
     cudaEvent_t e0, e1;
     FE_CUDA(cudaEventCreate(&e0));

@@ -76,7 +76,12 @@ struct fe_pattern {
     uint32_t *run_mask = nullptr;  // [n_e * mask_words] run starts over the element's blocks
     int64_t *run_ptr = nullptr;    // [n_e + 1]
     void *map_crac = nullptr;      // [n_runs * nln] uint8/uint16: run start position in block row
+    struct fe_colouring *colouring = nullptr;  // greedy element colouring (fe_pattern_colour)
 };
+
+void fe_colouring_free(fe_pattern *p, cudaStream_t s);
+int fe_assemble_coloured(const fe_pattern *p, const double *K, double *values, int accumulate, bool crac,
+                         cudaStream_t s);
 
 void fe_batch_state_destroy(fe_ctx *ctx);
 

@@ -41,6 +41,36 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
+// Combine one value per warp into one atomic per block (same-address
+// atomics from every warp serialise in L2).
+__device__ __forceinline__ void block_and_atomic(uint32_t v, unsigned long long *dst)
+{
+    __shared__ uint32_t red[32];
+    v = __reduce_and_sync(0xffffffffu, v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t x = 0xffffffffu;
+        for (int k = 0; k < nw; ++k) x &= red[k];
+        if (x != 0xffffffffu) atomicAnd(dst, (unsigned long long)x);
+    }
+}
+
+__device__ __forceinline__ void block_max_atomic(int v, int64_t *dst)
+{
+    __shared__ int red[32];
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int x = 0;
+        for (int k = 0; k < nw; ++k) x = max(x, red[k]);
+        if (x > 0) atomicMax((long long *)dst, (long long)x);
+    }
+}
+
 // ---------------------------------------------------------------- A1 ---
 // Block-size test for one compile-time b: every aligned group of b local
 // DOFs must be b consecutive indices starting at a multiple of b.
@@ -53,20 +83,20 @@ __device__ __forceinline__ void block_test(uint32_t cand, int c, int32_t d, bool
     }
 }
 
-template <int... Bs>
-__device__ __forceinline__ void block_tests(uint32_t cand, int c, int32_t d, bool is_start, bool valid, uint32_t &ok,
-                                            std::integer_sequence<int, Bs...>)
+// Any other block size (runtime b, kept out of line).
+__device__ __noinline__ uint32_t block_test_rt(int b, int c, int32_t d, bool is_start, bool valid)
 {
-    (block_test<Bs + 2>(cand, c, d, is_start, valid, ok), ...);
+    const bool good = (c % b == 0) ? ((uint32_t)d % (uint32_t)b == 0) : !is_start;
+    return (valid && !good) ? ~(1u << (b - 1)) : 0xffffffffu;
 }
 
 // One warp per element: DOF range, repeated DOFs (by warp shuffles), and the
 // candidate block sizes b (bit b-1 of `cand`, the divisors of n_loc) for
 // which the element lists whole aligned blocks.
-__global__ void k_validate(const int32_t *__restrict__ D, int64_t n_e, int32_t n_loc, int64_t n_dofs, uint32_t cand,
-                           int64_t *sc)
+template <int MAXW>
+__global__ void __launch_bounds__(256) k_validate(const int32_t *__restrict__ D, int64_t n_e, int32_t n_loc,
+                                                  int64_t n_dofs, uint32_t cand, int64_t *sc)
 {
-    constexpr int MAXW = FE_MAX_NLOC / 32;
     const int lane = threadIdx.x & 31;
     uint32_t blocks_all = 0xffffffffu;
     bool bad_range = false, dup = false;
@@ -87,24 +117,39 @@ __global__ void k_validate(const int32_t *__restrict__ D, int64_t n_e, int32_t n
             const bool valid = c < n_loc;
             const int32_t d = dv[w];
             if (valid && (d < 0 || (int64_t)d >= n_dofs)) bad_range = true;
-            // repeats: compare with every earlier local DOF
+            // repeats: lanes holding the same DOF (one word), else compare
+            // with every earlier local DOF
+            if (nw == 1) {
+                const unsigned same = __match_any_sync(0xffffffffu, d);
+                if (valid && __popc(same) > 1) dup = true;
+            } else {
 #pragma unroll
-            for (int w2 = 0; w2 <= w; ++w2) {
-                for (int k = 0; k < 32; ++k) {
-                    const int32_t o = __shfl_sync(0xffffffffu, dv[w2], k);
-                    if (valid && 32 * w2 + k < c && o == d) dup = true;
+                for (int w2 = 0; w2 <= w; ++w2) {
+                    for (int k = 0; k < 32; ++k) {
+                        const int32_t o = __shfl_sync(0xffffffffu, dv[w2], k);
+                        if (valid && 32 * w2 + k < c && o == d) dup = true;
+                    }
                 }
             }
             int32_t prev = __shfl_up_sync(0xffffffffu, d, 1);
             const int32_t last_prev_word = w > 0 ? __shfl_sync(0xffffffffu, dv[w > 0 ? w - 1 : 0], 31) : 0;
             if (lane == 0) prev = last_prev_word;
             const bool is_start = c == 0 || (int64_t)d != (int64_t)prev + 1;
-            block_tests(cand, c, d, is_start, valid, ok, std::make_integer_sequence<int, 31>{});
+            for (uint32_t m = cand; m; m &= m - 1) {  // only the candidate sizes
+                switch (__ffs(m)) {
+                case 2: block_test<2>(cand, c, d, is_start, valid, ok); break;
+                case 3: block_test<3>(cand, c, d, is_start, valid, ok); break;
+                case 4: block_test<4>(cand, c, d, is_start, valid, ok); break;
+                case 5: block_test<5>(cand, c, d, is_start, valid, ok); break;
+                case 6: block_test<6>(cand, c, d, is_start, valid, ok); break;
+                case 8: block_test<8>(cand, c, d, is_start, valid, ok); break;
+                default: ok &= block_test_rt(__ffs(m), c, d, is_start, valid);
+                }
+            }
         }
         blocks_all &= ok;
     }
-    blocks_all = __reduce_and_sync(0xffffffffu, blocks_all);
-    if (lane == 0 && blocks_all != 0xffffffffu) atomicAnd((unsigned long long *)&sc[S_BLOCKS], (unsigned long long)blocks_all);
+    block_and_atomic(blocks_all, (unsigned long long *)&sc[S_BLOCKS]);
     if (bad_range) set_err(sc, FE_ERR_DOF_RANGE);
     if (dup) set_err(sc, FE_ERR_DUP_DOF);
 }
@@ -152,8 +197,7 @@ __global__ void k_max_i32(const int32_t *__restrict__ x, int64_t n, int64_t *out
     int32_t m = 0;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
         m = max(m, x[t]);
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax((long long *)out, (long long)m);
+    block_max_atomic(m, out);
 }
 
 __global__ void k_fill_adj(const int32_t *__restrict__ N, int64_t n_inc, int64_t n_nodes,
@@ -252,6 +296,7 @@ __global__ void __launch_bounds__(256) k_row_keys(const int32_t *__restrict__ N,
                                                   int64_t *sc)
 {
     const int lane = threadIdx.x & 31;
+    int row_max = 0;
     for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
         const int64_t a = adj_ptr[v];
         const int n = (int)(adj_ptr[v + 1] - a) * nln;
@@ -297,9 +342,10 @@ __global__ void __launch_bounds__(256) k_row_keys(const int32_t *__restrict__ N,
         if (lane == 31) {
             node_len[v] = ik;
             node_runs2[v] = 2 * ir;
-            atomicMax((long long *)&sc[S_MAX_NODE], (long long)ik);
         }
+        row_max = max(row_max, __shfl_sync(0xffffffffu, ik, 31));
     }
+    block_max_atomic(row_max, &sc[S_MAX_NODE]);
 }
 
 // Rows with more than 256 candidates: the same with a bitonic sort in shared
@@ -312,6 +358,7 @@ __global__ void k_row_keys_smem(const int32_t *__restrict__ N, int32_t nln, int6
     extern __shared__ int32_t sbuf[];
     const int lane = threadIdx.x & 31;
     int32_t *buf = sbuf + (size_t)(threadIdx.x >> 5) * P;
+    int row_max = 0;
     for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
         const int64_t a = adj_ptr[v];
         const int n = (int)(adj_ptr[v + 1] - a) * nln;
@@ -346,29 +393,40 @@ __global__ void k_row_keys_smem(const int32_t *__restrict__ N, int32_t nln, int6
         if (lane == 0) {
             node_len[v] = L;
             node_runs2[v] = 2 * R;
-            atomicMax((long long *)&sc[S_MAX_NODE], (long long)L);
         }
+        row_max = max(row_max, L);
         __syncwarp();
     }
+    block_max_atomic(row_max, &sc[S_MAX_NODE]);
 }
 
 // One warp per node row v: the B DOF rows B*v+j get
 //   row_ptr  = B^2 * nrp[v] + j*B*L_v,   col_idx = B*key + comp (coalesced),
 //   crac_ptr = B * ncp[v] + j*2*R_v,     pairs (B*first key of a run, value position)
 // where nrp / ncp are the node-level scans of L and 2R.
-__global__ void __launch_bounds__(256) k_expand(int64_t n_nodes, int32_t B, int32_t nln,
+template <int BT>
+__global__ void __launch_bounds__(256) k_expand(int64_t n_nodes, int32_t B_rt, int32_t nln,
                                                 const int64_t *__restrict__ adj_ptr,
                                                 const int32_t *__restrict__ keys, const int32_t *__restrict__ node_len,
                                                 const int32_t *__restrict__ node_runs2,
                                                 const int64_t *__restrict__ nrp, const int64_t *__restrict__ ncp,
                                                 int64_t *__restrict__ row_ptr, int64_t *__restrict__ crac_ptr,
-                                                int32_t *__restrict__ col_idx, int32_t *__restrict__ col_align)
+                                                int32_t *__restrict__ col_idx, int32_t *__restrict__ col_align, int cap)
 {
+    extern __shared__ int32_t kbuf[];
+    const int B = BT > 0 ? BT : B_rt;  // compile-time block size for the common cases
     const int lane = threadIdx.x & 31;
+    int32_t *ks = kbuf + (size_t)(threadIdx.x >> 5) * cap;
     for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
         const int L = node_len[v];
         const int R2 = node_runs2[v];
-        const int32_t *kv = keys + adj_ptr[v] * nln;
+        const int32_t *kv_g = keys + adj_ptr[v] * nln;
+        const bool in_smem = L <= cap;
+        if (in_smem) {
+            for (int k = lane; k < L; k += 32) ks[k] = kv_g[k];
+            __syncwarp();
+        }
+        const int32_t *kv = in_smem ? ks : kv_g;
         const int64_t rb0 = (int64_t)B * B * nrp[v];
         const int64_t cb0 = (int64_t)B * ncp[v];
         for (int j = lane; j < B; j += 32) {
@@ -399,6 +457,7 @@ __global__ void __launch_bounds__(256) k_expand(int64_t n_nodes, int32_t B, int3
                 }
             }
         }
+        __syncwarp();
     }
 }
 
@@ -468,7 +527,7 @@ __global__ void k_map_runs(const int32_t *__restrict__ N, int32_t nln, int64_t n
                            const int64_t *__restrict__ adj_ptr, const uint32_t *__restrict__ adj,
                            const int64_t *__restrict__ crac_ptr, const int32_t *__restrict__ col_align,
                            const uint32_t *__restrict__ run_mask, const int64_t *__restrict__ run_ptr, int cap,
-                           MT *__restrict__ mapc, int64_t *sc)
+                           int rmax, MT *__restrict__ mapc, int64_t *sc)
 {
     extern __shared__ int32_t sbuf[];
     const int lane = threadIdx.x & 31;
@@ -486,17 +545,27 @@ __global__ void k_map_runs(const int32_t *__restrict__ N, int32_t nln, int64_t n
         }
         const int32_t row_base = ca[1];
         const int64_t a = adj_ptr[v], b = adj_ptr[v + 1];
-        const int total = (int)(b - a) * nln;
+        // (incidence, run) pairs over the lanes; rmax bounds the runs per element
+        const int total = (int)(b - a) * rmax;
         for (int q = lane; q < total; q += 32) {
-            const int s = q / nln;
-            const int kc = q - s * nln;
+            const int s = q / rmax;
+            const int ri = q - s * rmax;
             const uint32_t t = adj[a + s];
             const int64_t e = t / (uint32_t)nln;
             const int k = (int)(t - (uint32_t)(e * nln));
             const uint32_t *m = run_mask + e * mask_words;
-            if (!((m[kc >> 5] >> (kc & 31)) & 1u)) continue;  // not the first block of a run
-            int ri = __popc(m[kc >> 5] & ((1u << (kc & 31)) - 1u));
-            for (int w = 0; w < (kc >> 5); ++w) ri += __popc(m[w]);
+            // position of the ri-th set bit of the element's run-start mask
+            int kc = -1, seen = 0;
+            for (int w = 0; w < mask_words && kc < 0; ++w) {
+                uint32_t x = m[w];
+                const int cnt = __popc(x);
+                if (ri < seen + cnt) {
+                    for (int i = 0; i < ri - seen; ++i) x &= x - 1;  // drop the lower set bits
+                    kc = 32 * w + __ffs(x) - 1;
+                }
+                seen += cnt;
+            }
+            if (kc < 0) continue;  // the element has fewer runs
             const int64_t rp = run_ptr[e];
             const int nr = (int)(run_ptr[e + 1] - rp);
             const int32_t j = B * N[e * nln + kc];
@@ -530,6 +599,7 @@ struct Scratch {
 
 void pattern_release(fe_pattern *p, cudaStream_t s)
 {
+    fe_colouring_free(p, s);
     void *ptrs[] = {p->node_dofs, p->row_ptr, p->col_idx, p->crac_ptr, p->col_align, p->adj_ptr,
                     p->adj,       p->map_csr, p->run_mask, p->run_ptr, p->map_crac};
     for (void *x : ptrs) fe_free_async(x, s);
@@ -576,8 +646,12 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
         uint32_t cand = 0;  // block sizes that divide both n_loc and n_dofs
         for (int b = 2; b <= 32; ++b)
             if (n_loc % b == 0 && n_dofs % b == 0) cand |= 1u << (b - 1);
-        FE_LAUNCH((k_validate<<<fe_grid_for(n_e * 32, 256, sms, 16), 256, 0, s>>>(elem_dofs, n_e, n_loc, n_dofs, cand,
-                                                                               sc)));
+        if (n_loc <= 32)
+            FE_LAUNCH((k_validate<1><<<fe_grid_for(n_e * 32, 256, sms, 16), 256, 0, s>>>(elem_dofs, n_e, n_loc, n_dofs,
+                                                                                      cand, sc)));
+        else
+            FE_LAUNCH((k_validate<FE_MAX_NLOC / 32><<<fe_grid_for(n_e * 32, 256, sms, 16), 256, 0, s>>>(
+                elem_dofs, n_e, n_loc, n_dofs, cand, sc)));
         FE_CUDA(cudaGetLastError());
     }
     int64_t h1[S_COUNT];
@@ -698,10 +772,24 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
     FE_TRY(alloc_into(p, (void **)&p->crac_ptr, sizeof(int64_t) * (size_t)(n_dofs + 1), s));
     FE_TRY(alloc_into(p, (void **)&p->col_idx, sizeof(int32_t) * (size_t)(p->nnz + 1), s));
     FE_TRY(alloc_into(p, (void **)&p->col_align, sizeof(int32_t) * (size_t)p->n_ca, s));
-    if (n_nodes > 0)
-        FE_LAUNCH((k_expand<<<fe_grid_for(n_nodes * 32, 256, sms, 8), 256, 0, s>>>(
-            n_nodes, B, nln, p->adj_ptr, keys, node_len, node_runs2, nrp, ncp, p->row_ptr, p->crac_ptr, p->col_idx,
-            p->col_align)));
+    if (n_nodes > 0) {
+        const int kcap = std::max(1, std::min(p->max_node_len, 1024));
+        const size_t ksm = (size_t)8 * kcap * 4;
+        const int eg = fe_grid_for(n_nodes * 32, 256, sms, 8);
+        if (B == 3) {
+            FE_TRY(configure_smem(k_expand<3>, ksm));
+            FE_LAUNCH((k_expand<3><<<eg, 256, ksm, s>>>(n_nodes, B, nln, p->adj_ptr, keys, node_len, node_runs2, nrp,
+                                                        ncp, p->row_ptr, p->crac_ptr, p->col_idx, p->col_align, kcap)));
+        } else if (B == 1) {
+            FE_TRY(configure_smem(k_expand<1>, ksm));
+            FE_LAUNCH((k_expand<1><<<eg, 256, ksm, s>>>(n_nodes, B, nln, p->adj_ptr, keys, node_len, node_runs2, nrp,
+                                                        ncp, p->row_ptr, p->crac_ptr, p->col_idx, p->col_align, kcap)));
+        } else {
+            FE_TRY(configure_smem(k_expand<0>, ksm));
+            FE_LAUNCH((k_expand<0><<<eg, 256, ksm, s>>>(n_nodes, B, nln, p->adj_ptr, keys, node_len, node_runs2, nrp,
+                                                        ncp, p->row_ptr, p->crac_ptr, p->col_idx, p->col_align, kcap)));
+        }
+    }
     FE_LAUNCH((k_tail<<<1, 1, 0, s>>>(p->row_ptr, p->crac_ptr, nrp, ncp, n_nodes, n_dofs, B)));
     FE_LAUNCH((k_final_pair<<<1, 1, 0, s>>>(p->col_align, p->n_ca, n_dofs, p->nnz)));
     FE_CUDA(cudaGetLastError());
@@ -736,12 +824,12 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
                 FE_TRY(configure_smem(k_map_runs<uint8_t>, smem));
                 FE_LAUNCH((k_map_runs<uint8_t><<<fe_grid_for(n_nodes * 32, WM * 32, sms, 8), WM * 32, smem, s>>>(
                     p->node_dofs, nln, n_nodes, B, p->mask_words, p->adj_ptr, p->adj, p->crac_ptr, p->col_align,
-                    p->run_mask, p->run_ptr, cap, (uint8_t *)p->map_crac, sc)));
+                    p->run_mask, p->run_ptr, cap, p->uniform_runs ? p->runs_per_elem : nln, (uint8_t *)p->map_crac, sc)));
             } else {
                 FE_TRY(configure_smem(k_map_runs<uint16_t>, smem));
                 FE_LAUNCH((k_map_runs<uint16_t><<<fe_grid_for(n_nodes * 32, WM * 32, sms, 8), WM * 32, smem, s>>>(
                     p->node_dofs, nln, n_nodes, B, p->mask_words, p->adj_ptr, p->adj, p->crac_ptr, p->col_align,
-                    p->run_mask, p->run_ptr, cap, (uint16_t *)p->map_crac, sc)));
+                    p->run_mask, p->run_ptr, cap, p->uniform_runs ? p->runs_per_elem : nln, (uint16_t *)p->map_crac, sc)));
             }
             FE_CUDA(cudaGetLastError());
         }
@@ -1018,8 +1106,12 @@ int noalloc_impl(unsigned char *scratch, int64_t n_e, int32_t n_loc, int64_t n_d
         uint32_t cand = 0;
         for (int b = 2; b <= 32; ++b)
             if (n_loc % b == 0 && n_dofs % b == 0) cand |= 1u << (b - 1);
-        FE_LAUNCH((k_validate<<<fe_grid_for(n_e * 32, 256, sms, 16), 256, 0, s>>>(elem_dofs, n_e, n_loc, n_dofs, cand,
-                                                                               sc)));
+        if (n_loc <= 32)
+            FE_LAUNCH((k_validate<1><<<fe_grid_for(n_e * 32, 256, sms, 16), 256, 0, s>>>(elem_dofs, n_e, n_loc, n_dofs,
+                                                                                      cand, sc)));
+        else
+            FE_LAUNCH((k_validate<FE_MAX_NLOC / 32><<<fe_grid_for(n_e * 32, 256, sms, 16), 256, 0, s>>>(
+                elem_dofs, n_e, n_loc, n_dofs, cand, sc)));
         FE_CUDA(cudaGetLastError());
     }
     FE_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -1081,9 +1173,11 @@ int noalloc_impl(unsigned char *scratch, int64_t n_e, int32_t n_loc, int64_t n_d
     if (nnz_out) *nnz_out = nnz;
     if (nnz >= INT32_MAX) return FE_ERR_OVERFLOW;
     if (col_capacity < nnz) return FE_ERR_INVALID_ARG;  // *nnz_out tells the caller how much to provide
-    if (n_nodes > 0)
-        FE_LAUNCH((k_expand<<<fe_grid_for(n_nodes * 32, 256, sms, 8), 256, 0, s>>>(
-            n_nodes, B, nln, adj_ptr, keys, node_len, node_runs2, nrp, ncp, row_ptr, crac_ptr, col_idx, nullptr)));
+    if (n_nodes > 0) {
+        // rows longer than the staging capacity read their keys from global memory
+        FE_LAUNCH((k_expand<0><<<fe_grid_for(n_nodes * 32, 256, sms, 8), 256, (size_t)8 * 256 * 4, s>>>(
+            n_nodes, B, nln, adj_ptr, keys, node_len, node_runs2, nrp, ncp, row_ptr, crac_ptr, col_idx, nullptr, 256)));
+    }
     FE_LAUNCH((k_tail<<<1, 1, 0, s>>>(row_ptr, crac_ptr, nrp, ncp, n_nodes, n_dofs, B)));
     FE_CUDA(cudaGetLastError());
     FE_CUDA(cudaStreamSynchronize(s));

@@ -37,6 +37,7 @@ FE_PATTERN_ALL = 0x1F
 
 FE_ATOMIC = 0
 FE_DETERMINISTIC = 1
+FE_COLOURED = 2
 
 FE_KNOB_GATHER_KERNEL = 0
 FE_KNOB_GATHER_BATCH = 1
@@ -154,6 +155,8 @@ def load():
             "fe_pattern_crac": (i, [vp, pp, pp, ctypes.POINTER(i64)]),
             "fe_pattern_adjacency": (i, [vp, ctypes.POINTER(i32), pp, pp]),
             "fe_pattern_info_get": (i, [vp, ctypes.POINTER(fe_pattern_info)]),
+            "fe_pattern_colour": (i, [vp, vp, vp, ctypes.POINTER(i32)]),
+            "fe_pattern_colours": (i, [vp, ctypes.POINTER(i32), pp]),
             "fe_assemble_csr": (i, [vp, vp, vp, vp, i, i, vp]),
             "fe_assemble_crac": (i, [vp, vp, vp, vp, i, i, vp]),
             "fe_assemble_batch": (i, [vp, ctypes.POINTER(fe_batch_item), i32, i32, i32, i32,
@@ -306,6 +309,19 @@ def fe_pattern_info_get(pattern) -> dict:
     info = fe_pattern_info()
     _check(load().fe_pattern_info_get(pattern, ctypes.byref(info)), "fe_pattern_info_get")
     return {name: getattr(info, name) for name, _ in fe_pattern_info._fields_}
+
+
+def fe_pattern_colour(ctx, pattern, stream=None) -> int:
+    """Greedy first-fit element colouring on the device; returns the number of colours."""
+    n = ctypes.c_int32()
+    _check(load().fe_pattern_colour(ctx, pattern, _stream(stream), ctypes.byref(n)), "fe_pattern_colour")
+    return n.value
+
+
+def fe_pattern_colours(pattern):
+    n, c = ctypes.c_int32(), ctypes.c_void_p()
+    _check(load().fe_pattern_colours(pattern, ctypes.byref(n), ctypes.byref(c)), "fe_pattern_colours")
+    return n.value, c.value
 
 
 def fe_assemble_csr(ctx, pattern, elem_mats, values, mode=FE_ATOMIC, accumulate=0, stream=None):
