@@ -73,6 +73,14 @@ extern "C" {
                                fe_pattern_colour; every value is summed in
                                colour order (ascending element within a
                                colour), bit-reproducible                      */
+#define FE_ROWLOCK 3        /* element-parallel, each row of K_e added under
+                               the row's spin_int lock (Listings 3-5): the
+                               row pointer itself is the lock (locked value
+                               ~v), taken with a bounded spin; sum order
+                               unspecified.  The pattern's row pointers change
+                               while it runs: no other work on this pattern
+                               may run concurrently.  Elements of up to 32
+                               DOFs in blocks (4,1), (8,1), (8,3), (10,3).    */
 
 typedef struct fe_ctx fe_ctx;
 typedef struct fe_pattern fe_pattern;
@@ -281,6 +289,21 @@ int fe_assemble_csr(fe_ctx *ctx, const fe_pattern *pattern, const double *elem_m
  */
 int fe_assemble_crac(fe_ctx *ctx, const fe_pattern *pattern, const double *elem_mats,
                      double *values, int mode, int accumulate, void *stream);
+
+/* ---- consumers of the assembled matrix ----------------------------------- */
+
+/* y = G x over the CSR arrays (values in CSR order).  x device [n_dofs], y
+ * device [n_dofs].  One warp per row, fixed summation order (reproducible run
+ * to run; not the left-to-right order of a serial loop).  Asynchronous. */
+int fe_spmv_csr(fe_ctx *ctx, const fe_pattern *pattern, const double *values, const double *x, double *y,
+                void *stream);
+
+/* The same product through the CRAC arrays (§2.2): every run of consecutive
+ * columns multiplies a contiguous slice of values with a contiguous slice of
+ * x, so no column index is read per value (the CRAC SpMV of the paper's
+ * outlook).  Needs FE_PATTERN_CRAC. */
+int fe_spmv_crac(fe_ctx *ctx, const fe_pattern *pattern, const double *values, const double *x, double *y,
+                 void *stream);
 
 /* ---- batched assembly (many independent meshes, one launch) --------------
  * Not in the paper: a GPU runs thousands of small assemblies at once when

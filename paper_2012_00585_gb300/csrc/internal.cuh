@@ -82,6 +82,8 @@ struct fe_pattern {
 void fe_colouring_free(fe_pattern *p, cudaStream_t s);
 int fe_assemble_coloured(const fe_pattern *p, const double *K, double *values, int accumulate, bool crac,
                          cudaStream_t s);
+int fe_assemble_rowlock(const fe_pattern *p, const double *K, double *values, int accumulate, bool crac,
+                        cudaStream_t s);
 
 void fe_batch_state_destroy(fe_ctx *ctx);
 

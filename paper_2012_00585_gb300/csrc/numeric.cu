@@ -862,7 +862,8 @@ int assemble(fe_ctx *ctx, const fe_pattern *p, const double *K, double *values, 
              void *stream, bool crac)
 {
     if (!ctx || !p || p->ctx != ctx) return FE_ERR_INVALID_ARG;
-    if (mode != FE_ATOMIC && mode != FE_DETERMINISTIC && mode != FE_COLOURED) return FE_ERR_INVALID_ARG;
+    if (mode != FE_ATOMIC && mode != FE_DETERMINISTIC && mode != FE_COLOURED && mode != FE_ROWLOCK)
+        return FE_ERR_INVALID_ARG;
     if (accumulate != 0 && accumulate != 1) return FE_ERR_INVALID_ARG;
     if ((p->n_e > 0 && !K) || (p->nnz > 0 && !values)) return FE_ERR_INVALID_ARG;
     if (((uintptr_t)K & 7u) || ((uintptr_t)values & 7u)) return FE_ERR_INVALID_ARG;
@@ -874,8 +875,9 @@ int assemble(fe_ctx *ctx, const fe_pattern *p, const double *K, double *values, 
     if (prev != ctx->device) cudaSetDevice(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     int rc;
-    if (mode == FE_COLOURED) {
-        rc = fe_assemble_coloured(p, K, values, accumulate, crac, s);
+    if (mode == FE_COLOURED || mode == FE_ROWLOCK) {
+        rc = mode == FE_COLOURED ? fe_assemble_coloured(p, K, values, accumulate, crac, s)
+                                 : fe_assemble_rowlock(p, K, values, accumulate, crac, s);
         if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
         return rc;
     }

@@ -38,6 +38,7 @@ FE_PATTERN_ALL = 0x1F
 FE_ATOMIC = 0
 FE_DETERMINISTIC = 1
 FE_COLOURED = 2
+FE_ROWLOCK = 3
 
 FE_KNOB_GATHER_KERNEL = 0
 FE_KNOB_GATHER_BATCH = 1
@@ -159,6 +160,8 @@ def load():
             "fe_pattern_colours": (i, [vp, ctypes.POINTER(i32), pp]),
             "fe_assemble_csr": (i, [vp, vp, vp, vp, i, i, vp]),
             "fe_assemble_crac": (i, [vp, vp, vp, vp, i, i, vp]),
+            "fe_spmv_csr": (i, [vp, vp, vp, vp, vp, vp]),
+            "fe_spmv_crac": (i, [vp, vp, vp, vp, vp, vp]),
             "fe_assemble_batch": (i, [vp, ctypes.POINTER(fe_batch_item), i32, i32, i32, i32,
                                       ctypes.POINTER(fe_schedule), vp]),
             "fe_batch_autotune": (i, [vp, ctypes.POINTER(fe_batch_item), i32, i32, i32, vp,
@@ -332,6 +335,14 @@ def fe_assemble_csr(ctx, pattern, elem_mats, values, mode=FE_ATOMIC, accumulate=
 def fe_assemble_crac(ctx, pattern, elem_mats, values, mode=FE_ATOMIC, accumulate=0, stream=None):
     _check(load().fe_assemble_crac(ctx, pattern, _addr(elem_mats), _addr(values), int(mode), int(accumulate),
                                    _stream(stream)), "fe_assemble_crac")
+
+
+def fe_spmv_csr(ctx, pattern, values, x, y, stream=None):
+    _check(load().fe_spmv_csr(ctx, pattern, _addr(values), _addr(x), _addr(y), _stream(stream)), "fe_spmv_csr")
+
+
+def fe_spmv_crac(ctx, pattern, values, x, y, stream=None):
+    _check(load().fe_spmv_crac(ctx, pattern, _addr(values), _addr(x), _addr(y), _stream(stream)), "fe_spmv_crac")
 
 
 def _items(items):

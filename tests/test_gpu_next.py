@@ -1,0 +1,79 @@
+"""The consumers and alternative assemblies of the paper: SpMV through CSR
+and through CRAC (the paper's outlook), and the spin_int row-locked assembly
+(Listings 3-5), against the oracle."""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2012_00585_gb300 import feasm
+    c = feasm.fe_create(0)
+    yield c
+    feasm.fe_destroy(c)
+
+
+MESHES = [("hex5_d3", *wl.hex_q1_grid(5, 3)), ("tet3_d3", *wl.tet_p2_kuhn(3, d=3, seed=2)),
+          ("quad9", *wl.quad_q1_grid(9, 1)), ("hex4_d1", *wl.hex_q1_grid(4, 1))]
+
+
+@pytest.mark.parametrize("name,D,n_dofs", MESHES, ids=[m[0] for m in MESHES])
+def test_spmv_csr_and_crac(ctx, name, D, n_dofs):
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    K = wl.random_matrices(D.shape[0], D.shape[1], seed=1)
+    g = gu.GpuAssembly(ctx, D, n_dofs)
+    v = g.assemble(K, "csr", feasm.FE_DETERMINISTIC)
+    rp, ci = oracle.csr_pattern(D, n_dofs)
+    x = np.random.default_rng(2).standard_normal(n_dofs)
+    y_o = oracle.spmv_csr(rp, ci, v.cpu().numpy(), x)
+    xd = torch.from_numpy(x).cuda()
+    rows = np.repeat(np.arange(n_dofs), np.diff(rp))
+    scale = np.zeros(n_dofs)
+    np.add.at(scale, rows, np.abs(v.cpu().numpy() * x[ci]))
+    for f in (feasm.fe_spmv_csr, feasm.fe_spmv_crac):
+        y = torch.full((n_dofs,), float("nan"), dtype=torch.float64, device="cuda")
+        f(ctx, g.pattern.handle, v, xd, y)
+        torch.cuda.synchronize()
+        got = y.cpu().numpy()
+        assert np.all(np.abs(got - y_o) <= 1e-13 * scale + 1e-300), f.__name__
+        y2 = torch.empty_like(y)
+        f(ctx, g.pattern.handle, v, xd, y2)
+        torch.cuda.synchronize()
+        assert torch.equal(y, y2)  # reproducible run to run
+    g.free()
+
+
+@pytest.mark.parametrize("fmt", ["csr", "crac"])
+@pytest.mark.parametrize("name,D,n_dofs", MESHES, ids=[m[0] for m in MESHES])
+def test_rowlock_assembly(ctx, fmt, name, D, n_dofs):
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    g = gu.GpuAssembly(ctx, D, n_dofs)
+    rp0, ci0 = g.csr_host()
+    crp0, _ = g.crac_host()
+    # paper's all-ones element: integer sums, exact in any order
+    ones = wl.ones_matrices(D.shape[0], D.shape[1])
+    rp, ci = oracle.csr_pattern(D, n_dofs)
+    got = g.assemble(ones, fmt, feasm.FE_ROWLOCK).cpu().numpy()
+    assert np.array_equal(got, oracle.assemble_csr(D, ones, rp, ci))
+    K = wl.random_matrices(D.shape[0], D.shape[1], seed=4)
+    got = g.assemble(K, fmt, feasm.FE_ROWLOCK).cpu().numpy()
+    exp = oracle.assemble_csr(D, K, rp, ci)
+    gu.assert_within_row_tol(rp, got, exp, gu.row_tolerance(rp, exp, gu.contribution_abs_row_sums(D, K, n_dofs)))
+    assert feasm.fe_device_status(ctx) == 0
+    # the lock words (row pointers) are back to their values
+    rp1, _ = g.csr_host()
+    crp1, _ = g.crac_host()
+    assert np.array_equal(rp1, rp0) and np.array_equal(crp1, crp0)
+    g.free()
