@@ -33,6 +33,8 @@ METRIC = "element-matrix entries assembled/s"
 UNIT = "entries/s"
 N_ASSEMBLIES = 10
 VARIANTS = ("csr-atomic", "crac-atomic", "csr-det", "crac-det")
+# modes timed beside the step (not selectable as the step's own assembly)
+EXTRA_VARIANTS = ("csr-coloured", "crac-coloured", "csr-rowlock", "crac-rowlock")
 
 
 def parse():
@@ -47,9 +49,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "served"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "served", "sweep"],
                     help="single: the 64^3 elasticity step (default); batched: 256 meshes, one launch "
-                         "vs one launch per mesh; served: request stream with latency")
+                         "vs one launch per mesh; served: request stream with latency; sweep: the p- and "
+                         "d-benchmarks on structured Q_p quads, every assembly mode")
     ap.add_argument("--meshes", type=int, default=256, help="batched workload: number of meshes")
     ap.add_argument("--rate", type=float, default=2000.0, help="served workload: mean arrivals per second")
     ap.add_argument("--duration", type=float, default=2.0, help="served workload: seconds of arrivals")
@@ -183,7 +186,9 @@ def run_gpu(args, rank, world, local_rank):
     stream.synchronize()
 
     fmt, mode_name = args.variant.split("-")
-    mode = feasm.FE_ATOMIC if mode_name == "atomic" else feasm.FE_DETERMINISTIC
+    MODES = {"atomic": feasm.FE_ATOMIC, "det": feasm.FE_DETERMINISTIC, "coloured": feasm.FE_COLOURED,
+             "rowlock": feasm.FE_ROWLOCK}
+    mode = MODES[mode_name]
     assemble = feasm.fe_assemble_csr if fmt == "csr" else feasm.fe_assemble_crac
 
     def build():
@@ -240,22 +245,37 @@ def run_gpu(args, rank, world, local_rank):
     extra = {}
     if not args.no_variants:
         p = build()
+        n_col = feasm.fe_pattern_colour(ctx, p, stream)
         var = {}
-        for vname in VARIANTS:
-            f, m = vname.split("-")
-            fn = feasm.fe_assemble_csr if f == "csr" else feasm.fe_assemble_crac
-            md = feasm.FE_ATOMIC if m == "atomic" else feasm.FE_DETERMINISTIC
+
+        def time_us(fn, reps=10):
             for _ in range(3):
-                fn(ctx, p, Kd, values, md, 0, stream)
-            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+                fn()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
             for a, b in evs:
                 a.record(stream)
-                fn(ctx, p, Kd, values, md, 0, stream)
+                fn()
                 b.record(stream)
             torch.cuda.synchronize()
-            us = statistics.median(a.elapsed_time(b) for a, b in evs) * 1e3
+            return statistics.median(a.elapsed_time(b) for a, b in evs) * 1e3
+
+        for vname in VARIANTS + EXTRA_VARIANTS:
+            f, m = vname.split("-")
+            fn = feasm.fe_assemble_csr if f == "csr" else feasm.fe_assemble_crac
+            us = time_us(lambda: fn(ctx, p, Kd, values, MODES[m], 0, stream))
             var[vname] = {"us": round(us, 1), "alg_GBps": round(B / (us * 1e-6) / 1e9, 1),
                           "Gentries_per_s": round(N_ent / (us * 1e-6) / 1e9, 2)}
+        var["csr-coloured"]["n_colours"] = n_col
+        assert feasm.fe_device_status(ctx, stream) == 0
+        # the consumer: y = G x through CSR and through CRAC
+        x = torch.rand(n_dofs, dtype=torch.float64, device=dev)
+        y = torch.empty_like(x)
+        for f, fn, idx_bytes in (("csr", feasm.fe_spmv_csr, 4 * nnz + 8 * (n_dofs + 1)),
+                                 ("crac", feasm.fe_spmv_crac, 4 * info["n_ca"] + 8 * (n_dofs + 1))):
+            us = time_us(lambda: fn(ctx, p, values, x, y, stream))
+            sb = 8 * nnz + idx_bytes + 16 * n_dofs  # values, index arrays, x and y once each
+            var[f"spmv-{f}"] = {"us": round(us, 1), "alg_bytes": sb, "alg_GBps": round(sb / (us * 1e-6) / 1e9, 1),
+                                "GFLOP_per_s": round(2 * nnz / (us * 1e-6) / 1e9, 1)}
         feasm.fe_pattern_free(p)
         pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
         for a, b in pe:
@@ -524,6 +544,103 @@ def run_batched(args, local_rank):
     return line
 
 
+def run_sweep(args, local_rank):
+    """The p- and d-benchmarks of §4 on structured quads (Q_p, p <= 8;
+    d <= 8 and d = 20): per mesh, the pattern sizes (n_dofs, nnz, n_ca,
+    storage factor gamma = n_ca / nnz), the pattern build time and the median
+    time of every numeric mode through CSR and CRAC (L2 flushed before each
+    repetition: these matrices are L2-sized).  With the CPU baseline on, the
+    serial oracle's numeric time gives the paper's speed factor
+    c = t_serial / t_method per mode.  One step = each mesh assembled once in
+    deterministic CSR mode."""
+    import torch
+
+    import workloads as wl
+    from paper_2012_00585_gb300 import feasm as fe
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = fe.fe_create(local_rank)
+    modes = [("csr", "atomic"), ("crac", "atomic"), ("csr", "det"), ("crac", "det"), ("csr", "coloured"),
+             ("crac", "coloured"), ("csr", "rowlock"), ("crac", "rowlock")]
+    MODES = {"atomic": fe.FE_ATOMIC, "det": fe.FE_DETERMINISTIC, "coloured": fe.FE_COLOURED,
+             "rowlock": fe.FE_ROWLOCK}
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    launches0 = fe.fe_kernel_launches()
+
+    def med_ms(fn, reps=10):
+        for _ in range(3):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        with torch.cuda.stream(stream):
+            for a, b in evs:
+                flush.fill_(1.0)
+                a.record(stream)
+                fn()
+                b.record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+    rows = []
+    tot_ent = tot_alg = tot_ms = 0
+    for bench, m, p, d in wl.paper_sweep_points():
+        D, n_dofs = wl.quad_qp_grid(m, p, d)
+        n_e, n_loc = D.shape
+        K = wl.random_matrices(n_e, n_loc, seed=m + 10 * p + 100 * d)
+        with torch.cuda.stream(stream):
+            Dd = torch.from_numpy(D).to(dev)
+            Kd = torch.from_numpy(K).to(dev)
+        stream.synchronize()
+        build_ms = med_ms(lambda: fe.fe_pattern_free(
+            fe.fe_pattern_build(ctx, n_e, n_loc, n_dofs, Dd, fe.FE_PATTERN_ALL, stream)), reps=5)
+        pt = fe.fe_pattern_build(ctx, n_e, n_loc, n_dofs, Dd, fe.FE_PATTERN_ALL, stream)
+        info = fe.fe_pattern_info_get(pt)
+        n_col = fe.fe_pattern_colour(ctx, pt, stream)
+        nnz = info["nnz"]
+        vals = torch.empty(nnz, dtype=torch.float64, device=dev)
+        n_ent = n_e * n_loc * n_loc
+        alg = b_alg(n_e, n_loc, nnz)
+        row = {"bench": bench, "m": m, "p": p, "d": d, "n_loc": n_loc, "n_dofs": n_dofs, "nnz": nnz,
+               "n_ca": info["n_ca"], "gamma": round(info["n_ca"] / nnz, 4), "n_colours": n_col,
+               "pattern_build_ms": round(build_ms, 3), "us": {}, "Gentries_per_s": {}}
+        for f, mname in modes:
+            fn = fe.fe_assemble_csr if f == "csr" else fe.fe_assemble_crac
+            ms = med_ms(lambda: fn(ctx, pt, Kd, vals, MODES[mname], 0, stream))
+            row["us"][f"{f}-{mname}"] = round(ms * 1e3, 1)
+            row["Gentries_per_s"][f"{f}-{mname}"] = round(n_ent / (ms * 1e-3) / 1e9, 2)
+        assert fe.fe_device_status(ctx, stream) == 0
+        if not args.no_cpu_baseline:
+            import oracle
+            rp, ci = oracle.csr_pattern(D, n_dofs)
+            t = time.perf_counter()
+            oracle.assemble_csr(D, K, rp, ci)
+            t_ser = time.perf_counter() - t
+            row["oracle_numeric_ms"] = round(t_ser * 1e3, 2)
+            row["speed_factor_c"] = {k: round(t_ser * 1e6 / v, 1) for k, v in row["us"].items()}
+        tot_ent += n_ent
+        tot_alg += alg
+        tot_ms += row["us"]["csr-det"] * 1e-3
+        rows.append(row)
+        fe.fe_pattern_free(pt)
+        del Dd, Kd, vals
+    launches = fe.fe_kernel_launches() - launches0
+    hbm, src = measured_peaks()
+    line = {"metric": METRIC, "value": tot_ent / (tot_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": 10,
+            "warmup": 3, "ms_per_step": round(tot_ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "p- and d-benchmarks on structured squares: Q_p quads p=1..8 (d=1) and "
+                                   "p=1..4 (d=4) on 48x48, Q1 d=1..8 on 192x192, Q1 d=20 on 48x48; N(0,1) K; "
+                                   "one step = every mesh assembled once (deterministic CSR)",
+                       "l2": "flushed (256 MiB write) before every timed repetition",
+                       "entries_per_step": tot_ent, "alg_bytes_per_step": tot_alg},
+            "roofline": {"bound": "hbm", "achieved": round(tot_alg / (tot_ms * 1e-3) / 1e9, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(tot_alg / (tot_ms * 1e-3) / 1e9 / hbm, 4), "traffic": None,
+                         "peak_source": src},
+            "gpu_launches": int(launches), "points": rows}
+    fe.fe_destroy(ctx)
+    return line
+
+
 def run_served(args, local_rank):
     """Poisson stream of assembly requests (mean `rate`/s for `duration` s):
     90 % hex meshes with n ~ logU[8,48] (half Q1 Laplace d=1, half Q1
@@ -650,6 +767,10 @@ def main():
     if args.workload == "served":
         if rank == 0:
             print(json.dumps(run_served(args, local_rank)), flush=True)
+        return
+    if args.workload == "sweep":
+        if rank == 0:
+            print(json.dumps(run_sweep(args, local_rank)), flush=True)
         return
     if world > 1:
         import torch

@@ -79,8 +79,7 @@ extern "C" {
                                ~v), taken with a bounded spin; sum order
                                unspecified.  The pattern's row pointers change
                                while it runs: no other work on this pattern
-                               may run concurrently.  Elements of up to 32
-                               DOFs in blocks (4,1), (8,1), (8,3), (10,3).    */
+                               may run concurrently.                          */
 
 typedef struct fe_ctx fe_ctx;
 typedef struct fe_pattern fe_pattern;
@@ -270,8 +269,12 @@ int fe_pattern_info_get(const fe_pattern *pattern, fe_pattern_info *out);
  *              after element.  Read only.
  *   values     device, double [nnz], caller-owned; entry k belongs to
  *              (row of k, col_idx[k]).
- *   mode       FE_ATOMIC (needs FE_PATTERN_MAP_CSR) or FE_DETERMINISTIC (needs
- *              FE_PATTERN_MAP_CSR and FE_PATTERN_ADJ).
+ *   mode       FE_ATOMIC (needs FE_PATTERN_MAP_CSR), FE_DETERMINISTIC (needs
+ *              FE_PATTERN_MAP_CSR and FE_PATTERN_ADJ), FE_COLOURED (needs
+ *              FE_PATTERN_MAP_CSR and fe_pattern_colour first, else
+ *              FE_ERR_NOT_BUILT) or FE_ROWLOCK (needs FE_PATTERN_MAP_CSR; a
+ *              lock spin that runs out leaves the sum incomplete and sets
+ *              FE_ERR_TIMEOUT in fe_device_status).
  *   accumulate 0: values are overwritten (reset to zero first, §3);
  *              1: contributions are added to the values already there.
  * Asynchronous on `stream`.  FE_DETERMINISTIC reproduces the oracle's

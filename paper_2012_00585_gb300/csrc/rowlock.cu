@@ -88,12 +88,75 @@ __global__ void __launch_bounds__(256) k_rowlock(const double *__restrict__ K, i
     }
 }
 
+// Any element size (n_loc <= FE_MAX_NLOC): the same protocol, the warp
+// striding over the columns of the locked row; run positions of the column
+// blocks staged in shared memory per warp.
+template <typename MT, bool CRAC>
+__global__ void __launch_bounds__(256) k_rowlock_generic(const double *__restrict__ K, int64_t n_e, int32_t nln,
+                                                         int32_t B, Geo g, const MT *__restrict__ map,
+                                                         const MT *__restrict__ mapc, int64_t *locks, double *values,
+                                                         int *status)
+{
+    __shared__ int32_t k_s[8][FE_MAX_NLOC];
+    __shared__ int32_t off_s[8][FE_MAX_NLOC];
+    const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) & 7;
+    const int n_loc = nln * B;
+    const int64_t NN = (int64_t)n_loc * n_loc;
+    for (int64_t e = fe_warp_id(); e < n_e; e += fe_warps()) {
+        int64_t rp = 0;
+        int nr = 0;
+        if (CRAC) {
+            rp = g.run_ptr[e];
+            nr = (int)(g.run_ptr[e + 1] - rp);
+            for (int kc = lane; kc < nln; kc += 32)
+                run_of_multi(g.run_mask + e * g.mask_words, kc, k_s[w][kc], off_s[w][kc]);
+            __syncwarp();
+        }
+        const double *Ke = K + e * NN;
+        for (int r = 0; r < n_loc; ++r) {
+            const int64_t row = (int64_t)B * g.N[e * nln + r / B] + r % B;
+            unsigned long long *lk = (unsigned long long *)(locks + row);
+            int64_t v = 0;
+            int got = 0;
+            if (lane == 0) {
+                v = (int64_t)*(volatile long long *)lk;
+                if (v < 0) v = ~v;
+                for (uint32_t it = 0; it < LOCK_SPIN_LIMIT; ++it) {
+                    if (atomicCAS(lk, (unsigned long long)v, (unsigned long long)~v) == (unsigned long long)v) {
+                        got = 1;
+                        break;
+                    }
+                }
+                if (got) __threadfence();
+                else atomicCAS(status, 0, FE_ERR_TIMEOUT);
+            }
+            got = __shfl_sync(0xffffffffu, got, 0);
+            v = __shfl_sync(0xffffffffu, v, 0);
+            if (!got) continue;
+            const int64_t base = CRAC ? (int64_t)g.col_align[v + 1] : v;
+            for (int c = lane; c < n_loc; c += 32) {
+                const int kc = c / B;
+                int pos;
+                if (!CRAC) pos = (int)map[(e * nln + r / B) * nln + kc];
+                else pos = (int)mapc[rp * nln + (int64_t)(r / B) * nr + k_s[w][kc]] + off_s[w][kc];
+                double *dst = values + base + (int64_t)B * pos + c % B;
+                __stcg(dst, __ldcg(dst) + __ldcs(Ke + (int64_t)r * n_loc + c));
+            }
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                atomicExch(lk, (unsigned long long)v);
+            }
+            __syncwarp();
+        }
+    }
+}
+
 }  // namespace
 
 int fe_assemble_rowlock(const fe_pattern *p, const double *K, double *values, int accumulate, bool crac,
                         cudaStream_t s)
 {
-    if (p->n_loc > 32 || !(p->nln == 8 || p->nln == 4 || p->nln == 10)) return FE_ERR_UNSUPPORTED;
     if (!accumulate) FE_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * (size_t)p->nnz, s));
     if (p->n_e == 0) return FE_OK;
     const Geo g = geo_of(p);
@@ -124,7 +187,25 @@ int fe_assemble_rowlock(const fe_pattern *p, const double *K, double *values, in
     else if (p->nln == 10 && p->B == 3) FE_RL(10, 3);
     else if (p->nln == 8 && p->B == 1) FE_RL(8, 1);
     else if (p->nln == 4 && p->B == 1) FE_RL(4, 1);
-    else return FE_ERR_UNSUPPORTED;
+    else if (p->map_bytes == 1) {
+        if (crac)
+            k_rowlock_generic<uint8_t, true><<<grid, 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
+                                                                  (const uint8_t *)p->map_csr,
+                                                                  (const uint8_t *)p->map_crac, locks, values, st);
+        else
+            k_rowlock_generic<uint8_t, false><<<grid, 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
+                                                                   (const uint8_t *)p->map_csr,
+                                                                   (const uint8_t *)p->map_crac, locks, values, st);
+    } else {
+        if (crac)
+            k_rowlock_generic<uint16_t, true><<<grid, 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
+                                                                   (const uint16_t *)p->map_csr,
+                                                                   (const uint16_t *)p->map_crac, locks, values, st);
+        else
+            k_rowlock_generic<uint16_t, false><<<grid, 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
+                                                                    (const uint16_t *)p->map_csr,
+                                                                    (const uint16_t *)p->map_crac, locks, values, st);
+    }
 #undef FE_RL
     fe_note_launch();
     FE_CUDA(cudaGetLastError());

@@ -23,6 +23,7 @@ from .meshes import (  # noqa: F401
     hex_q1_grid,
     tet_p2_kuhn,
     batched_mesh_sizes,
+    paper_sweep_points,
 )
 from .elements import (  # noqa: F401
     laplace_q1_quad,

@@ -54,6 +54,18 @@ def quad_qp_grid(m: int, p: int, d: int = 1):
     return _interleave(nodes, d), d * s * s
 
 
+def paper_sweep_points():
+    """The p- and d-benchmark meshes of §4 on structured squares, as
+    (benchmark, m, p, d): Q_p quads on the 4th mesh (48 x 48) for p = 1..8 at
+    d = 1 and p = 1..4 at d = 4; Q1 on the 6th mesh (192 x 192) for d = 1..8;
+    Q1 on the 4th mesh at d = 20."""
+    pts = [("p_d1", 48, p, 1) for p in range(1, 9)]
+    pts += [("p_d4", 48, p, 4) for p in range(1, 5)]
+    pts += [("d", 192, 1, d) for d in range(1, 9)]
+    pts.append(("d20", 48, 1, 20))
+    return pts
+
+
 def hex_q1_grid(n: int, d: int = 1):
     """n^3 trilinear Q1 hexes on the unit cube, natural lexicographic numbering.
 
