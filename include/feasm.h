@@ -146,12 +146,16 @@ uint64_t fe_kernel_launches(void);
  * them (FE_DETERMINISTIC stays bit-identical), only speed does. */
 #define FE_KNOB_GATHER_KERNEL 0  /* FE_DETERMINISTIC: 1 register-batched row gather
                                     (default), 2 shared-memory-staged row
-                                    gather, 3 pipelined staged gather        */
+                                    gather, 3 pipelined staged gather, 4 row
+                                    gather fed by bulk copies (TMA) through a
+                                    ring of stages                           */
 #define FE_KNOB_GATHER_BATCH 1   /* incidences per register batch: 4 or 8   */
 #define FE_KNOB_GATHER_WARPS 2   /* warps per block of the gather: 1..8      */
 #define FE_KNOB_ATOMIC_KERNEL 3  /* FE_ATOMIC: 1 register warp-per-element,
                                     2 bulk-copy (TMA) staged warp-per-element */
 #define FE_KNOB_ATOMIC_WARPS 4   /* warps per block of the staged kernel     */
+#define FE_KNOB_GATHER_STAGES 5  /* ring stages per warp of gather kernel 4:
+                                    2..8 (0: 4)                              */
 #define FE_KNOB_COUNT 8
 
 /* Set / read one schedule knob.  FE_ERR_INVALID_ARG for an unknown knob or a

@@ -276,15 +276,17 @@ int fe_tune_set(fe_ctx *ctx, int knob, int value)
     if (!ctx || knob < 0 || knob >= FE_KNOB_COUNT) return FE_ERR_INVALID_ARG;
     int lo = 0, hi = 0;
     switch (knob) {
-    case FE_KNOB_GATHER_KERNEL: hi = 3; break;
+    case FE_KNOB_GATHER_KERNEL: hi = 4; break;
     case FE_KNOB_GATHER_BATCH: hi = 8; break;
     case FE_KNOB_GATHER_WARPS: hi = 8; break;
     case FE_KNOB_ATOMIC_KERNEL: hi = 2; break;
     case FE_KNOB_ATOMIC_WARPS: hi = 8; break;
+    case FE_KNOB_GATHER_STAGES: hi = 8; break;
     default: return FE_ERR_INVALID_ARG;
     }
     if (value < lo || value > hi) return FE_ERR_INVALID_ARG;
     if (knob == FE_KNOB_GATHER_BATCH && value != 0 && value != 4 && value != 8) return FE_ERR_INVALID_ARG;
+    if (knob == FE_KNOB_GATHER_STAGES && value == 1) return FE_ERR_INVALID_ARG;
     ctx->knob[knob] = value;
     return FE_OK;
 }

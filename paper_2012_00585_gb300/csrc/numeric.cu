@@ -601,6 +601,258 @@ __global__ void __launch_bounds__(128) k_gather_pipe(const double *__restrict__ 
     cp_async_wait<0>();
 }
 
+// Shared memory of one warp of k_gather_bulk: S stages of UB slices, S
+// mbarriers, per-stage metadata (UB incidence ids; count, adjacency range,
+// row start and row length), the row accumulator.
+__host__ __device__ inline size_t bulk_warp_bytes(int chk, int cap, int S, int UB)
+{
+    const size_t b = (size_t)S * UB * chk * 8 + (size_t)S * 8 + (size_t)S * 5 * 8 + (size_t)S * UB * 4 +
+                     (size_t)cap * 8 + 8;
+    return (b + 127) & ~(size_t)127;
+}
+
+// Row gather with the K slices moved by the bulk-copy (TMA) engine: the
+// SM's load path streams about half of what bulk copies do.  Each warp walks
+// its node rows v0, v0 + W, ... (W = all warps) as a software pipeline:
+//   iteration i loads the incidence ids of row i+S+1 and the adjacency and
+//   row pointers of row i+S+2 into registers, computes the slots of row i+1
+//   from the metadata of its stage, waits for row i's slices, adds them in
+//   ascending element order into the row accumulator, writes the row, and
+//   refills row i's stage with the slices of row i+S (lanes 0..n-1 issue one
+//   bulk copy each; the stage's mbarrier counts the bytes).
+// The first UB incidences of a row are staged, further ones (high-degree
+// nodes) are read directly.  Bit-identical to the sequential sum.  A wait that
+// runs out sets FE_ERR_TIMEOUT, waits (bounded) for the copies in flight and
+// ends the warp.
+template <int NLN, int BB, typename MT, bool CRAC, int UB>
+__global__ void __launch_bounds__(128) k_gather_bulk(const double *__restrict__ K, int64_t n_nodes, Geo g,
+                                                     const MT *__restrict__ map, const MT *__restrict__ mapc,
+                                                     int cap, int S, int accumulate, double *values, int *status)
+{
+    constexpr int NLOC = NLN * BB;
+    constexpr int NN = NLOC * NLOC;
+    constexpr int CHK = BB * NLOC;
+    constexpr int IT = (CHK + 31) / 32;
+    constexpr uint32_t CHKB = CHK * 8;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    unsigned char *wbase = smem_raw + (size_t)(threadIdx.x >> 5) * bulk_warp_bytes(CHK, cap, S, UB);
+    double *kst = (double *)wbase;                             // [S][UB * CHK]
+    uint64_t *bar = (uint64_t *)(kst + (size_t)S * UB * CHK);  // [S]
+    int64_t *meta = (int64_t *)(bar + S);                      // [S][5]: n, a, b, rb, RL
+    uint32_t *meta_t = (uint32_t *)(meta + 5 * S);             // [S][UB]
+    double *acc = (double *)(((uintptr_t)(meta_t + S * UB) + 7) & ~(uintptr_t)7);  // [cap]
+    int jr_[IT], c_[IT], ku[IT], offu[IT];
+#pragma unroll
+    for (int j = 0; j < IT; ++j) {
+        const int q = lane + 32 * j;
+        const int qq = q < CHK ? q : 0;
+        jr_[j] = qq / NLOC;
+        c_[j] = qq % NLOC;
+        ku[j] = 0;
+        offu[j] = 0;
+        if (CRAC && g.uniform_R) run_of(g.run_mask[0], c_[j] / BB, ku[j], offu[j]);
+    }
+    const int64_t W = fe_warps(), v0 = fe_warp_id();
+    if (v0 >= n_nodes) return;
+    const int64_t n_rows = (n_nodes - v0 + W - 1) / W;  // rows of this warp
+    if (lane == 0) {
+        for (int st = 0; st < S; ++st) fe_mbar_init(&bar[st], 1);
+        fe_fence_mbar_init();
+    }
+    __syncwarp();
+    const uint64_t pol = fe_policy_evict_first();
+
+    struct Ptr {
+        int64_t a, b, rb, RL;
+    };
+    auto load_ptr = [&](int64_t i) {
+        Ptr p{0, 0, 0, 0};
+        if (i < n_rows) {
+            const int64_t v = v0 + i * W;
+            p.a = g.adj_ptr[v];
+            p.b = g.adj_ptr[v + 1];
+            const int64_t i0 = (int64_t)BB * v;
+            if (!CRAC) {
+                p.rb = g.row_ptr[i0];
+                p.RL = g.row_ptr[i0 + 1] - p.rb;
+            } else {
+                p.rb = crac_row_base(g, i0);
+                p.RL = crac_row_base(g, i0 + 1) - p.rb;
+            }
+        }
+        return p;
+    };
+    auto load_ids = [&](const Ptr &p) { return lane < min((int64_t)UB, p.b - p.a) ? g.adj[p.a + lane] : 0u; };
+    int64_t issued = 0;
+    // row i's stage: metadata, then one bulk copy per staged incidence
+    auto issue = [&](int64_t i, const Ptr &p, uint32_t t) {
+        if (i >= n_rows) return;
+        const int st = (int)(i % S);
+        const int n = (int)min((int64_t)UB, p.b - p.a);
+        if (lane < n) meta_t[st * UB + lane] = t;
+        if (lane == 0) {
+            meta[st * 5 + 0] = n;
+            meta[st * 5 + 1] = p.a;
+            meta[st * 5 + 2] = p.b;
+            meta[st * 5 + 3] = p.rb;
+            meta[st * 5 + 4] = p.RL;
+            fe_fence_proxy_async();
+            fe_mbar_expect_tx(&bar[st], (uint32_t)n * CHKB);
+        }
+        __syncwarp();
+        if (lane < n) {
+            const uint32_t e = t / NLN;
+            const uint32_t kr = t - e * NLN;
+            fe_bulk_g2s(kst + ((size_t)st * UB + lane) * CHK, K + (int64_t)e * NN + (int64_t)kr * CHK, CHKB, &bar[st],
+                        pol);
+        }
+        ++issued;
+    };
+    // slots (relative to the row start) of the staged incidences of row i
+    auto slots = [&](int64_t i, int (&rel)[UB][IT]) {
+        const int st = (int)(i % S);
+        const int n = i < n_rows ? (int)meta[st * 5 + 0] : 0;
+        const int RL = i < n_rows ? (int)meta[st * 5 + 4] : 0;
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const uint32_t t = u < n ? meta_t[st * UB + u] : 0u;
+            const uint32_t e = t / NLN;
+            const int kr = (int)(t - e * NLN);
+            int64_t rp = 0;
+            int nr = 0;
+            uint32_t m = 0;
+            if (CRAC && u < n) {
+                if (g.uniform_R) {
+                    nr = g.uniform_R;
+                    rp = (int64_t)e * nr;
+                } else {
+                    rp = g.run_ptr[e];
+                    nr = (int)(g.run_ptr[e + 1] - rp);
+                    m = g.run_mask[e];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < IT; ++j) {
+                rel[u][j] = 0;
+                if (u < n && lane + 32 * j < CHK) {
+                    const int kc = c_[j] / BB;
+                    int pos;
+                    if (!CRAC) {
+                        pos = (int)map[(int64_t)t * NLN + kc];
+                    } else {
+                        int k = ku[j], off = offu[j];
+                        if (!g.uniform_R) run_of(m, kc, k, off);
+                        pos = (int)mapc[rp * NLN + (int64_t)kr * nr + k] + off;
+                    }
+                    rel[u][j] = jr_[j] * RL + BB * pos + c_[j] % BB;
+                }
+            }
+        }
+    };
+
+    // prologue: rows 0..S-1 staged; ids of row S and pointers of row S+1 in registers
+    for (int64_t i = 0; i < S; ++i) {
+        const Ptr p = load_ptr(i);
+        issue(i, p, load_ids(p));
+    }
+    Ptr pA = load_ptr(S);
+    uint32_t tA = load_ids(pA);
+    Ptr pB = load_ptr(S + 1);
+    int rel[UB][IT], reln[UB][IT];
+    slots(0, rel);
+
+    bool ok = true;
+    int64_t i = 0;
+    for (; i < n_rows; ++i) {
+        const uint32_t tN = load_ids(pB);  // row i+S+1
+        const Ptr pN = load_ptr(i + S + 2);
+        slots(i + 1, reln);
+        const int st = (int)(i % S);
+        const int n = (int)meta[st * 5 + 0];
+        const int64_t a = meta[st * 5 + 1], b = meta[st * 5 + 2], rb = meta[st * 5 + 3];
+        const int RL = (int)meta[st * 5 + 4];
+        const int total = BB * RL;
+        for (int k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
+        const bool landed = fe_mbar_wait(&bar[st], (uint32_t)((i / S) & 1));
+        if (!__all_sync(0xffffffffu, landed)) {
+            ok = false;
+            break;
+        }
+        __syncwarp();
+        const double *stg = kst + (size_t)st * UB * CHK;
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            if (u < n) {
+                double kv[IT], av[IT];
+#pragma unroll
+                for (int j = 0; j < IT; ++j)
+                    if (lane + 32 * j < CHK) kv[j] = stg[u * CHK + lane + 32 * j];
+                // the IT slots of one incidence are distinct: load all, then store all
+#pragma unroll
+                for (int j = 0; j < IT; ++j)
+                    if (lane + 32 * j < CHK) av[j] = acc[rel[u][j]];
+#pragma unroll
+                for (int j = 0; j < IT; ++j)
+                    if (lane + 32 * j < CHK) acc[rel[u][j]] = av[j] + kv[j];
+            }
+            __syncwarp();
+        }
+        // incidences beyond the staged ones: read directly
+        for (int64_t s = a + UB; s < b; ++s) {
+            const uint32_t t = g.adj[s];
+            const uint32_t e = t / NLN;
+            const int kr = (int)(t - e * NLN);
+            const double *src = K + (int64_t)e * NN + (int64_t)kr * CHK;
+            int64_t rp = 0;
+            int nr = 0;
+            uint32_t m = 0;
+            if (CRAC) {
+                if (g.uniform_R) {
+                    nr = g.uniform_R;
+                    rp = (int64_t)e * nr;
+                } else {
+                    rp = g.run_ptr[e];
+                    nr = (int)(g.run_ptr[e + 1] - rp);
+                    m = g.run_mask[e];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < IT; ++j) {
+                const int q = lane + 32 * j;
+                if (q < CHK) {
+                    const int kc = c_[j] / BB;
+                    int pos;
+                    if (!CRAC) {
+                        pos = (int)map[(int64_t)t * NLN + kc];
+                    } else {
+                        int k = ku[j], off = offu[j];
+                        if (!g.uniform_R) run_of(m, kc, k, off);
+                        pos = (int)mapc[rp * NLN + (int64_t)kr * nr + k] + off;
+                    }
+                    const int r = jr_[j] * RL + BB * pos + c_[j] % BB;
+                    acc[r] += __ldcs(src + q);
+                }
+            }
+            __syncwarp();
+        }
+        for (int k = lane; k < total; k += 32) __stcs(values + rb + k, acc[k]);
+        __syncwarp();
+        issue(i + S, pA, tA);  // row i's stage is free
+        pA = pB;
+        tA = tN;
+        pB = pN;
+#pragma unroll
+        for (int u = 0; u < UB; ++u)
+#pragma unroll
+            for (int j = 0; j < IT; ++j) rel[u][j] = reln[u][j];
+    }
+    if (!ok) {
+        if (lane == 0) atomicCAS(status, 0, FE_ERR_TIMEOUT);
+        for (; i < issued; ++i) fe_mbar_wait(&bar[i % S], (uint32_t)((i / S) & 1));
+    }
+}
+
 __host__ __device__ inline size_t atomic_warp_bytes(int nn, int nloc, int nln)
 {
     const size_t b = (size_t)2 * nn * 8 + (size_t)nloc * 8 + (size_t)nln * nln * 4 + 2 * (size_t)nln * 4 + 24;
@@ -780,6 +1032,29 @@ int launch_gather(const fe_pattern *p, const double *K, double *values, int accu
     int W = ctx->knob[FE_KNOB_GATHER_WARPS];
     if constexpr (NLN > 0) {
         constexpr int CHK = BB * NLN * BB;
+        if (kind == 4 && tma_ok(p, K, CHK)) {
+            constexpr int UB = 8;
+            int S = ctx->knob[FE_KNOB_GATHER_STAGES] > 0 ? ctx->knob[FE_KNOB_GATHER_STAGES] : 4;
+            int Wb = (W > 0 && W <= 4) ? W : 4;  // launch bound: 128 threads
+            size_t bsmem = (size_t)Wb * bulk_warp_bytes(CHK, cap, S, UB);
+            while (bsmem > 200 * 1024 && (Wb > 1 || S > 2)) {
+                if (Wb > 1) Wb >>= 1;
+                else --S;
+                bsmem = (size_t)Wb * bulk_warp_bytes(CHK, cap, S, UB);
+            }
+            if (bsmem <= 200 * 1024) {
+                FE_TRY(configure_smem(k_gather_bulk<NLN, BB, MT, CRAC, UB>, bsmem));
+                int bgrid;
+                FE_TRY(grid_by_occupancy(k_gather_bulk<NLN, BB, MT, CRAC, UB>, Wb * 32, bsmem, sms, p->n_nodes,
+                                         &bgrid));
+                k_gather_bulk<NLN, BB, MT, CRAC, UB><<<bgrid, Wb * 32, bsmem, s>>>(
+                    K, p->n_nodes, g, (const MT *)p->map_csr, (const MT *)p->map_crac, cap, S, accumulate, values,
+                    ctx->d_status);
+                fe_note_launch();
+                FE_CUDA(cudaGetLastError());
+                return FE_OK;
+            }
+        }
         if (kind == 3 && tma_ok(p, K, CHK)) {
             if (W <= 0 || W > 4) W = 4;
             const size_t psmem = (size_t)W * pipe_warp_bytes(CHK, cap);

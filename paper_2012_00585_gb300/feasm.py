@@ -45,6 +45,7 @@ FE_KNOB_GATHER_BATCH = 1
 FE_KNOB_GATHER_WARPS = 2
 FE_KNOB_ATOMIC_KERNEL = 3
 FE_KNOB_ATOMIC_WARPS = 4
+FE_KNOB_GATHER_STAGES = 5
 FE_KNOB_COUNT = 8
 
 FE_FORMAT_CSR = 0
