@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--knob", action="append", default=[], metavar="NAME=VALUE",
+                    help="set a schedule knob before the run, e.g. GATHER_KERNEL=4 (FE_KNOB_<NAME>)")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "served", "sweep"],
                     help="single: the 64^3 elasticity step (default); batched: 256 meshes, one launch "
                          "vs one launch per mesh; served: request stream with latency; sweep: the p- and "
@@ -91,10 +93,22 @@ def measured_peaks():
 
 
 def source_hash():
+    """Hash of what decides the traffic of the default deterministic kernel:
+    the k_gather_node definition, its launch lines and the shared device
+    bodies (assemble_body.cuh)."""
+    csrc = os.path.join(ROOT, "paper_2012_00585_gb300", "csrc")
+    with open(os.path.join(csrc, "numeric.cu")) as f:
+        src = f.read()
+    k0 = src.index("k_gather_node(const double")
+    k0 = src.rindex("template", 0, k0)
+    k1 = src.index("\n}\n", k0)
+    l0 = src.index("    if (W <= 0) W = 2;")
+    l1 = src.index("k_gather_generic<MT, CRAC>, smem", l0)
     h = hashlib.sha256()
-    for f in ("numeric.cu", "internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2012_00585_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    h.update(src[k0:k1].encode())
+    h.update(src[l0:l1].encode())
+    with open(os.path.join(csrc, "assemble_body.cuh"), "rb") as f:
+        h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -174,6 +188,9 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
     ctx = feasm.fe_create(local_rank)
+    for kv in args.knob:
+        name, value = kv.split("=")
+        feasm.fe_tune_set(ctx, getattr(feasm, "FE_KNOB_" + name.upper()), int(value))
 
     n = args.n
     D, n_dofs = wl.hex_q1_grid(n, 3)
@@ -311,7 +328,8 @@ def run_gpu(args, rank, world, local_rank):
                                f"; step = pattern build + {N_ASSEMBLIES} numeric assemblies ({args.variant})",
                    "global_batch": world, "entries_per_assembly": N_ent, "nnz": nnz, "n_ca": info["n_ca"],
                    "l2": "inputs larger than L2 (K = %.2f GB per assembly)" % (8 * N_ent / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   **({"knobs": args.knob} if args.knob else {})},
         "roofline": roofline,
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps,
@@ -326,20 +344,24 @@ def run_gpu(args, rank, world, local_rank):
 
 
 def hbm_probe(ctx, feasm, dev, stream):
-    """Live read-only and copy bandwidth of this GPU (2 GiB streamed, best
-    of 5): the copy rate matches the measured peak; the read-only rate bounds
-    a kernel whose traffic is mostly reads."""
+    """Live bandwidth of this GPU (2 GiB streamed, best of 6): read-only by
+    the SMs' loads, copy, and read-only by bulk copies (TMA).  The copy rate
+    matches the measured peak; loads alone stream about half of what bulk
+    copies do."""
     import torch
     n = 1 << 28
     a = torch.ones(n, dtype=torch.float64, device=dev)
     b = torch.empty(n, dtype=torch.float64, device=dev)
     out = {}
-    for name, dst, mult in (("read", None, 1), ("copy", b, 2)):
+    for name, dst, mult in (("read", None, 1), ("copy", b, 2), ("read_bulk", None, 1)):
         best = 1e30
         for _ in range(6):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            feasm.fe_hbm_probe(ctx, a, dst, n, stream)
+            if name == "read_bulk":
+                feasm.fe_hbm_probe_bulk(ctx, a, n, stream)
+            else:
+                feasm.fe_hbm_probe(ctx, a, dst, n, stream)
             e1.record(stream)
             e1.synchronize()
             best = min(best, e0.elapsed_time(e1))

@@ -135,6 +135,12 @@ int fe_device_status(fe_ctx *ctx, void *stream);
  * bound a read-dominated or a balanced kernel. */
 int fe_hbm_probe(fe_ctx *ctx, const double *src, double *dst, int64_t n, void *stream);
 
+/* The read-only stream of fe_hbm_probe moved by the bulk-copy (TMA) engine
+ * into shared memory instead of by the SMs' loads (n even, src 16-byte
+ * aligned): the two rates differ by about two on GB300, which is why the
+ * read-dominated kernels are compared with both. */
+int fe_hbm_probe_bulk(fe_ctx *ctx, const double *src, int64_t n, void *stream);
+
 /* Number of kernels this library has launched in this process so far (all
  * contexts and threads); a caller brackets a region with two reads to count
  * the launches inside it. */

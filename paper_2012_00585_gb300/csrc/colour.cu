@@ -106,18 +106,18 @@ int launch_colour(const fe_pattern *p, const double *K, const int32_t *elems, in
                   cudaStream_t s)
 {
     const Geo g = geo_of(p);
-    const int grid = fe_grid_for(count * 32, 256, p->ctx->num_sms, 8);
+    const int sms = p->ctx->num_sms;
     const MT *map = (const MT *)p->map_csr, *mapc = (const MT *)p->map_crac;
     if (p->nln == 8 && p->B == 3)
-        k_colour_assemble<8, 3, MT, CRAC><<<grid, 256, 0, s>>>(K, elems, count, g, map, mapc, values);
+        k_colour_assemble<8, 3, MT, CRAC><<<fe_grid_resident(k_colour_assemble<8, 3, MT, CRAC>, count * 32, 256, sms), 256, 0, s>>>(K, elems, count, g, map, mapc, values);
     else if (p->nln == 10 && p->B == 3)
-        k_colour_assemble<10, 3, MT, CRAC><<<grid, 256, 0, s>>>(K, elems, count, g, map, mapc, values);
+        k_colour_assemble<10, 3, MT, CRAC><<<fe_grid_resident(k_colour_assemble<10, 3, MT, CRAC>, count * 32, 256, sms), 256, 0, s>>>(K, elems, count, g, map, mapc, values);
     else if (p->nln == 8 && p->B == 1)
-        k_colour_assemble<8, 1, MT, CRAC><<<grid, 256, 0, s>>>(K, elems, count, g, map, mapc, values);
+        k_colour_assemble<8, 1, MT, CRAC><<<fe_grid_resident(k_colour_assemble<8, 1, MT, CRAC>, count * 32, 256, sms), 256, 0, s>>>(K, elems, count, g, map, mapc, values);
     else if (p->nln == 4 && p->B == 1)
-        k_colour_assemble<4, 1, MT, CRAC><<<grid, 256, 0, s>>>(K, elems, count, g, map, mapc, values);
+        k_colour_assemble<4, 1, MT, CRAC><<<fe_grid_resident(k_colour_assemble<4, 1, MT, CRAC>, count * 32, 256, sms), 256, 0, s>>>(K, elems, count, g, map, mapc, values);
     else
-        k_colour_assemble_generic<MT, CRAC><<<grid, 256, 0, s>>>(K, elems, count, p->nln, p->B, g, map, mapc, values);
+        k_colour_assemble_generic<MT, CRAC><<<fe_grid_resident(k_colour_assemble_generic<MT, CRAC>, count * 32, 256, sms), 256, 0, s>>>(K, elems, count, p->nln, p->B, g, map, mapc, values);
     fe_note_launch();
     FE_CUDA(cudaGetLastError());
     return FE_OK;

@@ -107,5 +107,18 @@ static inline int fe_grid_for(int64_t work, int threads, int num_sms, int per_sm
     return (int)blocks;
 }
 
+// Resident blocks per SM of a kernel at this block shape (cached per kernel,
+// block size and dynamic shared memory; at least 1).
+int fe_resident_blocks(const void *kernel, int threads, size_t smem);
+
+// Grid of a grid-strided kernel: enough blocks for `work` threads, at most
+// one full wave of resident blocks (a partial second wave would hold a
+// share of the strided work at low occupancy).
+template <typename KernelT>
+inline int fe_grid_resident(KernelT kernel, int64_t work, int threads, int num_sms, size_t smem = 0)
+{
+    return fe_grid_for(work, threads, num_sms, fe_resident_blocks((const void *)kernel, threads, smem));
+}
+
 __device__ __forceinline__ int64_t fe_warp_id() { return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
 __device__ __forceinline__ int64_t fe_warps() { return ((int64_t)gridDim.x * blockDim.x) >> 5; }

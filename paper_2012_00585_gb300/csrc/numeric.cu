@@ -1009,11 +1009,12 @@ int launch_atomic(const fe_pattern *p, const double *K, double *values, cudaStre
             k_atomic_tma<NLN, BB, MT, CRAC><<<grid, W * 32, smem, s>>>(
                 K, p->n_e, g, (const MT *)p->map_csr, (const MT *)p->map_crac, values, p->ctx->d_status);
         } else {
-            k_atomic_elem<NLN, BB, MT, CRAC><<<fe_grid_for(p->n_e * 32, 256, sms, 8), 256, 0, s>>>(
+            k_atomic_elem<NLN, BB, MT, CRAC><<<fe_grid_resident(k_atomic_elem<NLN, BB, MT, CRAC>, p->n_e * 32, 256, sms),
+                                               256, 0, s>>>(
                 K, p->n_e, g, (const MT *)p->map_csr, (const MT *)p->map_crac, values);
         }
     } else {
-        k_atomic_generic<MT, CRAC><<<fe_grid_for(p->n_e * 32, 256, sms, 8), 256, 0, s>>>(
+        k_atomic_generic<MT, CRAC><<<fe_grid_resident(k_atomic_generic<MT, CRAC>, p->n_e * 32, 256, sms), 256, 0, s>>>(
             K, p->n_e, p->nln, p->B, g, (const MT *)p->map_csr, (const MT *)p->map_crac, values);
     }
     fe_note_launch();
@@ -1102,7 +1103,8 @@ int launch_gather(const fe_pattern *p, const double *K, double *values, int accu
         }
     } else {
         FE_TRY(configure_smem(k_gather_generic<MT, CRAC>, smem));
-        k_gather_generic<MT, CRAC><<<grid, W * 32, smem, s>>>(K, p->n_nodes, p->nln, p->B, g,
+        const int ggrid = fe_grid_resident(k_gather_generic<MT, CRAC>, p->n_nodes * 32, W * 32, sms, smem);
+        k_gather_generic<MT, CRAC><<<ggrid, W * 32, smem, s>>>(K, p->n_nodes, p->nln, p->B, g,
                                                               (const MT *)p->map_csr, (const MT *)p->map_crac,
                                                               cap, accumulate, values);
     }

@@ -161,25 +161,25 @@ int fe_assemble_rowlock(const fe_pattern *p, const double *K, double *values, in
     if (p->n_e == 0) return FE_OK;
     const Geo g = geo_of(p);
     int64_t *locks = crac ? p->crac_ptr : p->row_ptr;  // the row pointers are the locks (restored on exit)
-    const int grid = fe_grid_for(p->n_e * 32, 256, p->ctx->num_sms, 8);
+    const int sms = p->ctx->num_sms;
     int *st = p->ctx->d_status;
 #define FE_RL(NLN_, BB_)                                                                                            \
     do {                                                                                                            \
         if (p->map_bytes == 1) {                                                                                    \
             if (crac)                                                                                               \
-                k_rowlock<NLN_, BB_, uint8_t, true><<<grid, 256, 0, s>>>(K, p->n_e, g, (const uint8_t *)p->map_csr,  \
+                k_rowlock<NLN_, BB_, uint8_t, true><<<fe_grid_resident(k_rowlock<NLN_, BB_, uint8_t, true>, p->n_e * 32, 256, sms), 256, 0, s>>>(K, p->n_e, g, (const uint8_t *)p->map_csr,  \
                                                                          (const uint8_t *)p->map_crac, locks,        \
                                                                          values, st);                                \
             else                                                                                                    \
-                k_rowlock<NLN_, BB_, uint8_t, false><<<grid, 256, 0, s>>>(K, p->n_e, g, (const uint8_t *)p->map_csr, \
+                k_rowlock<NLN_, BB_, uint8_t, false><<<fe_grid_resident(k_rowlock<NLN_, BB_, uint8_t, false>, p->n_e * 32, 256, sms), 256, 0, s>>>(K, p->n_e, g, (const uint8_t *)p->map_csr, \
                                                                           (const uint8_t *)p->map_crac, locks,       \
                                                                           values, st);                               \
         } else {                                                                                                    \
             if (crac)                                                                                               \
-                k_rowlock<NLN_, BB_, uint16_t, true><<<grid, 256, 0, s>>>(                                           \
+                k_rowlock<NLN_, BB_, uint16_t, true><<<fe_grid_resident(k_rowlock<NLN_, BB_, uint16_t, true>, p->n_e * 32, 256, sms), 256, 0, s>>>(                                           \
                     K, p->n_e, g, (const uint16_t *)p->map_csr, (const uint16_t *)p->map_crac, locks, values, st);   \
             else                                                                                                    \
-                k_rowlock<NLN_, BB_, uint16_t, false><<<grid, 256, 0, s>>>(                                          \
+                k_rowlock<NLN_, BB_, uint16_t, false><<<fe_grid_resident(k_rowlock<NLN_, BB_, uint16_t, false>, p->n_e * 32, 256, sms), 256, 0, s>>>(                                          \
                     K, p->n_e, g, (const uint16_t *)p->map_csr, (const uint16_t *)p->map_crac, locks, values, st);   \
         }                                                                                                           \
     } while (0)
@@ -189,20 +189,20 @@ int fe_assemble_rowlock(const fe_pattern *p, const double *K, double *values, in
     else if (p->nln == 4 && p->B == 1) FE_RL(4, 1);
     else if (p->map_bytes == 1) {
         if (crac)
-            k_rowlock_generic<uint8_t, true><<<grid, 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
+            k_rowlock_generic<uint8_t, true><<<fe_grid_resident(k_rowlock_generic<uint8_t, true>, p->n_e * 32, 256, sms), 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
                                                                   (const uint8_t *)p->map_csr,
                                                                   (const uint8_t *)p->map_crac, locks, values, st);
         else
-            k_rowlock_generic<uint8_t, false><<<grid, 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
+            k_rowlock_generic<uint8_t, false><<<fe_grid_resident(k_rowlock_generic<uint8_t, false>, p->n_e * 32, 256, sms), 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
                                                                    (const uint8_t *)p->map_csr,
                                                                    (const uint8_t *)p->map_crac, locks, values, st);
     } else {
         if (crac)
-            k_rowlock_generic<uint16_t, true><<<grid, 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
+            k_rowlock_generic<uint16_t, true><<<fe_grid_resident(k_rowlock_generic<uint16_t, true>, p->n_e * 32, 256, sms), 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
                                                                    (const uint16_t *)p->map_csr,
                                                                    (const uint16_t *)p->map_crac, locks, values, st);
         else
-            k_rowlock_generic<uint16_t, false><<<grid, 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
+            k_rowlock_generic<uint16_t, false><<<fe_grid_resident(k_rowlock_generic<uint16_t, false>, p->n_e * 32, 256, sms), 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
                                                                     (const uint16_t *)p->map_csr,
                                                                     (const uint16_t *)p->map_crac, locks, values, st);
     }

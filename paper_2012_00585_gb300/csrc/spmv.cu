@@ -14,59 +14,107 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// One warp per row, rows strided by all warps; the next row's pointers are
+// loaded one row ahead, and the entries are taken 128 at a time: column
+// indices and values of four 32-entry windows first, then the x gathers, then
+// the products (in window order, so the sum order is fixed).
 __global__ void __launch_bounds__(256) k_spmv_csr(int64_t n_rows, const int64_t *__restrict__ row_ptr,
                                                   const int32_t *__restrict__ col_idx,
                                                   const double *__restrict__ values, const double *__restrict__ x,
                                                   double *__restrict__ y)
 {
     const int lane = threadIdx.x & 31;
-    for (int64_t i = fe_warp_id(); i < n_rows; i += fe_warps()) {
-        const int64_t a = row_ptr[i], b = row_ptr[i + 1];
+    const int64_t W = fe_warps();
+    int64_t i = fe_warp_id();
+    int64_t a = 0, b = 0;
+    if (i < n_rows) {
+        a = row_ptr[i];
+        b = row_ptr[i + 1];
+    }
+    for (; i < n_rows; i += W) {
+        int64_t an = 0, bn = 0;
+        if (i + W < n_rows) {
+            an = row_ptr[i + W];
+            bn = row_ptr[i + W + 1];
+        }
         double s = 0.0;
-        for (int64_t k = a + lane; k < b; k += 32) s += __ldcs(values + k) * __ldg(x + __ldcs(col_idx + k));
+        for (int64_t k0 = a; k0 < b; k0 += 128) {
+            int32_t c[4];
+            double v[4], xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t k = k0 + 32 * u + lane;
+                c[u] = k < b ? __ldcs(col_idx + k) : -1;
+                v[u] = k < b ? __ldcs(values + k) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s += v[u] * xv[u];
+        }
         s = warp_sum(s);
         if (lane == 0) y[i] = s;
+        a = an;
+        b = bn;
     }
 }
 
-// The row's pairs are read 32 at a time (lane r holds pair r); the run of
-// value position p is the last pair whose position is <= p, found by a
-// five-step binary search over the lanes (every lane takes part in every
-// shuffle: the loop over positions has the same trip count on all lanes).
+// CRAC: the row's value positions are taken 32 at a time, p = base + lane
+// (values coalesced).  The pairs of up to 32 runs are held one per lane; the
+// run of each position comes from a ballot of the runs starting inside the
+// window and a population count (the run holding the window's first position
+// is the last one starting at or before it).  Row starts (first value
+// position and pair range) are loaded one row ahead.  The product order per
+// lane is fixed: reproducible run to run.
 __global__ void __launch_bounds__(256) k_spmv_crac(int64_t n_rows, const int64_t *__restrict__ crac_ptr,
                                                    const int32_t *__restrict__ col_align,
                                                    const double *__restrict__ values, const double *__restrict__ x,
                                                    double *__restrict__ y)
 {
     const int lane = threadIdx.x & 31;
-    for (int64_t i = fe_warp_id(); i < n_rows; i += fe_warps()) {
-        const int64_t pa = crac_ptr[i], pb = crac_ptr[i + 1];
+    const int64_t W = fe_warps();
+    int64_t i = fe_warp_id();
+    int64_t pa = 0, pb = 0;
+    if (i < n_rows) {
+        pa = crac_ptr[i];
+        pb = crac_ptr[i + 1];
+    }
+    for (; i < n_rows; i += W) {
+        int64_t pan = 0, pbn = 0;
+        if (i + W < n_rows) {
+            pan = crac_ptr[i + W];
+            pbn = crac_ptr[i + W + 1];
+        }
         const int n_runs = (int)((pb - pa) >> 1);
         double s = 0.0;
         for (int r0 = 0; r0 < n_runs; r0 += 32) {
             const int r = r0 + lane;
-            const int last = min(32, n_runs - r0);  // runs in this group
+            const int last = min(32, n_runs - r0);  // runs held in this group
             const int32_t first = r < n_runs ? col_align[pa + 2 * r] : 0;
             const int32_t pos = r < n_runs ? col_align[pa + 2 * r + 1] : INT32_MAX;
-            // value positions of the group: from its first run to the next pair's position
             const int32_t p0 = __shfl_sync(0xffffffffu, pos, 0);
-            const int32_t pend = col_align[pa + 2 * (r0 + last) + 1];
+            const int32_t pend = col_align[pa + 2 * (r0 + last) + 1];  // next pair's position
             for (int32_t base = p0; base < pend; base += 32) {
-                const int32_t p = base + lane;
-                int lo = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int cand = lo + step;
-                    const int32_t pc = __shfl_sync(0xffffffffu, pos, cand < 32 ? cand : 31);
-                    if (cand < last && pc <= p) lo = cand;
+                // runs of this group starting at or before the window's start, and inside it
+                const int before = __popc(__ballot_sync(0xffffffffu, lane < last && pos <= base)) - 1;
+                // bit o of `starts` set when a run of the group starts at base + o (o > 0)
+                uint32_t starts = 0;
+                {
+                    const int o = pos - base;
+                    const uint32_t mine = (lane < last && o > 0 && o < 32) ? (1u << o) : 0u;
+                    starts = __reduce_or_sync(0xffffffffu, mine);
                 }
-                const int32_t f = __shfl_sync(0xffffffffu, first, lo);
-                const int32_t ps = __shfl_sync(0xffffffffu, pos, lo);
+                const int k = before + __popc(starts & ((2u << lane) - 1u));
+                const int32_t f = __shfl_sync(0xffffffffu, first, k);
+                const int32_t ps = __shfl_sync(0xffffffffu, pos, k);
+                const int32_t p = base + lane;
                 if (p < pend) s += __ldcs(values + p) * __ldg(x + f + (p - ps));
             }
         }
         s = warp_sum(s);
         if (lane == 0) y[i] = s;
+        pa = pan;
+        pb = pbn;
     }
 }
 
@@ -80,9 +128,12 @@ int spmv(fe_ctx *ctx, const fe_pattern *p, const double *values, const double *x
     if (prev != ctx->device) cudaSetDevice(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (p->n_dofs > 0) {
-        const int grid = fe_grid_for(p->n_dofs * 32, 256, ctx->num_sms, 8);
-        if (crac) k_spmv_crac<<<grid, 256, 0, s>>>(p->n_dofs, p->crac_ptr, p->col_align, values, x, y);
-        else k_spmv_csr<<<grid, 256, 0, s>>>(p->n_dofs, p->row_ptr, p->col_idx, values, x, y);
+        if (crac)
+            k_spmv_crac<<<fe_grid_resident(k_spmv_crac, p->n_dofs * 32, 256, ctx->num_sms), 256, 0, s>>>(
+                p->n_dofs, p->crac_ptr, p->col_align, values, x, y);
+        else
+            k_spmv_csr<<<fe_grid_resident(k_spmv_csr, p->n_dofs * 32, 256, ctx->num_sms), 256, 0, s>>>(
+                p->n_dofs, p->row_ptr, p->col_idx, values, x, y);
         fe_note_launch();
     }
     const cudaError_t e = cudaGetLastError();

@@ -149,6 +149,7 @@ def load():
             "fe_device_status": (i, [vp, vp]),
             "fe_tune_set": (i, [vp, i, i]),
             "fe_hbm_probe": (i, [vp, vp, vp, i64, vp]),
+            "fe_hbm_probe_bulk": (i, [vp, vp, i64, vp]),
             "fe_tune_get": (i, [vp, i, ctypes.POINTER(i)]),
             "fe_pattern_build": (i, [vp, i64, i32, i64, vp, u32, vp, pp]),
             "fe_pattern_free": (i, [vp]),
@@ -237,6 +238,11 @@ def fe_device_status(ctx, stream=None) -> int:
 def fe_hbm_probe(ctx, src, dst=None, n=None, stream=None):
     n = src.numel() if n is None else n
     _check(load().fe_hbm_probe(ctx, _addr(src), _addr(dst), int(n), _stream(stream)), "fe_hbm_probe")
+
+
+def fe_hbm_probe_bulk(ctx, src, n=None, stream=None):
+    n = src.numel() if n is None else n
+    _check(load().fe_hbm_probe_bulk(ctx, _addr(src), int(n), _stream(stream)), "fe_hbm_probe_bulk")
 
 
 def fe_tune_set(ctx, knob: int, value: int):

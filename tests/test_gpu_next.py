@@ -23,8 +23,16 @@ def ctx():
     feasm.fe_destroy(c)
 
 
+def _scattered():
+    """200 elements of 6 random DOFs out of 300: unused DOFs give empty rows."""
+    rng = np.random.default_rng(5)
+    D = np.stack([rng.choice(300, size=6, replace=False) for _ in range(200)]).astype(np.int32)
+    assert len(np.unique(D)) < 300
+    return D, 300
+
+
 MESHES = [("hex5_d3", *wl.hex_q1_grid(5, 3)), ("tet3_d3", *wl.tet_p2_kuhn(3, d=3, seed=2)),
-          ("quad9", *wl.quad_q1_grid(9, 1)), ("hex4_d1", *wl.hex_q1_grid(4, 1))]
+          ("quad9", *wl.quad_q1_grid(9, 1)), ("hex4_d1", *wl.hex_q1_grid(4, 1)), ("scattered", *_scattered())]
 
 
 @pytest.mark.parametrize("name,D,n_dofs", MESHES, ids=[m[0] for m in MESHES])
