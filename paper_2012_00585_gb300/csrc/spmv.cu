@@ -1,118 +1,114 @@
 // Sparse matrix-vector product y = G x over the assembled matrix, through
 // CSR (column index per value) and through CRAC (one (first column, value
 // position) pair per run of consecutive columns, §2.2): the consumer of the
-// assembled matrix that the paper's outlook names.  One warp per row; each
-// lane's products are summed in a fixed order (lane-strided partial sums,
-// then a fixed shuffle tree), so results are reproducible run to run.
+// assembled matrix that the paper's outlook names.  A group of lanes per row;
+// each lane's products are summed in a fixed order (lane-strided partial
+// sums, then a fixed shuffle tree), so results are reproducible run to run.
 #include "internal.cuh"
 
 namespace {
 
-__device__ __forceinline__ double warp_sum(double v)
+// G lanes per row (32/G rows per warp; on GB300 the FP64 pipe, not memory,
+// limits a warp-per-row product: a warp-wide reduction per row costs more
+// adds than the row has entries).  Row groups are strided by all warps; the
+// next group's pointers are loaded one group ahead.  Each lane sums its
+// entries k = a + lane, a + lane + G, ... in order, then a fixed shuffle tree
+// over the G lanes: the sum order is fixed (reproducible run to run).
+constexpr int SPMV_G = 8;
+
+template <int G>
+__device__ __forceinline__ double group_sum(double v)
 {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// One warp per row, rows strided by all warps; the next row's pointers are
-// loaded one row ahead, and the entries are taken 128 at a time: column
-// indices and values of four 32-entry windows first, then the x gathers, then
-// the products (in window order, so the sum order is fixed).
 __global__ void __launch_bounds__(256) k_spmv_csr(int64_t n_rows, const int64_t *__restrict__ row_ptr,
                                                   const int32_t *__restrict__ col_idx,
                                                   const double *__restrict__ values, const double *__restrict__ x,
                                                   double *__restrict__ y)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t W = fe_warps();
-    int64_t i = fe_warp_id();
+    constexpr int G = SPMV_G, R = 32 / G;
+    const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
+    const int64_t stride = fe_warps() * R;
+    int64_t i = fe_warp_id() * R + sub;
     int64_t a = 0, b = 0;
     if (i < n_rows) {
         a = row_ptr[i];
         b = row_ptr[i + 1];
     }
-    for (; i < n_rows; i += W) {
+    for (int64_t base = fe_warp_id() * R; base < n_rows; base += stride, i += stride) {
         int64_t an = 0, bn = 0;
-        if (i + W < n_rows) {
-            an = row_ptr[i + W];
-            bn = row_ptr[i + W + 1];
+        if (i + stride < n_rows) {
+            an = row_ptr[i + stride];
+            bn = row_ptr[i + stride + 1];
         }
         double s = 0.0;
-        for (int64_t k0 = a; k0 < b; k0 += 128) {
+        for (int64_t k0 = a + gl; k0 < b; k0 += 4 * G) {
             int32_t c[4];
-            double v[4], xv[4];
+            double v[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int64_t k = k0 + 32 * u + lane;
+                const int64_t k = k0 + u * G;
                 c[u] = k < b ? __ldcs(col_idx + k) : -1;
                 v[u] = k < b ? __ldcs(values + k) : 0.0;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : 0.0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) s += v[u] * xv[u];
+            for (int u = 0; u < 4; ++u)
+                if (c[u] >= 0) s += v[u] * __ldg(x + c[u]);
         }
-        s = warp_sum(s);
-        if (lane == 0) y[i] = s;
+        s = group_sum<G>(s);
+        if (gl == 0 && i < n_rows) y[i] = s;
         a = an;
         b = bn;
     }
 }
 
-// CRAC: the row's value positions are taken 32 at a time, p = base + lane
-// (values coalesced).  The pairs of up to 32 runs are held one per lane; the
-// run of each position comes from a ballot of the runs starting inside the
-// window and a population count (the run holding the window's first position
-// is the last one starting at or before it).  Row starts (first value
-// position and pair range) are loaded one row ahead.  The product order per
-// lane is fixed: reproducible run to run.
+// CRAC: the same G lanes per row over the value positions p (coalesced);
+// each lane walks the row's runs with its positions (the pairs are read
+// through L1; runs are rarely shorter than G, so a lane moves about one run
+// per step).  The column of p is first + (p - pos) of its run.
 __global__ void __launch_bounds__(256) k_spmv_crac(int64_t n_rows, const int64_t *__restrict__ crac_ptr,
                                                    const int32_t *__restrict__ col_align,
                                                    const double *__restrict__ values, const double *__restrict__ x,
                                                    double *__restrict__ y)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t W = fe_warps();
-    int64_t i = fe_warp_id();
+    constexpr int G = SPMV_G, R = 32 / G;
+    const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
+    const int64_t stride = fe_warps() * R;
+    int64_t i = fe_warp_id() * R + sub;
     int64_t pa = 0, pb = 0;
     if (i < n_rows) {
         pa = crac_ptr[i];
         pb = crac_ptr[i + 1];
     }
-    for (; i < n_rows; i += W) {
+    for (int64_t base = fe_warp_id() * R; base < n_rows; base += stride, i += stride) {
         int64_t pan = 0, pbn = 0;
-        if (i + W < n_rows) {
-            pan = crac_ptr[i + W];
-            pbn = crac_ptr[i + W + 1];
+        if (i + stride < n_rows) {
+            pan = crac_ptr[i + stride];
+            pbn = crac_ptr[i + stride + 1];
         }
-        const int n_runs = (int)((pb - pa) >> 1);
         double s = 0.0;
-        for (int r0 = 0; r0 < n_runs; r0 += 32) {
-            const int r = r0 + lane;
-            const int last = min(32, n_runs - r0);  // runs held in this group
-            const int32_t first = r < n_runs ? col_align[pa + 2 * r] : 0;
-            const int32_t pos = r < n_runs ? col_align[pa + 2 * r + 1] : INT32_MAX;
-            const int32_t p0 = __shfl_sync(0xffffffffu, pos, 0);
-            const int32_t pend = col_align[pa + 2 * (r0 + last) + 1];  // next pair's position
-            for (int32_t base = p0; base < pend; base += 32) {
-                // runs of this group starting at or before the window's start, and inside it
-                const int before = __popc(__ballot_sync(0xffffffffu, lane < last && pos <= base)) - 1;
-                // bit o of `starts` set when a run of the group starts at base + o (o > 0)
-                uint32_t starts = 0;
-                {
-                    const int o = pos - base;
-                    const uint32_t mine = (lane < last && o > 0 && o < 32) ? (1u << o) : 0u;
-                    starts = __reduce_or_sync(0xffffffffu, mine);
+        if (pb > pa) {
+            // run r: (first, pos) at pa + 2r; its end is the position of the next pair
+            // (the next row's first pair, or the final pair, after the last run)
+            int64_t r2 = pa;
+            int32_t first = __ldg(col_align + r2), pos = __ldg(col_align + r2 + 1);
+            int32_t next = __ldg(col_align + r2 + 3);
+            const int32_t pend = __ldg(col_align + pb + 1);
+            for (int32_t p = pos + gl; p < pend; p += G) {
+                while (p >= next) {
+                    r2 += 2;
+                    first = __ldg(col_align + r2);
+                    pos = __ldg(col_align + r2 + 1);
+                    next = __ldg(col_align + r2 + 3);
                 }
-                const int k = before + __popc(starts & ((2u << lane) - 1u));
-                const int32_t f = __shfl_sync(0xffffffffu, first, k);
-                const int32_t ps = __shfl_sync(0xffffffffu, pos, k);
-                const int32_t p = base + lane;
-                if (p < pend) s += __ldcs(values + p) * __ldg(x + f + (p - ps));
+                s += __ldcs(values + p) * __ldg(x + first + (p - pos));
             }
         }
-        s = warp_sum(s);
-        if (lane == 0) y[i] = s;
+        s = group_sum<G>(s);
+        if (gl == 0 && i < n_rows) y[i] = s;
         pa = pan;
         pb = pbn;
     }
@@ -128,11 +124,12 @@ int spmv(fe_ctx *ctx, const fe_pattern *p, const double *values, const double *x
     if (prev != ctx->device) cudaSetDevice(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (p->n_dofs > 0) {
+        const int64_t work = (p->n_dofs + 32 / SPMV_G - 1) / (32 / SPMV_G) * 32;  // threads: one warp per row group
         if (crac)
-            k_spmv_crac<<<fe_grid_resident(k_spmv_crac, p->n_dofs * 32, 256, ctx->num_sms), 256, 0, s>>>(
+            k_spmv_crac<<<fe_grid_resident(k_spmv_crac, work, 256, ctx->num_sms), 256, 0, s>>>(
                 p->n_dofs, p->crac_ptr, p->col_align, values, x, y);
         else
-            k_spmv_csr<<<fe_grid_resident(k_spmv_csr, p->n_dofs * 32, 256, ctx->num_sms), 256, 0, s>>>(
+            k_spmv_csr<<<fe_grid_resident(k_spmv_csr, work, 256, ctx->num_sms), 256, 0, s>>>(
                 p->n_dofs, p->row_ptr, p->col_idx, values, x, y);
         fe_note_launch();
     }
