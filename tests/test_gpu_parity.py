@@ -389,3 +389,22 @@ def test_every_kernel_variant(ctx, gkind, akind):
         feasm.fe_tune_set(ctx, feasm.FE_KNOB_GATHER_KERNEL, 0)
         feasm.fe_tune_set(ctx, feasm.FE_KNOB_ATOMIC_KERNEL, 0)
         feasm.fe_tune_set(ctx, feasm.FE_KNOB_GATHER_STAGES, 0)
+
+
+@pytest.mark.parametrize("fmt", ["csr", "crac"])
+def test_signed_zero_contributions(ctx, fmt):
+    """Listing 2 starts every slot at +0.0: a slot whose contributions are all
+    -0.0 sums to +0.0, and a -0.0 first term does not leave a -0.0 behind.
+    The deterministic path must give the same bits."""
+    from paper_2012_00585_gb300 import feasm
+    for D, n_dofs in (wl.hex_q1_grid(4, 3), wl.tet_p2_kuhn(2, d=3, seed=3)):
+        n_e, n_loc = D.shape
+        K = np.full((n_e, n_loc, n_loc), -0.0)
+        K[1::3] = wl.random_matrices((n_e + 1) // 3, n_loc, seed=9)[: K[1::3].shape[0]]
+        g = gu.GpuAssembly(ctx, D, n_dofs)
+        rp, ci = oracle.csr_pattern(D, n_dofs)
+        exp = oracle.assemble_csr(D, K, rp, ci)
+        assert np.any(np.signbit(K)) and not np.any(np.signbit(exp[exp == 0]))
+        got = g.assemble(K, fmt, feasm.FE_DETERMINISTIC).cpu().numpy()
+        assert np.array_equal(got.view(np.uint64), exp.view(np.uint64))
+        g.free()
