@@ -162,6 +162,10 @@ uint64_t fe_kernel_launches(void);
 #define FE_KNOB_ATOMIC_WARPS 4   /* warps per block of the staged kernel     */
 #define FE_KNOB_GATHER_STAGES 5  /* ring stages per warp of gather kernel 4:
                                     2..8 (0: 4)                              */
+#define FE_KNOB_LOCK_SPIN 6      /* FE_ROWLOCK: a lock is given up after
+                                    2^value compare-and-swap attempts, 4..24
+                                    (0: 2^22); the row is then skipped and
+                                    FE_ERR_TIMEOUT recorded                  */
 #define FE_KNOB_COUNT 8
 
 /* Set / read one schedule knob.  FE_ERR_INVALID_ARG for an unknown knob or a
@@ -330,6 +334,12 @@ int fe_spmv_crac(fe_ctx *ctx, const fe_pattern *pattern, const double *values, c
 #define FE_SCHED_THREAD_PER_ENTRY 2  /* FE_ATOMIC: a thread per K entry        */
 #define FE_SCHED_BLOCK_PER_ELEMENT 3 /* FE_ATOMIC: a thread block per element  */
 #define FE_SCHED_WARP_PER_ROW 4      /* FE_DETERMINISTIC: a warp per node row  */
+#define FE_SCHED_WARP_PER_ELEMENT_TMA 5 /* FE_ATOMIC: a warp per element, K_e
+                                       moved into shared memory by one bulk
+                                       copy (TMA), double-buffered; items
+                                       with n_loc > 32, a generic shape or a
+                                       K not 16-byte aligned take the
+                                       warp-per-element path               */
 
 typedef struct fe_schedule {
     int32_t kind;  /* FE_SCHED_*                                               */

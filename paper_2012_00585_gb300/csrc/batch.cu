@@ -21,6 +21,7 @@
 
 #include "assemble_body.cuh"
 #include "internal.cuh"
+#include "tma.cuh"
 
 using namespace fe_dev;
 
@@ -38,6 +39,7 @@ struct BatchItemDev {
     int64_t nnz;
     int64_t tile_begin;  // first global tile of this item
     int32_t nln, B, shape, map_bytes;
+    int32_t staged;      // FE_SCHED_WARP_PER_ELEMENT_TMA: K_e moved by a bulk copy
 };
 
 int shape_of(const fe_pattern *p)
@@ -66,6 +68,113 @@ __device__ __noinline__ void atomic_elem_call(const BatchItemDev *__restrict__ i
 {
     const Geo g = it->g;
     atomic_element<NLN, BB, MT, CRAC>(it->K, e, g, (const MT *)it->map, (const MT *)it->mapc, it->values, lane);
+}
+
+// FE_SCHED_WARP_PER_ELEMENT_TMA: elements [u0, u1) of one item through the
+// warp's two stages (kst, bar; phase bit s = parity of the next wait on stage
+// s).  While element e is added, the copy of e+1 is in flight; the tables
+// of e (row starts; block positions, or run positions and the run index /
+// offset of every column block) are loaded while its own copy lands, then
+// every entry is one atomic add.  tab holds NLN*NLN + 2*NLN ints.  Returns
+// false when a wait ran out (after waiting, bounded, for the copy in flight).
+template <int NLN, int BB, typename MT, bool CRAC>
+__device__ __noinline__ bool staged_tile(const BatchItemDev *__restrict__ it, int64_t u0, int64_t u1, int lane,
+                                         double *kst, int stage, uint64_t *bar, uint32_t *phase_io, int64_t *base_s,
+                                         int32_t *tab, uint64_t pol)
+{
+    constexpr int NLOC = NLN * BB;
+    constexpr int NN = NLOC * NLOC;
+    constexpr int IT = (NN + 31) / 32;
+    constexpr uint32_t NNB = NN * 8;
+    const Geo g = it->g;
+    const double *K = it->K;
+    double *values = it->values;
+    const MT *map = (const MT *)it->map;
+    const MT *mapc = (const MT *)it->mapc;
+    int32_t *pos_s = tab;               // [NLN*NLN] block positions (CRAC: run positions)
+    int32_t *kk_s = pos_s + NLN * NLN;  // CRAC: run index | run count << 16, per column block
+    int32_t *off_s = kk_s + NLN;        // CRAC: offset inside the run
+    uint32_t phase = *phase_io;
+    auto issue = [&](int64_t e, int s_) {
+        if (lane == 0) {
+            fe_fence_proxy_async();
+            fe_mbar_expect_tx(&bar[s_], NNB);
+            fe_bulk_g2s(kst + (size_t)s_ * stage, K + e * NN, NNB, &bar[s_], pol);
+        }
+    };
+    int st = 0;
+    issue(u0, st);
+    for (int64_t e = u0; e < u1; ++e) {
+        const bool next = e + 1 < u1;
+        if (next) issue(e + 1, st ^ 1);
+        if (lane < NLOC) {
+            const int64_t row = (int64_t)BB * g.N[e * NLN + lane / BB] + lane % BB;
+            base_s[lane] = CRAC ? crac_row_base(g, row) : g.row_ptr[row];
+        }
+        if (!CRAC) {
+            for (int q = lane; q < NLN * NLN; q += 32) pos_s[q] = (int)map[e * NLN * NLN + q];
+        } else {
+            int64_t rp;
+            int nr;
+            if (g.uniform_R) {
+                nr = g.uniform_R;
+                rp = e * nr;
+            } else {
+                rp = g.run_ptr[e];
+                nr = (int)(g.run_ptr[e + 1] - rp);
+            }
+            const uint32_t m = g.uniform_R ? g.run_mask[0] : g.run_mask[e];
+            for (int q = lane; q < NLN * nr; q += 32) pos_s[q] = (int)mapc[rp * NLN + q];
+            if (lane < NLN) {
+                int k, off;
+                run_of(m, lane, k, off);
+                kk_s[lane] = k | (nr << 16);
+                off_s[lane] = off;
+            }
+        }
+        if (!__all_sync(0xffffffffu, fe_mbar_wait(&bar[st], (phase >> st) & 1u))) {
+            fe_mbar_wait(&bar[st], (phase >> st) & 1u);  // once more, bounded, for the copy itself
+            if (next) fe_mbar_wait(&bar[st ^ 1], (phase >> (st ^ 1)) & 1u);
+            *phase_io = phase;
+            return false;
+        }
+        phase ^= 1u << st;
+        __syncwarp();
+        const double *stg = kst + (size_t)st * stage;
+#pragma unroll 6
+        for (int j = 0; j < IT; ++j) {
+            const int q = lane + 32 * j;
+            if (q < NN) {
+                const int r = q / NLOC, c = q % NLOC;
+                const int kc = c / BB;
+                int pos;
+                if (!CRAC) {
+                    pos = pos_s[(r / BB) * NLN + kc];
+                } else {
+                    const int kw = kk_s[kc];
+                    pos = pos_s[(r / BB) * (kw >> 16) + (kw & 0xffff)] + off_s[kc];
+                }
+                atomicAdd(values + base_s[r] + BB * pos + c % BB, stg[q]);
+            }
+        }
+        __syncwarp();
+        st ^= 1;
+    }
+    *phase_io = phase;
+    return true;
+}
+
+template <typename MT, bool CRAC>
+__device__ __forceinline__ bool staged_tile_any(const BatchItemDev *it, int shape, int64_t u0, int64_t u1, int lane,
+                                                double *kst, int stage, uint64_t *bar, uint32_t *phase,
+                                                int64_t *base_s, int32_t *tab, uint64_t pol)
+{
+    switch (shape) {
+    case SH_4_1: return staged_tile<4, 1, MT, CRAC>(it, u0, u1, lane, kst, stage, bar, phase, base_s, tab, pol);
+    case SH_8_1: return staged_tile<8, 1, MT, CRAC>(it, u0, u1, lane, kst, stage, bar, phase, base_s, tab, pol);
+    case SH_8_3: return staged_tile<8, 3, MT, CRAC>(it, u0, u1, lane, kst, stage, bar, phase, base_s, tab, pol);
+    default: return staged_tile<10, 3, MT, CRAC>(it, u0, u1, lane, kst, stage, bar, phase, base_s, tab, pol);
+    }
 }
 
 template <typename MT, bool CRAC>
@@ -147,10 +256,21 @@ __device__ __forceinline__ int64_t entry_slot(const BatchItemDev &it, int64_t e,
 
 constexpr int SCHED_THREADS = 256;
 
+// Shared memory of the warp-level schedules before the bulk-copy stages:
+// per warp FE_MAX_NLOC row starts and 2 x FE_MAX_NLOC run entries.
+__host__ __device__ constexpr size_t batch_tables_bytes(int warps)
+{
+    return (size_t)warps * FE_MAX_NLOC * 8 + (size_t)warps * 2 * FE_MAX_NLOC * 4;
+}
+
+// Block size of a schedule (one size for all; 4-warp blocks of the
+// bulk-copy schedule measured slower).
+constexpr int sched_threads(int) { return SCHED_THREADS; }
+
 template <bool CRAC, int SCHED>
 __global__ void __launch_bounds__(SCHED_THREADS) k_batch(const BatchItemDev *__restrict__ items, int n_items,
                                                          int64_t total_tiles, int tile, int cap, int accumulate,
-                                                         unsigned long long *counter)
+                                                         unsigned long long *counter, int stage, int *status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long block_tile;
@@ -204,37 +324,78 @@ __global__ void __launch_bounds__(SCHED_THREADS) k_batch(const BatchItemDev *__r
         return;
     }
     // warp-level schedules
+    const int nw = blockDim.x >> 5;
     double *acc = (double *)smem_raw + (size_t)wib * cap;                       // deterministic
     int64_t *base_s = (int64_t *)smem_raw + (size_t)wib * FE_MAX_NLOC;          // atomic, generic shapes
-    int32_t *k_s = (int32_t *)((int64_t *)smem_raw + (size_t)(SCHED_THREADS / 32) * FE_MAX_NLOC) +
-                   (size_t)wib * 2 * FE_MAX_NLOC;
+    int32_t *k_s = (int32_t *)((int64_t *)smem_raw + (size_t)nw * FE_MAX_NLOC) + (size_t)wib * 2 * FE_MAX_NLOC;
     int32_t *off_s = k_s + FE_MAX_NLOC;
-    for (;;) {
-        unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(counter, 1ull);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= (unsigned long long)total_tiles) break;
-        const BatchItemDev &it = items[find_item(items, n_items, (int64_t)t)];
-        const int64_t u0 = ((int64_t)t - it.tile_begin) * tile, u1 = min(u0 + tile, it.units);
-        if (SCHED == FE_SCHED_WARP_PER_ROW) {
-            for (int64_t v = u0; v < u1; ++v) {
-                if (it.map_bytes == 1) gather_row_any<uint8_t, CRAC>(&it, it.shape, v, acc, accumulate, lane);
-                else gather_row_any<uint16_t, CRAC>(&it, it.shape, v, acc, accumulate, lane);
+    // FE_SCHED_WARP_PER_ELEMENT_TMA: two stages of `stage` doubles and two
+    // mbarriers per warp, after the tables
+    double *kst = (double *)(smem_raw + batch_tables_bytes(nw)) + (size_t)wib * 2 * stage;
+    uint64_t *bar = (uint64_t *)(smem_raw + batch_tables_bytes(nw) + (size_t)nw * 2 * stage * 8) + 2 * wib;
+    if constexpr (SCHED == FE_SCHED_WARP_PER_ELEMENT_TMA) {
+        // tiles from the counter; a staged item's tile goes through the
+        // warp's two stages in one call, other items take the register path
+        if (lane == 0) {
+            fe_mbar_init(&bar[0], 1);
+            fe_mbar_init(&bar[1], 1);
+            fe_fence_mbar_init();
+        }
+        __syncwarp();
+        const uint64_t pol = fe_policy_evict_first();
+        uint32_t phase = 0;
+        for (;;) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(counter, 1ull);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= (unsigned long long)total_tiles) break;
+            const BatchItemDev &it = items[find_item(items, n_items, (int64_t)t)];
+            const int64_t u0 = ((int64_t)t - it.tile_begin) * tile, u1 = min(u0 + tile, it.units);
+            if (it.staged) {
+                const bool ok = it.map_bytes == 1
+                                    ? staged_tile_any<uint8_t, CRAC>(&it, it.shape, u0, u1, lane, kst, stage, bar,
+                                                                     &phase, base_s, k_s, pol)
+                                    : staged_tile_any<uint16_t, CRAC>(&it, it.shape, u0, u1, lane, kst, stage, bar,
+                                                                      &phase, base_s, k_s, pol);
+                if (!ok) {
+                    if (lane == 0) atomicCAS(status, 0, FE_ERR_TIMEOUT);
+                    return;
+                }
+            } else {
+                for (int64_t e = u0; e < u1; ++e) {
+                    if (it.map_bytes == 1) atomic_elem_any<uint8_t, CRAC>(&it, it.shape, e, lane, base_s, k_s, off_s);
+                    else atomic_elem_any<uint16_t, CRAC>(&it, it.shape, e, lane, base_s, k_s, off_s);
+                }
             }
-        } else if (SCHED == FE_SCHED_WARP_PER_ELEMENT) {
-            for (int64_t e = u0; e < u1; ++e) {
-                if (it.map_bytes == 1) atomic_elem_any<uint8_t, CRAC>(&it, it.shape, e, lane, base_s, k_s, off_s);
-                else atomic_elem_any<uint16_t, CRAC>(&it, it.shape, e, lane, base_s, k_s, off_s);
-            }
-        } else {  // thread per entry: the tile's entries spread over the lanes
-            const int n_loc = it.nln * it.B;
-            const int64_t NN = (int64_t)n_loc * n_loc;
-            for (int64_t x = u0 * NN + lane; x < u1 * NN; x += 32) {
-                const int64_t e = x / NN;
-                const int q = (int)(x - e * NN);
-                const int64_t slot = it.map_bytes == 1 ? entry_slot<uint8_t, CRAC>(it, e, q)
-                                                       : entry_slot<uint16_t, CRAC>(it, e, q);
-                atomicAdd(it.values + slot, __ldcs(it.K + x));
+        }
+    } else {
+        for (;;) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(counter, 1ull);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= (unsigned long long)total_tiles) break;
+            const BatchItemDev &it = items[find_item(items, n_items, (int64_t)t)];
+            const int64_t u0 = ((int64_t)t - it.tile_begin) * tile, u1 = min(u0 + tile, it.units);
+            if (SCHED == FE_SCHED_WARP_PER_ROW) {
+                for (int64_t v = u0; v < u1; ++v) {
+                    if (it.map_bytes == 1) gather_row_any<uint8_t, CRAC>(&it, it.shape, v, acc, accumulate, lane);
+                    else gather_row_any<uint16_t, CRAC>(&it, it.shape, v, acc, accumulate, lane);
+                }
+            } else if (SCHED == FE_SCHED_WARP_PER_ELEMENT) {
+                for (int64_t e = u0; e < u1; ++e) {
+                    if (it.map_bytes == 1) atomic_elem_any<uint8_t, CRAC>(&it, it.shape, e, lane, base_s, k_s, off_s);
+                    else atomic_elem_any<uint16_t, CRAC>(&it, it.shape, e, lane, base_s, k_s, off_s);
+                }
+            } else {  // thread per entry: the tile's entries spread over the lanes
+                const int n_loc = it.nln * it.B;
+                const int64_t NN = (int64_t)n_loc * n_loc;
+                for (int64_t x = u0 * NN + lane; x < u1 * NN; x += 32) {
+                    const int64_t e = x / NN;
+                    const int q = (int)(x - e * NN);
+                    const int64_t slot = it.map_bytes == 1 ? entry_slot<uint8_t, CRAC>(it, e, q)
+                                                           : entry_slot<uint16_t, CRAC>(it, e, q);
+                    atomicAdd(it.values + slot, __ldcs(it.K + x));
+                }
             }
         }
     }
@@ -254,8 +415,12 @@ __global__ void k_batch_zero(const BatchItemDev *__restrict__ items, int n_items
 struct Plan {
     std::vector<BatchItemDev> host;
     int64_t total_tiles = 0;
-    int cap = 1;  // doubles of accumulator per warp (deterministic)
+    int cap = 1;    // doubles of accumulator per warp (deterministic)
+    int stage = 0;  // doubles per bulk-copy stage (FE_SCHED_WARP_PER_ELEMENT_TMA)
 };
+
+// Largest K_e (doubles) a bulk-copy stage holds: 32 x 32.
+constexpr int STAGE_MAX = 32 * 32;
 
 int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mode, int tile, Plan &plan)
 {
@@ -283,56 +448,68 @@ int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
         d.B = p->B;
         d.shape = shape_of(p);
         d.map_bytes = p->map_bytes;
+        const int nn = p->n_loc * p->n_loc;
+        d.staged = d.shape != SH_GENERIC && nn <= STAGE_MAX && (nn * 8) % 16 == 0 &&
+                   ((uintptr_t)items[i].elem_mats & 15u) == 0;
+        if (d.staged) plan.stage = std::max(plan.stage, (nn + 1) & ~1);
         plan.total_tiles += (d.units + tile - 1) / tile;
         plan.cap = std::max(plan.cap, p->B * p->max_row_len);
     }
     return FE_OK;
 }
 
-size_t batch_smem(int mode, int sched, int cap)
+size_t batch_smem(int mode, int sched, int cap, int stage)
 {
     const int W = SCHED_THREADS / 32;
     if (mode == FE_DETERMINISTIC) return (size_t)W * cap * 8;
     if (sched == FE_SCHED_BLOCK_PER_ELEMENT) return (size_t)FE_MAX_NLOC * 16;
-    return (size_t)W * FE_MAX_NLOC * 8 + (size_t)W * 2 * FE_MAX_NLOC * 4;
+    if (sched == FE_SCHED_WARP_PER_ELEMENT_TMA) {
+        const int w = sched_threads(sched) / 32;
+        return batch_tables_bytes(w) + (size_t)w * 2 * stage * 8 + (size_t)w * 16;
+    }
+    return batch_tables_bytes(W);
 }
 
 template <bool CRAC, int SCHED>
 int launch_batch_t(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t total, int tile, int cap, int acc,
-                   unsigned long long *counter, size_t smem, cudaStream_t s)
+                   unsigned long long *counter, size_t smem, int stage, cudaStream_t s)
 {
     auto kern = k_batch<CRAC, SCHED>;
+    constexpr int threads = sched_threads(SCHED);
     if (smem > 48 * 1024) FE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SCHED_THREADS, smem));
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) return FE_ERR_UNSUPPORTED;
-    const int64_t want = SCHED == FE_SCHED_BLOCK_PER_ELEMENT ? total : (total + 7) / 8;
+    const int64_t want = SCHED == FE_SCHED_BLOCK_PER_ELEMENT ? total : (total + threads / 32 - 1) / (threads / 32);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * per_sm, want));
-    kern<<<grid, SCHED_THREADS, smem, s>>>(d_items, n, total, tile, cap, acc, counter);
+    kern<<<grid, threads, smem, s>>>(d_items, n, total, tile, cap, acc, counter, stage, ctx->d_status);
     fe_note_launch();
     FE_CUDA(cudaGetLastError());
     return FE_OK;
 }
 
 int launch_batch(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t total, int format, int mode, int acc,
-                 int sched, int tile, int cap, unsigned long long *counter, cudaStream_t s)
+                 int sched, int tile, int cap, int stage, unsigned long long *counter, cudaStream_t s)
 {
-    const size_t smem = batch_smem(mode, sched, cap);
+    const size_t smem = batch_smem(mode, sched, cap, stage);
     if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
     const bool crac = format == FE_FORMAT_CRAC;
     if (mode == FE_DETERMINISTIC)
-        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s)
-                    : launch_batch_t<false, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s);
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s);
     switch (sched) {
     case FE_SCHED_THREAD_PER_ENTRY:
-        return crac ? launch_batch_t<true, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s)
-                    : launch_batch_t<false, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s);
+        return crac ? launch_batch_t<true, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s)
+                    : launch_batch_t<false, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s);
     case FE_SCHED_BLOCK_PER_ELEMENT:
-        return crac ? launch_batch_t<true, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s)
-                    : launch_batch_t<false, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s);
+        return crac ? launch_batch_t<true, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s)
+                    : launch_batch_t<false, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s);
+    case FE_SCHED_WARP_PER_ELEMENT_TMA:
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s);
     default:
-        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s)
-                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, s);
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s);
     }
 }
 
@@ -341,7 +518,7 @@ bool sched_valid(int mode, const fe_schedule &sc)
     if (sc.tile < 1 || sc.tile > (1 << 20)) return false;
     if (mode == FE_DETERMINISTIC) return sc.kind == FE_SCHED_WARP_PER_ROW;
     return sc.kind == FE_SCHED_WARP_PER_ELEMENT || sc.kind == FE_SCHED_THREAD_PER_ENTRY ||
-           sc.kind == FE_SCHED_BLOCK_PER_ELEMENT;
+           sc.kind == FE_SCHED_BLOCK_PER_ELEMENT || sc.kind == FE_SCHED_WARP_PER_ELEMENT_TMA;
 }
 
 }  // namespace
@@ -385,7 +562,10 @@ std::tuple<int, int, uint64_t, int> signature(const fe_batch_item *items, int n,
 
 fe_schedule default_schedule(int mode)
 {
-    return mode == FE_DETERMINISTIC ? fe_schedule{FE_SCHED_WARP_PER_ROW, 64} : fe_schedule{FE_SCHED_WARP_PER_ELEMENT, 64};
+    // measured on 256 hex meshes (n ~ logU[8,48]): tiles of 8 elements keep the warps on
+    // neighbouring elements (atomics hit L2) at few tile fetches
+    return mode == FE_DETERMINISTIC ? fe_schedule{FE_SCHED_WARP_PER_ROW, 64}
+                                    : fe_schedule{FE_SCHED_WARP_PER_ELEMENT_TMA, 8};
 }
 
 struct DeviceScope {
@@ -422,7 +602,7 @@ int run_batch(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
         if (cudaGetLastError() != cudaSuccess) rc = FE_ERR_DEVICE;
     }
     if (rc == FE_OK && plan.total_tiles > 0)
-        rc = launch_batch(ctx, d_items, n, plan.total_tiles, format, mode, acc, sc.kind, sc.tile, plan.cap, counter, s);
+        rc = launch_batch(ctx, d_items, n, plan.total_tiles, format, mode, acc, sc.kind, sc.tile, plan.cap, plan.stage, counter, s);
     fe_free_async(d_items, s);
     fe_free_async(counter, s);
     return rc;
@@ -477,6 +657,7 @@ int fe_batch_autotune(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, 
         for (int t : {4, 16, 64, 256, 1024}) cands.push_back({FE_SCHED_WARP_PER_ROW, t});
     } else {
         for (int t : {4, 16, 64, 256, 1024}) cands.push_back({FE_SCHED_WARP_PER_ELEMENT, t});
+        for (int t : {6, 8, 12, 16}) cands.push_back({FE_SCHED_WARP_PER_ELEMENT_TMA, t});
         for (int t : {4, 32}) cands.push_back({FE_SCHED_THREAD_PER_ENTRY, t});
         for (int t : {1, 8}) cands.push_back({FE_SCHED_BLOCK_PER_ELEMENT, t});
     }
@@ -548,8 +729,10 @@ int fe_batch_graph_create(fe_ctx *ctx, const fe_batch_item *items, int32_t n_ite
     if (cudaMalloc((void **)&g->d_items, sizeof(BatchItemDev) * n_items) != cudaSuccess ||
         cudaMalloc((void **)&g->counter, sizeof(unsigned long long)) != cudaSuccess)
         rc = FE_ERR_OOM;
-    if (rc == FE_OK && cudaMemcpy(g->d_items, plan.host.data(), sizeof(BatchItemDev) * n_items,
-                                  cudaMemcpyHostToDevice) != cudaSuccess)
+    // uploaded on the caller's stream (ordered after the work that built the patterns)
+    if (rc == FE_OK && (cudaMemcpyAsync(g->d_items, plan.host.data(), sizeof(BatchItemDev) * n_items,
+                                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
         rc = FE_ERR_DEVICE;
     cudaStream_t cs = nullptr;
     if (rc == FE_OK && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = FE_ERR_DEVICE;
@@ -562,13 +745,12 @@ int fe_batch_graph_create(fe_ctx *ctx, const fe_batch_item *items, int32_t n_ite
         }
         if (lrc == FE_OK && plan.total_tiles > 0)
             lrc = launch_batch(ctx, g->d_items, n_items, plan.total_tiles, format, mode, accumulate, sc.kind, sc.tile,
-                               plan.cap, g->counter, cs);
+                               plan.cap, plan.stage, g->counter, cs);
         const cudaError_t ec = cudaStreamEndCapture(cs, &g->graph);
         rc = lrc != FE_OK ? lrc : (ec == cudaSuccess ? FE_OK : FE_ERR_DEVICE);
     }
     if (rc == FE_OK && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) rc = FE_ERR_DEVICE;
     if (cs) cudaStreamDestroy(cs);
-    (void)s;
     if (rc != FE_OK) {
         if (g->exec) cudaGraphExecDestroy(g->exec);
         if (g->graph) cudaGraphDestroy(g->graph);

@@ -18,12 +18,12 @@ using namespace fe_dev;
 
 namespace {
 
-constexpr uint32_t LOCK_SPIN_LIMIT = 1u << 22;
+constexpr int LOCK_SPIN_LOG2_DEFAULT = 22;  // compare-and-swap attempts per lock: 2^22
 
 template <int NLN, int BB, typename MT, bool CRAC>
 __global__ void __launch_bounds__(256) k_rowlock(const double *__restrict__ K, int64_t n_e, Geo g,
                                                  const MT *__restrict__ map, const MT *__restrict__ mapc,
-                                                 int64_t *locks, double *values, int *status)
+                                                 int64_t *locks, double *values, int *status, uint32_t spin_limit)
 {
     constexpr int NLOC = NLN * BB;
     constexpr int NN = NLOC * NLOC;
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) k_rowlock(const double *__restrict__ K, i
             if (lane == 0) {
                 v = (int64_t)*(volatile long long *)lk;
                 if (v < 0) v = ~v;
-                for (uint32_t it = 0; it < LOCK_SPIN_LIMIT; ++it) {
+                for (uint32_t it = 0; it < spin_limit; ++it) {
                     if (atomicCAS(lk, (unsigned long long)v, (unsigned long long)~v) == (unsigned long long)v) {
                         got = 1;
                         break;
@@ -95,7 +95,7 @@ template <typename MT, bool CRAC>
 __global__ void __launch_bounds__(256) k_rowlock_generic(const double *__restrict__ K, int64_t n_e, int32_t nln,
                                                          int32_t B, Geo g, const MT *__restrict__ map,
                                                          const MT *__restrict__ mapc, int64_t *locks, double *values,
-                                                         int *status)
+                                                         int *status, uint32_t spin_limit)
 {
     __shared__ int32_t k_s[8][FE_MAX_NLOC];
     __shared__ int32_t off_s[8][FE_MAX_NLOC];
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) k_rowlock_generic(const double *__restric
             if (lane == 0) {
                 v = (int64_t)*(volatile long long *)lk;
                 if (v < 0) v = ~v;
-                for (uint32_t it = 0; it < LOCK_SPIN_LIMIT; ++it) {
+                for (uint32_t it = 0; it < spin_limit; ++it) {
                     if (atomicCAS(lk, (unsigned long long)v, (unsigned long long)~v) == (unsigned long long)v) {
                         got = 1;
                         break;
@@ -163,24 +163,26 @@ int fe_assemble_rowlock(const fe_pattern *p, const double *K, double *values, in
     int64_t *locks = crac ? p->crac_ptr : p->row_ptr;  // the row pointers are the locks (restored on exit)
     const int sms = p->ctx->num_sms;
     int *st = p->ctx->d_status;
+    const int lg = p->ctx->knob[FE_KNOB_LOCK_SPIN] > 0 ? p->ctx->knob[FE_KNOB_LOCK_SPIN] : LOCK_SPIN_LOG2_DEFAULT;
+    const uint32_t spin = 1u << lg;
 #define FE_RL(NLN_, BB_)                                                                                            \
     do {                                                                                                            \
         if (p->map_bytes == 1) {                                                                                    \
             if (crac)                                                                                               \
                 k_rowlock<NLN_, BB_, uint8_t, true><<<fe_grid_resident(k_rowlock<NLN_, BB_, uint8_t, true>, p->n_e * 32, 256, sms), 256, 0, s>>>(K, p->n_e, g, (const uint8_t *)p->map_csr,  \
                                                                          (const uint8_t *)p->map_crac, locks,        \
-                                                                         values, st);                                \
+                                                                         values, st, spin);                                \
             else                                                                                                    \
                 k_rowlock<NLN_, BB_, uint8_t, false><<<fe_grid_resident(k_rowlock<NLN_, BB_, uint8_t, false>, p->n_e * 32, 256, sms), 256, 0, s>>>(K, p->n_e, g, (const uint8_t *)p->map_csr, \
                                                                           (const uint8_t *)p->map_crac, locks,       \
-                                                                          values, st);                               \
+                                                                          values, st, spin);                               \
         } else {                                                                                                    \
             if (crac)                                                                                               \
                 k_rowlock<NLN_, BB_, uint16_t, true><<<fe_grid_resident(k_rowlock<NLN_, BB_, uint16_t, true>, p->n_e * 32, 256, sms), 256, 0, s>>>(                                           \
-                    K, p->n_e, g, (const uint16_t *)p->map_csr, (const uint16_t *)p->map_crac, locks, values, st);   \
+                    K, p->n_e, g, (const uint16_t *)p->map_csr, (const uint16_t *)p->map_crac, locks, values, st, spin);   \
             else                                                                                                    \
                 k_rowlock<NLN_, BB_, uint16_t, false><<<fe_grid_resident(k_rowlock<NLN_, BB_, uint16_t, false>, p->n_e * 32, 256, sms), 256, 0, s>>>(                                          \
-                    K, p->n_e, g, (const uint16_t *)p->map_csr, (const uint16_t *)p->map_crac, locks, values, st);   \
+                    K, p->n_e, g, (const uint16_t *)p->map_csr, (const uint16_t *)p->map_crac, locks, values, st, spin);   \
         }                                                                                                           \
     } while (0)
     if (p->nln == 8 && p->B == 3) FE_RL(8, 3);
@@ -191,20 +193,20 @@ int fe_assemble_rowlock(const fe_pattern *p, const double *K, double *values, in
         if (crac)
             k_rowlock_generic<uint8_t, true><<<fe_grid_resident(k_rowlock_generic<uint8_t, true>, p->n_e * 32, 256, sms), 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
                                                                   (const uint8_t *)p->map_csr,
-                                                                  (const uint8_t *)p->map_crac, locks, values, st);
+                                                                  (const uint8_t *)p->map_crac, locks, values, st, spin);
         else
             k_rowlock_generic<uint8_t, false><<<fe_grid_resident(k_rowlock_generic<uint8_t, false>, p->n_e * 32, 256, sms), 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
                                                                    (const uint8_t *)p->map_csr,
-                                                                   (const uint8_t *)p->map_crac, locks, values, st);
+                                                                   (const uint8_t *)p->map_crac, locks, values, st, spin);
     } else {
         if (crac)
             k_rowlock_generic<uint16_t, true><<<fe_grid_resident(k_rowlock_generic<uint16_t, true>, p->n_e * 32, 256, sms), 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
                                                                    (const uint16_t *)p->map_csr,
-                                                                   (const uint16_t *)p->map_crac, locks, values, st);
+                                                                   (const uint16_t *)p->map_crac, locks, values, st, spin);
         else
             k_rowlock_generic<uint16_t, false><<<fe_grid_resident(k_rowlock_generic<uint16_t, false>, p->n_e * 32, 256, sms), 256, 0, s>>>(K, p->n_e, p->nln, p->B, g,
                                                                     (const uint16_t *)p->map_csr,
-                                                                    (const uint16_t *)p->map_crac, locks, values, st);
+                                                                    (const uint16_t *)p->map_crac, locks, values, st, spin);
     }
 #undef FE_RL
     fe_note_launch();

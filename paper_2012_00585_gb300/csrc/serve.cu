@@ -18,6 +18,7 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "internal.cuh"
@@ -101,6 +102,7 @@ struct fe_server {
     std::unordered_map<uint64_t, Ticket> tickets;
     std::unordered_map<uint64_t, CacheEntry> cache;
     size_t budget = 0, in_use = 0;
+    size_t cache_bytes = 0;  // bytes of the built patterns in the cache (part of in_use)
     std::vector<cudaStream_t> streams;
     cudaStream_t build_stream = nullptr;
     int next_stream = 0, max_batch = 64;
@@ -128,14 +130,19 @@ size_t values_estimate(const fe_request &r, const fe_pattern *p)
 }
 
 // Evict unreferenced cached patterns, least recently used first, until
-// `need` more bytes fit.  Caller holds the lock.
+// `need` more bytes fit.  A pattern that a queued request will use is kept:
+// evicting it would only make that request rebuild it.  Caller holds the
+// lock.
 void evict_for(fe_server *sv, size_t need)
 {
+    std::unordered_set<uint64_t> wanted;
+    for (uint64_t id : sv->pending) wanted.insert(sv->tickets[id].req.pattern_key);
     while (sv->in_use + need > sv->budget) {
         uint64_t victim = 0;
         uint64_t oldest = UINT64_MAX;
         for (auto &kv : sv->cache)
-            if (kv.second.refs == 0 && !kv.second.building && kv.second.last_use < oldest) {
+            if (kv.second.refs == 0 && !kv.second.building && kv.second.last_use < oldest &&
+                !wanted.count(kv.first)) {
                 oldest = kv.second.last_use;
                 victim = kv.first;
             }
@@ -143,6 +150,7 @@ void evict_for(fe_server *sv, size_t need)
         CacheEntry ce = sv->cache[victim];
         sv->cache.erase(victim);
         sv->in_use -= ce.bytes;
+        sv->cache_bytes -= std::min(ce.bytes, sv->cache_bytes);
         ++sv->stats.evictions;
         cudaStreamSynchronize(sv->build_stream);
         for (cudaStream_t s : sv->streams) cudaStreamSynchronize(s);
@@ -370,6 +378,7 @@ void builder_loop(fe_server *sv)
         }
         ce.p = p;
         ce.bytes = (size_t)p->device_bytes;
+        sv->cache_bytes += ce.bytes;
         ce.building = false;
         // the estimate charged to this request becomes the pattern's real size
         const size_t est = pattern_estimate(req);

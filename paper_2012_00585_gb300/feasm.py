@@ -46,6 +46,7 @@ FE_KNOB_GATHER_WARPS = 2
 FE_KNOB_ATOMIC_KERNEL = 3
 FE_KNOB_ATOMIC_WARPS = 4
 FE_KNOB_GATHER_STAGES = 5
+FE_KNOB_LOCK_SPIN = 6
 FE_KNOB_COUNT = 8
 
 FE_FORMAT_CSR = 0
@@ -54,6 +55,7 @@ FE_SCHED_WARP_PER_ELEMENT = 1
 FE_SCHED_THREAD_PER_ENTRY = 2
 FE_SCHED_BLOCK_PER_ELEMENT = 3
 FE_SCHED_WARP_PER_ROW = 4
+FE_SCHED_WARP_PER_ELEMENT_TMA = 5
 
 _lib = None
 _lock = threading.Lock()

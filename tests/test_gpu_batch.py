@@ -84,7 +84,7 @@ def test_batch_deterministic_bit_exact(ctx, batch, fmt, sched):
 
 
 @pytest.mark.parametrize("fmt", [0, 1])
-@pytest.mark.parametrize("sched", [(1, 1), (1, 16), (2, 1), (2, 4), (3, 1), (3, 4)])
+@pytest.mark.parametrize("sched", [(1, 1), (1, 16), (2, 1), (2, 4), (3, 1), (3, 4), (5, 1), (5, 16), (5, 64)])
 def test_batch_atomic_schedules(ctx, batch, fmt, sched):
     import torch
     from paper_2012_00585_gb300 import feasm
@@ -116,7 +116,7 @@ def test_autotune_then_default_uses_it(ctx, batch, mode):
     from paper_2012_00585_gb300 import feasm
     kind, tile, ms = feasm.fe_batch_autotune(ctx, _items(batch), 0, mode)
     assert ms > 0 and tile >= 1
-    assert kind == feasm.FE_SCHED_WARP_PER_ROW if mode == 1 else kind in (1, 2, 3)
+    assert kind == feasm.FE_SCHED_WARP_PER_ROW if mode == 1 else kind in (1, 2, 3, 5)
     for r in batch:
         r["v"].fill_(float("nan"))
     feasm.fe_assemble_batch(ctx, _items(batch), 0, mode)
@@ -152,3 +152,22 @@ def test_graph_replay_with_new_values(ctx, batch, mode):
         feasm.fe_batch_graph_destroy(g)
         for r in batch:  # restore the module's K for other tests
             r["Kd"].copy_(torch.from_numpy(r["K"]))
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_batch_staged_schedule_with_unaligned_matrices(ctx, batch, fmt):
+    """A K buffer that is only 8-byte aligned cannot be moved by bulk copies:
+    that item takes the warp-per-element path inside the same launch, and the
+    result is unchanged."""
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    items = _items(batch)
+    r = batch[4]  # hex 4^3, d = 3 (24 x 24)
+    buf = torch.empty(r["Kd"].numel() + 1, dtype=torch.float64, device="cuda")
+    k_odd = buf[1:].view(r["Kd"].shape)
+    k_odd.copy_(r["Kd"])
+    assert k_odd.data_ptr() % 16 == 8
+    items[4] = (r["pat"], k_odd, r["v"])
+    feasm.fe_assemble_batch(ctx, items, fmt, feasm.FE_ATOMIC, 0, (feasm.FE_SCHED_WARP_PER_ELEMENT_TMA, 8))
+    _check(batch, feasm.FE_ATOMIC)
+    assert feasm.fe_device_status(ctx) == 0

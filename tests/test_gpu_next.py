@@ -85,3 +85,42 @@ def test_rowlock_assembly(ctx, fmt, name, D, n_dofs):
     crp1, _ = g.crac_host()
     assert np.array_equal(rp1, rp0) and np.array_equal(crp1, crp0)
     g.free()
+
+
+@pytest.mark.parametrize("fmt", ["csr", "crac"])
+def test_rowlock_timeout_is_reported(ctx, fmt):
+    """Failure detection without a fault: one row's lock word is left held
+    (its row pointer complemented, as a holder that never releases), the
+    bounded spin runs out, the row is skipped and FE_ERR_TIMEOUT reaches the
+    host through the device status word; the rest of the matrix is right and
+    the context stays usable."""
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    D, n_dofs = wl.hex_q1_grid(3, 1)
+    K = wl.random_matrices(D.shape[0], D.shape[1], seed=12)
+    g = gu.GpuAssembly(ctx, D, n_dofs)
+    rp, ci = oracle.csr_pattern(D, n_dofs)
+    exp = oracle.assemble_csr(D, K, rp, ci)
+    locks = (g.pattern.csr() if fmt == "csr" else g.pattern.crac())[0]
+    held = 21  # an interior DOF of the 4x4x4-node grid
+    saved = locks[held].item()
+    feasm.fe_tune_set(ctx, feasm.FE_KNOB_LOCK_SPIN, 10)
+    try:
+        locks[held] = ~saved
+        torch.cuda.synchronize()
+        got = g.assemble(K, fmt, feasm.FE_ROWLOCK).cpu().numpy()
+        assert feasm.fe_device_status(ctx) == feasm.FE_ERR_TIMEOUT
+        locks[held] = saved
+        torch.cuda.synchronize()
+    finally:
+        feasm.fe_tune_set(ctx, feasm.FE_KNOB_LOCK_SPIN, 0)
+    row = np.repeat(np.arange(n_dofs), np.diff(rp))
+    other = row != held
+    tau = gu.row_tolerance(rp, exp, gu.contribution_abs_row_sums(D, K, n_dofs))
+    assert np.all(np.abs(got[other] - exp[other]) <= tau[row[other]])
+    assert np.all(got[~other] == 0.0)  # the held row received nothing
+    # released: the same call is complete again and the status is clean
+    got = g.assemble(K, fmt, feasm.FE_ROWLOCK).cpu().numpy()
+    assert feasm.fe_device_status(ctx) == 0
+    gu.assert_within_row_tol(rp, got, exp, tau)
+    g.free()
