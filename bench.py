@@ -51,10 +51,11 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--knob", action="append", default=[], metavar="NAME=VALUE",
                     help="set a schedule knob before the run, e.g. GATHER_KERNEL=4 (FE_KNOB_<NAME>)")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "served", "sweep"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "served", "sweep", "tet96"],
                     help="single: the 64^3 elasticity step (default); batched: 256 meshes, one launch "
                          "vs one launch per mesh; served: request stream with latency; sweep: the p- and "
-                         "d-benchmarks on structured Q_p quads, every assembly mode")
+                         "d-benchmarks on structured Q_p quads, every assembly mode; tet96: the 96^3 "
+                         "Kuhn-split P2 tet mesh with permuted node ids (30x30 SPD K)")
     ap.add_argument("--meshes", type=int, default=256, help="batched workload: number of meshes")
     ap.add_argument("--rate", type=float, default=2000.0, help="served workload: mean arrivals per second")
     ap.add_argument("--duration", type=float, default=2.0, help="served workload: seconds of arrivals")
@@ -440,12 +441,50 @@ def oracle_sample(n, n_numeric):
     return t_pat, t_num, K.size
 
 
+def host_info():
+    """Host core count and CPU model (x86 'model name', Arm implementer/part)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        for key in ("model name", "Model", "CPU part"):
+            for line in txt.splitlines():
+                if line.startswith(key):
+                    model = line.split(":", 1)[1].strip()
+                    break
+            if model:
+                break
+    except OSError:
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.machine()}
+
+
+class OneCore:
+    """Runs the enclosed oracle work pinned to one host core (restored after)."""
+
+    def __enter__(self):
+        self.saved = None
+        if hasattr(os, "sched_getaffinity"):
+            self.saved = os.sched_getaffinity(0)
+            os.sched_setaffinity(0, {min(self.saved)})
+        return self
+
+    def __exit__(self, *exc):
+        if self.saved is not None:
+            os.sched_setaffinity(0, self.saved)
+
+
 def cpu_baseline(n):
-    t_pat, t_num, N_ent = oracle_sample(n, 2)
+    with OneCore():
+        t_pat, t_num, N_ent = oracle_sample(n, 2)
     t_step = t_pat + N_ASSEMBLIES * t_num
     return {"value": N_ASSEMBLIES * N_ent / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"hex Q1 {n}^3 elasticity: serial oracle pattern + CRAC once ({t_pat:.2f} s) and 2 numeric "
-                      f"assemblies ({t_num:.2f} s each), step time = pattern + {N_ASSEMBLIES} x numeric"}
+            "host": host_info(),
+            "numeric_only_entries_per_s": N_ent / t_num,
+            "sample": f"hex Q1 {n}^3 elasticity: serial oracle pinned to one core, pattern + CRAC once "
+                      f"({t_pat:.2f} s) and 2 numeric assemblies ({t_num:.2f} s each), step time = pattern + "
+                      f"{N_ASSEMBLIES} x numeric"}
 
 
 def run_reference(args):
@@ -463,21 +502,23 @@ def run_reference(args):
         for _ in range(N_ASSEMBLIES):
             oracle.assemble_csr(D, K, rp, ci)
 
-    for _ in range(args.warmup):
-        step()
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    sec = (time.perf_counter() - t) / args.steps
+    with OneCore():
+        for _ in range(args.warmup):
+            step()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        sec = (time.perf_counter() - t) / args.steps
     value = N_ASSEMBLIES * K.size / sec
-    sample = f"hex Q1 {n}^3 elasticity (3 DOF/node, {D.shape[0]} elements): serial oracle pattern + CRAC + " \
-             f"{N_ASSEMBLIES} assemblies per step"
+    sample = f"hex Q1 {n}^3 elasticity (3 DOF/node, {D.shape[0]} elements): serial oracle pinned to one core, " \
+             f"pattern + CRAC + {N_ASSEMBLIES} assemblies per step"
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"hex Q1 {args.n}^3 elasticity, 3 DOF/node; step = pattern build + "
                                    f"{N_ASSEMBLIES} numeric assemblies", "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -663,6 +704,78 @@ def run_sweep(args, local_rank):
     return line
 
 
+def run_tet(args, local_rank):
+    """The unstructured workload: a 96^3 hex grid split into 6 Kuhn tets per
+    cube, quadratic P2 tets (10 nodes, 3 DOF/node, 30x30 K), node ids
+    permuted by a seeded shuffle; K = (G G^T + its transpose)/2 + 30 I with
+    G ~ N(0,1), drawn on the device.  Pattern built once; every mode timed
+    (median of 5 after 3 warm-ups; K = 38 GB, larger than L2).  value: the
+    deterministic CSR assembly."""
+    import torch
+
+    import workloads as wl
+    from paper_2012_00585_gb300 import feasm as fe
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = fe.fe_create(local_rank)
+    n = 96
+    D, n_dofs = wl.tet_p2_kuhn(n, d=3, seed=0)
+    n_e, n_loc = D.shape
+    N_ent = n_e * n_loc * n_loc
+    with torch.cuda.stream(stream):
+        Dd = torch.from_numpy(D).to(dev)
+        Kd = wl.random_spd_matrices(n_e, n_loc, seed=1, device=dev)
+    stream.synchronize()
+    launches0 = fe.fe_kernel_launches()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    p = fe.fe_pattern_build(ctx, n_e, n_loc, n_dofs, Dd, fe.FE_PATTERN_ALL, stream)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = b0.elapsed_time(b1)
+    info = fe.fe_pattern_info_get(p)
+    nnz = info["nnz"]
+    values = torch.empty(nnz, dtype=torch.float64, device=dev)
+    B = b_alg(n_e, n_loc, nnz)
+    var = {}
+    for vname in VARIANTS:
+        f, m = vname.split("-")
+        fn = fe.fe_assemble_csr if f == "csr" else fe.fe_assemble_crac
+        md = fe.FE_ATOMIC if m == "atomic" else fe.FE_DETERMINISTIC
+        for _ in range(3):
+            fn(ctx, p, Kd, values, md, 0, stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for a, b in evs:
+            a.record(stream)
+            fn(ctx, p, Kd, values, md, 0, stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(b) for a, b in evs)
+        var[vname] = {"ms": round(ms, 3), "alg_GBps": round(B / (ms * 1e-3) / 1e9, 1),
+                      "Gentries_per_s": round(N_ent / (ms * 1e-3) / 1e9, 2)}
+    assert fe.fe_device_status(ctx, stream) == 0
+    launches = fe.fe_kernel_launches() - launches0
+    hbm, src = measured_peaks()
+    det = var["csr-det"]["ms"]
+    line = {"metric": METRIC, "value": N_ent / (det * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": 5, "warmup": 3,
+            "ms_per_step": det, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{n}^3 hex grid, 6 Kuhn tets per cube, P2 (10 nodes), 3 DOF/node, node ids "
+                                   f"permuted ({n_dofs} DOFs, {n_e} elements, 30x30 SPD FP64 K on the device); "
+                                   "step = one deterministic CSR assembly",
+                       "entries_per_assembly": N_ent, "nnz": nnz, "n_ca": info["n_ca"],
+                       "gamma": round(info["n_ca"] / nnz, 4), "pattern_build_ms": round(build_ms, 2),
+                       "l2": "inputs larger than L2 (K = %.1f GB)" % (8 * N_ent / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": round(B / (det * 1e-3) / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(B / (det * 1e-3) / 1e9 / hbm, 4), "traffic": None, "peak_source": src,
+                         "alg_bytes_per_launch": B},
+            "gpu_launches": int(launches), "variants": var}
+    fe.fe_pattern_free(p)
+    fe.fe_destroy(ctx)
+    return line
+
+
 def run_served(args, local_rank):
     """Poisson stream of assembly requests (mean `rate`/s for `duration` s):
     90 % hex meshes with n ~ logU[8,48] (half Q1 Laplace d=1, half Q1
@@ -793,6 +906,10 @@ def main():
     if args.workload == "sweep":
         if rank == 0:
             print(json.dumps(run_sweep(args, local_rank)), flush=True)
+        return
+    if args.workload == "tet96":
+        if rank == 0:
+            print(json.dumps(run_tet(args, local_rank)), flush=True)
         return
     if world > 1:
         import torch
