@@ -104,7 +104,7 @@ def source_hash():
     k0 = src.rindex("template", 0, k0)
     k1 = src.index("\n}\n", k0)
     l0 = src.index("    if (W <= 0) W = 2;")
-    l1 = src.index("k_gather_generic<MT, CRAC>, smem", l0)
+    l1 = src.index("\n    } else {\n", l0)  # end of the k_gather_node launches
     h = hashlib.sha256()
     h.update(src[k0:k1].encode())
     h.update(src[l0:l1].encode())
@@ -624,6 +624,9 @@ def run_sweep(args, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
     ctx = fe.fe_create(local_rank)
+    for kv in args.knob:
+        name, value = kv.split("=")
+        fe.fe_tune_set(ctx, getattr(fe, "FE_KNOB_" + name.upper()), int(value))
     modes = [("csr", "atomic"), ("crac", "atomic"), ("csr", "det"), ("crac", "det"), ("csr", "coloured"),
              ("crac", "coloured"), ("csr", "rowlock"), ("crac", "rowlock")]
     MODES = {"atomic": fe.FE_ATOMIC, "det": fe.FE_DETERMINISTIC, "coloured": fe.FE_COLOURED,
@@ -695,7 +698,8 @@ def run_sweep(args, local_rank):
                                    "p=1..4 (d=4) on 48x48, Q1 d=1..8 on 192x192, Q1 d=20 on 48x48; N(0,1) K; "
                                    "one step = every mesh assembled once (deterministic CSR)",
                        "l2": "flushed (256 MiB write) before every timed repetition",
-                       "entries_per_step": tot_ent, "alg_bytes_per_step": tot_alg},
+                       "entries_per_step": tot_ent, "alg_bytes_per_step": tot_alg,
+                       **({"knobs": args.knob} if args.knob else {})},
             "roofline": {"bound": "hbm", "achieved": round(tot_alg / (tot_ms * 1e-3) / 1e9, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(tot_alg / (tot_ms * 1e-3) / 1e9 / hbm, 4), "traffic": None,
                          "peak_source": src},

@@ -235,9 +235,16 @@ __global__ void __launch_bounds__(256) k_gather_node(const double *__restrict__ 
     }
 }
 
-template <typename MT, bool CRAC>
+// Any element shape.  A unit is R of the B DOF rows of a node (R chosen by
+// the host so that the accumulator, R x row length doubles, stays small for
+// large B); the rows of a node have the same length and are contiguous in
+// values, and the unit's part of each incidence's K slice is contiguous too.
+// BATCHED (large slices): each lane loads 4 entries' values and slots
+// before its 4 adds (the slots of one incidence are distinct).  Incidences
+// in ascending element order.
+template <typename MT, bool CRAC, bool BATCHED>
 __global__ void __launch_bounds__(256) k_gather_generic(const double *__restrict__ K, int64_t n_nodes, int32_t nln,
-                                                        int32_t B, Geo g, const MT *__restrict__ map,
+                                                        int32_t B, int32_t R, Geo g, const MT *__restrict__ map,
                                                         const MT *__restrict__ mapc, int cap, int accumulate,
                                                         double *values)
 {
@@ -246,8 +253,11 @@ __global__ void __launch_bounds__(256) k_gather_generic(const double *__restrict
     double *acc = acc_all + (size_t)(threadIdx.x >> 5) * cap;
     const int n_loc = nln * B;
     const int64_t NN = (int64_t)n_loc * n_loc;
-    const int chk = B * n_loc;
-    for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
+    const int G = BATCHED ? (B + R - 1) / R : 1;  // units per node (one without row groups)
+    for (int64_t u = fe_warp_id(); u < n_nodes * G; u += fe_warps()) {
+        const int64_t v = BATCHED ? u / G : u;
+        const int j0 = BATCHED ? (int)(u - v * G) * R : 0;
+        const int nr_rows = BATCHED ? min(R, B - j0) : B;
         const int64_t i0 = (int64_t)B * v;
         int64_t rb, RL;
         if (!CRAC) {
@@ -257,32 +267,66 @@ __global__ void __launch_bounds__(256) k_gather_generic(const double *__restrict
             rb = crac_row_base(g, i0);
             RL = crac_row_base(g, i0 + 1) - rb;
         }
-        const int64_t total = B * RL;
+        rb += j0 * RL;
+        const int64_t total = nr_rows * RL;
+        const int chk = nr_rows * n_loc;
         for (int64_t k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
         __syncwarp();
         for (int64_t s = g.adj_ptr[v]; s < g.adj_ptr[v + 1]; ++s) {
             const uint32_t t = g.adj[s];
             const int64_t e = t / (uint32_t)nln;
             const int kr = (int)(t - (uint32_t)e * (uint32_t)nln);
-            const double *chunk = K + e * NN + (int64_t)kr * chk;
+            const double *chunk = K + e * NN + ((int64_t)kr * B + j0) * n_loc;
             int64_t rp = 0;
             int nr = 0;
             if (CRAC) {
                 rp = g.run_ptr[e];
                 nr = (int)(g.run_ptr[e + 1] - rp);
             }
-            for (int q = lane; q < chk; q += 32) {
-                const int jr = q / n_loc, c = q - jr * n_loc;
-                const int kc = c / B;
-                int pos;
-                if (!CRAC) {
-                    pos = (int)map[(int64_t)t * nln + kc];
-                } else {
-                    int k, off;
-                    run_of_multi(g.run_mask + e * g.mask_words, kc, k, off);
-                    pos = (int)mapc[rp * nln + (int64_t)kr * nr + k] + off;
+            if (!BATCHED) {
+                // one entry per lane at a time (fewer registers: more warps for small slices)
+                for (int q = lane; q < chk; q += 32) {
+                    const int jr = q / n_loc, c = q - jr * n_loc;
+                    const int kc = c / B;
+                    int pos;
+                    if (!CRAC) {
+                        pos = (int)map[(int64_t)t * nln + kc];
+                    } else {
+                        int k, off;
+                        run_of_multi(g.run_mask + e * g.mask_words, kc, k, off);
+                        pos = (int)mapc[rp * nln + (int64_t)kr * nr + k] + off;
+                    }
+                    acc[jr * RL + (int64_t)B * pos + c % B] += chunk[q];
                 }
-                acc[jr * RL + (int64_t)B * pos + c % B] += chunk[q];
+                __syncwarp();
+                continue;
+            }
+            for (int q0 = lane; q0 < chk; q0 += 128) {
+                double kv[4];
+                int slot[4];
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const int q = q0 + 32 * w;
+                    kv[w] = 0.0;
+                    slot[w] = -1;
+                    if (q < chk) {
+                        const int jr = q / n_loc, c = q - jr * n_loc;
+                        const int kc = c / B;
+                        int pos;
+                        if (!CRAC) {
+                            pos = (int)map[(int64_t)t * nln + kc];
+                        } else {
+                            int k, off;
+                            run_of_multi(g.run_mask + e * g.mask_words, kc, k, off);
+                            pos = (int)mapc[rp * nln + (int64_t)kr * nr + k] + off;
+                        }
+                        kv[w] = chunk[q];  // plain load: neighbouring rows' slices share lines
+                        slot[w] = (int)(jr * RL + (int64_t)B * pos + c % B);
+                    }
+                }
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+                    if (slot[w] >= 0) acc[slot[w]] += kv[w];
             }
             __syncwarp();
         }
@@ -1102,11 +1146,27 @@ int launch_gather(const fe_pattern *p, const double *K, double *values, int accu
                 K, p->n_nodes, g, (const MT *)p->map_csr, (const MT *)p->map_crac, cap, accumulate, values);
         }
     } else {
-        FE_TRY(configure_smem(k_gather_generic<MT, CRAC>, smem));
-        const int ggrid = fe_grid_resident(k_gather_generic<MT, CRAC>, p->n_nodes * 32, W * 32, sms, smem);
-        k_gather_generic<MT, CRAC><<<ggrid, W * 32, smem, s>>>(K, p->n_nodes, p->nln, p->B, g,
-                                                              (const MT *)p->map_csr, (const MT *)p->map_crac,
-                                                              cap, accumulate, values);
+        // rows per unit: a node's B rows, split into equal groups when their
+        // accumulator would exceed 1024 doubles (large B, e.g. 20 DOF/node)
+        const int64_t whole = (int64_t)p->B * std::max(1, p->max_row_len);
+        const int groups = (int)std::min<int64_t>(p->B, (whole + 1023) / 1024);
+        const int R = (p->B + groups - 1) / groups;
+        const int gcap = std::max(1, R * p->max_row_len);
+        int GW = ctx->knob[FE_KNOB_GATHER_WARPS] > 0 ? ctx->knob[FE_KNOB_GATHER_WARPS] : 2;
+        while (GW > 1 && (size_t)GW * gcap * 8 > 64 * 1024) GW >>= 1;
+        const size_t gsmem = (size_t)GW * gcap * 8;
+        if (gsmem > 200 * 1024) return FE_ERR_UNSUPPORTED;
+        const int64_t units = p->n_nodes * ((p->B + R - 1) / R);
+        auto launch = [&](auto kern) -> int {
+            FE_TRY(configure_smem(kern, gsmem));
+            const int ggrid = fe_grid_resident(kern, units * 32, GW * 32, sms, gsmem);
+            kern<<<ggrid, GW * 32, gsmem, s>>>(K, p->n_nodes, p->nln, p->B, R, g, (const MT *)p->map_csr,
+                                               (const MT *)p->map_crac, gcap, accumulate, values);
+            return FE_OK;
+        };
+        // without row groups and with small slices: the instance with fewer registers
+        if (groups > 1 || R * p->n_loc > 128) FE_TRY(launch(k_gather_generic<MT, CRAC, true>));
+        else FE_TRY(launch(k_gather_generic<MT, CRAC, false>));
     }
     fe_note_launch();
     FE_CUDA(cudaGetLastError());
