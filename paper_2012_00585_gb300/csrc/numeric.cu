@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) k_atomic_generic(const double *__restrict
 // Incidences are taken U at a time: their K slices and slots are loaded
 // first, then added strictly in ascending element order.
 template <int NLN, int BB, typename MT, bool CRAC, int U>
-__global__ void __launch_bounds__(256) k_gather_node(const double *__restrict__ K, int64_t n_nodes, Geo g,
+__global__ void __launch_bounds__(256, U == 4 ? 4 : 1) k_gather_node(const double *__restrict__ K, int64_t n_nodes, Geo g,
                                                      const MT *__restrict__ map, const MT *__restrict__ mapc, int cap,
                                                      int accumulate, double *values)
 {
