@@ -305,6 +305,9 @@ def run_gpu(args, rank, world, local_rank):
         extra["variants"] = var
         extra["pattern_build_ms"] = round(statistics.median(a.elapsed_time(b) for a, b in pe), 3)
 
+    if not args.no_variants:
+        extra["c1_latency"] = c1_latency(ctx, feasm, dev, stream)
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, ctx, feasm, D, Kd, n_dofs, nnz, mode, assemble, stream, dev, world, dist)
@@ -342,6 +345,52 @@ def run_gpu(args, rank, world, local_rank):
     out.update(extra)
     feasm.fe_destroy(ctx)
     return out, (D, Kref, n_dofs)
+
+
+def c1_latency(ctx, feasm, dev, stream):
+    """The 16x16 Q1 Laplace quad mesh (289 DOFs, 256 elements): latency, not
+    bandwidth.  Device time per call (CUDA events, median of 50) of the
+    pattern build and each assembly, and the host time to issue one
+    assembly call (100 back-to-back calls)."""
+    import numpy as np
+    import torch
+
+    import workloads as wl
+    D, n_dofs = wl.quad_q1_grid(16, 1)
+    n_e, n_loc = D.shape
+    with torch.cuda.stream(stream):
+        Dd = torch.from_numpy(D).to(dev)
+        Kd = torch.from_numpy(wl.broadcast_matrices(wl.laplace_q1_quad(), n_e)).to(dev)
+    stream.synchronize()
+
+    def dev_us(fn, reps=50):
+        for _ in range(5):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in evs:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return round(statistics.median(a.elapsed_time(b) for a, b in evs) * 1e3, 2)
+
+    out = {"workload": "16x16 Q1 quads, 4x4 Laplace (256 elements, 289 DOFs)"}
+    out["pattern_build_us"] = dev_us(lambda: feasm.fe_pattern_free(
+        feasm.fe_pattern_build(ctx, n_e, n_loc, n_dofs, Dd, feasm.FE_PATTERN_ALL, stream)), reps=20)
+    p = feasm.fe_pattern_build(ctx, n_e, n_loc, n_dofs, Dd, feasm.FE_PATTERN_ALL, stream)
+    v = torch.empty(feasm.fe_pattern_info_get(p)["nnz"], dtype=torch.float64, device=dev)
+    for name, fn, mode in (("csr-det", feasm.fe_assemble_csr, feasm.FE_DETERMINISTIC),
+                           ("csr-atomic", feasm.fe_assemble_csr, feasm.FE_ATOMIC),
+                           ("crac-det", feasm.fe_assemble_crac, feasm.FE_DETERMINISTIC)):
+        out[name + "_us"] = dev_us(lambda: fn(ctx, p, Kd, v, mode, 0, stream))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(100):
+        feasm.fe_assemble_csr(ctx, p, Kd, v, feasm.FE_DETERMINISTIC, 0, stream)
+    out["host_us_per_call"] = round((time.perf_counter() - t) / 100 * 1e6, 2)
+    torch.cuda.synchronize()
+    feasm.fe_pattern_free(p)
+    return out
 
 
 def hbm_probe(ctx, feasm, dev, stream):

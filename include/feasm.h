@@ -162,6 +162,8 @@ uint64_t fe_kernel_launches(void);
 #define FE_KNOB_ATOMIC_WARPS 4   /* warps per block of the staged kernel     */
 #define FE_KNOB_GATHER_STAGES 5  /* ring stages per warp of gather kernel 4:
                                     2..8 (0: 4)                              */
+#define FE_KNOB_SPMV_LANES 7     /* lanes per row of fe_spmv_*: 2, 4, 8 or 16
+                                    (0: 4)                                   */
 #define FE_KNOB_LOCK_SPIN 6      /* FE_ROWLOCK: a lock is given up after
                                     2^value compare-and-swap attempts, 4..24
                                     (0: 2^22); the row is then skipped and

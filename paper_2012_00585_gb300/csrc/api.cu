@@ -335,12 +335,15 @@ int fe_tune_set(fe_ctx *ctx, int knob, int value)
     case FE_KNOB_ATOMIC_WARPS: hi = 8; break;
     case FE_KNOB_GATHER_STAGES: hi = 8; break;
     case FE_KNOB_LOCK_SPIN: hi = 24; break;
+    case FE_KNOB_SPMV_LANES: hi = 16; break;
     default: return FE_ERR_INVALID_ARG;
     }
     if (value < lo || value > hi) return FE_ERR_INVALID_ARG;
     if (knob == FE_KNOB_GATHER_BATCH && value != 0 && value != 4 && value != 8) return FE_ERR_INVALID_ARG;
     if (knob == FE_KNOB_GATHER_STAGES && value == 1) return FE_ERR_INVALID_ARG;
     if (knob == FE_KNOB_LOCK_SPIN && value != 0 && value < 4) return FE_ERR_INVALID_ARG;
+    if (knob == FE_KNOB_SPMV_LANES && value != 0 && value != 2 && value != 4 && value != 8 && value != 16)
+        return FE_ERR_INVALID_ARG;
     ctx->knob[knob] = value;
     return FE_OK;
 }

@@ -8,13 +8,13 @@
 
 namespace {
 
-// G lanes per row (32/G rows per warp; on GB300 the FP64 pipe, not memory,
-// limits a warp-per-row product: a warp-wide reduction per row costs more
-// adds than the row has entries).  Row groups are strided by all warps; the
+// G lanes per row (32/G rows per warp; on GB300 the FP64 pipe limits the
+// product: a warp-wide reduction per row costs more adds than the row has
+// entries, and fewer lanes per row waste fewer predicated multiply-adds).  Row groups are strided by all warps; the
 // next group's pointers are loaded one group ahead.  Each lane sums its
 // entries k = a + lane, a + lane + G, ... in order, then a fixed shuffle tree
 // over the G lanes: the sum order is fixed (reproducible run to run).
-constexpr int SPMV_G = 8;
+constexpr int SPMV_G = 4;  // default lanes per row (FE_KNOB_SPMV_LANES); fastest of 2/4/8/16 measured
 
 template <int G>
 __device__ __forceinline__ double group_sum(double v)
@@ -24,12 +24,13 @@ __device__ __forceinline__ double group_sum(double v)
     return v;
 }
 
+template <int G>
 __global__ void __launch_bounds__(256) k_spmv_csr(int64_t n_rows, const int64_t *__restrict__ row_ptr,
                                                   const int32_t *__restrict__ col_idx,
                                                   const double *__restrict__ values, const double *__restrict__ x,
                                                   double *__restrict__ y)
 {
-    constexpr int G = SPMV_G, R = 32 / G;
+    constexpr int R = 32 / G, UNR = G >= 8 ? 4 : 2;  // entries per lane per step
     const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
     const int64_t stride = fe_warps() * R;
     int64_t i = fe_warp_id() * R + sub;
@@ -45,17 +46,17 @@ __global__ void __launch_bounds__(256) k_spmv_csr(int64_t n_rows, const int64_t 
             bn = row_ptr[i + stride + 1];
         }
         double s = 0.0;
-        for (int64_t k0 = a + gl; k0 < b; k0 += 4 * G) {
-            int32_t c[4];
-            double v[4];
+        for (int64_t k0 = a + gl; k0 < b; k0 += UNR * G) {
+            int32_t c[UNR];
+            double v[UNR];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < UNR; ++u) {
                 const int64_t k = k0 + u * G;
                 c[u] = k < b ? __ldcs(col_idx + k) : -1;
                 v[u] = k < b ? __ldcs(values + k) : 0.0;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < UNR; ++u)
                 if (c[u] >= 0) s += v[u] * __ldg(x + c[u]);
         }
         s = group_sum<G>(s);
@@ -69,12 +70,13 @@ __global__ void __launch_bounds__(256) k_spmv_csr(int64_t n_rows, const int64_t 
 // each lane walks the row's runs with its positions (the pairs are read
 // through L1; runs are rarely shorter than G, so a lane moves about one run
 // per step).  The column of p is first + (p - pos) of its run.
+template <int G>
 __global__ void __launch_bounds__(256) k_spmv_crac(int64_t n_rows, const int64_t *__restrict__ crac_ptr,
                                                    const int32_t *__restrict__ col_align,
                                                    const double *__restrict__ values, const double *__restrict__ x,
                                                    double *__restrict__ y)
 {
-    constexpr int G = SPMV_G, R = 32 / G;
+    constexpr int R = 32 / G;
     const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
     const int64_t stride = fe_warps() * R;
     int64_t i = fe_warp_id() * R + sub;
@@ -124,13 +126,22 @@ int spmv(fe_ctx *ctx, const fe_pattern *p, const double *values, const double *x
     if (prev != ctx->device) cudaSetDevice(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (p->n_dofs > 0) {
-        const int64_t work = (p->n_dofs + 32 / SPMV_G - 1) / (32 / SPMV_G) * 32;  // threads: one warp per row group
-        if (crac)
-            k_spmv_crac<<<fe_grid_resident(k_spmv_crac, work, 256, ctx->num_sms), 256, 0, s>>>(
-                p->n_dofs, p->crac_ptr, p->col_align, values, x, y);
-        else
-            k_spmv_csr<<<fe_grid_resident(k_spmv_csr, work, 256, ctx->num_sms), 256, 0, s>>>(
-                p->n_dofs, p->row_ptr, p->col_idx, values, x, y);
+        const int G = ctx->knob[FE_KNOB_SPMV_LANES] > 0 ? ctx->knob[FE_KNOB_SPMV_LANES] : SPMV_G;
+        const int64_t work = (p->n_dofs + 32 / G - 1) / (32 / G) * 32;  // threads: one warp per row group
+        auto go = [&](auto csr_kern, auto crac_kern) {
+            if (crac)
+                crac_kern<<<fe_grid_resident(crac_kern, work, 256, ctx->num_sms), 256, 0, s>>>(
+                    p->n_dofs, p->crac_ptr, p->col_align, values, x, y);
+            else
+                csr_kern<<<fe_grid_resident(csr_kern, work, 256, ctx->num_sms), 256, 0, s>>>(
+                    p->n_dofs, p->row_ptr, p->col_idx, values, x, y);
+        };
+        switch (G) {
+        case 2: go(k_spmv_csr<2>, k_spmv_crac<2>); break;
+        case 16: go(k_spmv_csr<16>, k_spmv_crac<16>); break;
+        case 8: go(k_spmv_csr<8>, k_spmv_crac<8>); break;
+        default: go(k_spmv_csr<4>, k_spmv_crac<4>); break;
+        }
         fe_note_launch();
     }
     const cudaError_t e = cudaGetLastError();

@@ -47,6 +47,7 @@ FE_KNOB_ATOMIC_KERNEL = 3
 FE_KNOB_ATOMIC_WARPS = 4
 FE_KNOB_GATHER_STAGES = 5
 FE_KNOB_LOCK_SPIN = 6
+FE_KNOB_SPMV_LANES = 7
 FE_KNOB_COUNT = 8
 
 FE_FORMAT_CSR = 0

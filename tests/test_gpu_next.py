@@ -35,10 +35,12 @@ MESHES = [("hex5_d3", *wl.hex_q1_grid(5, 3)), ("tet3_d3", *wl.tet_p2_kuhn(3, d=3
           ("quad9", *wl.quad_q1_grid(9, 1)), ("hex4_d1", *wl.hex_q1_grid(4, 1)), ("scattered", *_scattered())]
 
 
+@pytest.mark.parametrize("lanes", [0, 2, 8, 16])
 @pytest.mark.parametrize("name,D,n_dofs", MESHES, ids=[m[0] for m in MESHES])
-def test_spmv_csr_and_crac(ctx, name, D, n_dofs):
+def test_spmv_csr_and_crac(ctx, name, D, n_dofs, lanes):
     import torch
     from paper_2012_00585_gb300 import feasm
+    feasm.fe_tune_set(ctx, feasm.FE_KNOB_SPMV_LANES, lanes)
     K = wl.random_matrices(D.shape[0], D.shape[1], seed=1)
     g = gu.GpuAssembly(ctx, D, n_dofs)
     v = g.assemble(K, "csr", feasm.FE_DETERMINISTIC)
@@ -60,6 +62,7 @@ def test_spmv_csr_and_crac(ctx, name, D, n_dofs):
         torch.cuda.synchronize()
         assert torch.equal(y, y2)  # reproducible run to run
     g.free()
+    feasm.fe_tune_set(ctx, feasm.FE_KNOB_SPMV_LANES, 0)
 
 
 @pytest.mark.parametrize("fmt", ["csr", "crac"])
