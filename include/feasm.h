@@ -236,6 +236,12 @@ int fe_pattern_csr_noalloc(int64_t n_elem, int32_t dofs_per_elem, int64_t n_dofs
 /* Release a pattern.  Waits for the device to finish pending work first. */
 int fe_pattern_free(fe_pattern *pattern);
 
+/* Stream-ordered release: the pattern's device arrays are freed at the
+ * current point of `stream` (no host wait); the handle is invalid on return.
+ * Every use of the pattern on other streams must be ordered before that
+ * point (e.g. by events) by the caller. */
+int fe_pattern_free_async(fe_pattern *pattern, void *stream);
+
 /* Borrowed device pointers to the CSR arrays (§2.2, Fig. 1c): row_ptr int64
  * [n_dofs + 1], col_idx int32 [nnz] sorted ascending within each row.  Valid
  * until fe_pattern_free.  Any output pointer may be NULL. */

@@ -894,6 +894,23 @@ int fe_pattern_free(fe_pattern *p)
     return FE_OK;
 }
 
+int fe_pattern_free_async(fe_pattern *p, void *stream)
+{
+    if (!p) return FE_ERR_INVALID_ARG;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    const int dev = p->ctx->device;
+    if (prev != dev) cudaSetDevice(dev);
+    pattern_release(p, (cudaStream_t)stream);
+    const cudaError_t e = cudaGetLastError();
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        fe_set_last_cuda_error(e, "fe_pattern_free_async", __LINE__);
+        return FE_ERR_DEVICE;
+    }
+    return FE_OK;
+}
+
 int fe_pattern_csr(const fe_pattern *p, const int64_t **row_ptr, const int32_t **col_idx, int64_t *nnz)
 {
     if (!p) return FE_ERR_INVALID_ARG;

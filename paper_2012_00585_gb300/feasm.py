@@ -156,6 +156,7 @@ def load():
             "fe_tune_get": (i, [vp, i, ctypes.POINTER(i)]),
             "fe_pattern_build": (i, [vp, i64, i32, i64, vp, u32, vp, pp]),
             "fe_pattern_free": (i, [vp]),
+            "fe_pattern_free_async": (i, [vp, vp]),
             "fe_pattern_csr_noalloc": (i, [i64, i32, i64, vp, vp, vp, i64, ctypes.POINTER(i64), vp]),
             "fe_pattern_csr": (i, [vp, pp, pp, ctypes.POINTER(i64)]),
             "fe_pattern_crac": (i, [vp, pp, pp, ctypes.POINTER(i64)]),
@@ -297,6 +298,10 @@ def fe_pattern_csr_noalloc(n_elem, dofs_per_elem, n_dofs, elem_dofs, row_ptr, co
 
 def fe_pattern_free(pattern):
     _check(load().fe_pattern_free(pattern), "fe_pattern_free")
+
+
+def fe_pattern_free_async(pattern, stream=None):
+    _check(load().fe_pattern_free_async(pattern, _stream(stream)), "fe_pattern_free_async")
 
 
 def fe_pattern_csr(pattern):

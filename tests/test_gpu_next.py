@@ -127,3 +127,25 @@ def test_rowlock_timeout_is_reported(ctx, fmt):
     assert feasm.fe_device_status(ctx) == 0
     gu.assert_within_row_tol(rp, got, exp, tau)
     g.free()
+
+
+def test_pattern_free_async_is_stream_ordered(ctx):
+    """fe_pattern_free_async releases the arrays at the stream's current
+    point: work queued before it on the stream still reads them."""
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    D, n_dofs = wl.hex_q1_grid(4, 3)
+    K = wl.random_matrices(D.shape[0], D.shape[1], seed=21)
+    rp, ci = oracle.csr_pattern(D, n_dofs)
+    exp = oracle.assemble_csr(D, K, rp, ci)
+    s = torch.cuda.Stream()
+    Dd = torch.from_numpy(D).cuda()
+    Kd = torch.from_numpy(K).cuda()
+    for _ in range(3):
+        p = feasm.fe_pattern_build(ctx, D.shape[0], D.shape[1], n_dofs, Dd, feasm.FE_PATTERN_ALL, s)
+        v = torch.empty(feasm.fe_pattern_info_get(p)["nnz"], dtype=torch.float64, device="cuda")
+        feasm.fe_assemble_csr(ctx, p, Kd, v, feasm.FE_DETERMINISTIC, 0, s)
+        feasm.fe_pattern_free_async(p, s)
+        s.synchronize()
+        assert np.array_equal(v.cpu().numpy().view(np.uint64), exp.view(np.uint64))
+    assert feasm.fe_device_status(ctx) == 0
