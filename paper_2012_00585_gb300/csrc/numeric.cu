@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) k_atomic_generic(const double *__restrict
 // Incidences are taken U at a time: their K slices and slots are loaded
 // first, then added strictly in ascending element order.
 template <int NLN, int BB, typename MT, bool CRAC, int U>
-__global__ void __launch_bounds__(256, U == 4 ? 4 : 1) k_gather_node(const double *__restrict__ K, int64_t n_nodes, Geo g,
+__global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_gather_node(const double *__restrict__ K, int64_t n_nodes, Geo g,
                                                      const MT *__restrict__ map, const MT *__restrict__ mapc, int cap,
                                                      int accumulate, double *values)
 {
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(256) k_gather_generic(const double *__restrict
                 rp = g.run_ptr[e];
                 nr = (int)(g.run_ptr[e + 1] - rp);
             }
-            if (!BATCHED) {
+            if constexpr (!BATCHED) {
                 // one entry per lane at a time (fewer registers: more warps for small slices)
                 for (int q = lane; q < chk; q += 32) {
                     const int jr = q / n_loc, c = q - jr * n_loc;
@@ -298,35 +298,34 @@ __global__ void __launch_bounds__(256) k_gather_generic(const double *__restrict
                     }
                     acc[jr * RL + (int64_t)B * pos + c % B] += chunk[q];
                 }
-                __syncwarp();
-                continue;
-            }
-            for (int q0 = lane; q0 < chk; q0 += 128) {
-                double kv[4];
-                int slot[4];
+            } else {
+                for (int q0 = lane; q0 < chk; q0 += 128) {
+                    double kv[4];
+                    int slot[4];
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    const int q = q0 + 32 * w;
-                    kv[w] = 0.0;
-                    slot[w] = -1;
-                    if (q < chk) {
-                        const int jr = q / n_loc, c = q - jr * n_loc;
-                        const int kc = c / B;
-                        int pos;
-                        if (!CRAC) {
-                            pos = (int)map[(int64_t)t * nln + kc];
-                        } else {
-                            int k, off;
-                            run_of_multi(g.run_mask + e * g.mask_words, kc, k, off);
-                            pos = (int)mapc[rp * nln + (int64_t)kr * nr + k] + off;
+                    for (int w = 0; w < 4; ++w) {
+                        const int q = q0 + 32 * w;
+                        kv[w] = 0.0;
+                        slot[w] = -1;
+                        if (q < chk) {
+                            const int jr = q / n_loc, c = q - jr * n_loc;
+                            const int kc = c / B;
+                            int pos;
+                            if (!CRAC) {
+                                pos = (int)map[(int64_t)t * nln + kc];
+                            } else {
+                                int k, off;
+                                run_of_multi(g.run_mask + e * g.mask_words, kc, k, off);
+                                pos = (int)mapc[rp * nln + (int64_t)kr * nr + k] + off;
+                            }
+                            kv[w] = chunk[q];  // plain load: neighbouring rows' slices share lines
+                            slot[w] = (int)(jr * RL + (int64_t)B * pos + c % B);
                         }
-                        kv[w] = chunk[q];  // plain load: neighbouring rows' slices share lines
-                        slot[w] = (int)(jr * RL + (int64_t)B * pos + c % B);
                     }
-                }
 #pragma unroll
-                for (int w = 0; w < 4; ++w)
-                    if (slot[w] >= 0) acc[slot[w]] += kv[w];
+                    for (int w = 0; w < 4; ++w)
+                        if (slot[w] >= 0) acc[slot[w]] += kv[w];
+                }
             }
             __syncwarp();
         }
