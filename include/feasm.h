@@ -111,6 +111,13 @@ typedef struct fe_pattern_info {
  * memory pool for patterns and workspace.  *out receives the handle. */
 int fe_create(fe_ctx **out, int device, size_t hbm_budget_bytes);
 
+/* fe_create with an upper bound on the context's memory pool: every device
+ * allocation the library makes for this context (patterns, workspace) comes
+ * from the pool, and one that would take it past `pool_limit_bytes` fails
+ * with FE_ERR_OOM, cleanly (the call releases what it had allocated; the
+ * context stays usable).  0 = no bound beyond the device's. */
+int fe_create_ex(fe_ctx **out, int device, size_t hbm_budget_bytes, size_t pool_limit_bytes);
+
 /* Destroy a context: waits for its device work, then frees its memory.  Every
  * pattern created from it must have been freed. */
 int fe_destroy(fe_ctx *ctx);
@@ -154,7 +161,8 @@ uint64_t fe_kernel_launches(void);
                                     (default), 2 shared-memory-staged row
                                     gather, 3 pipelined staged gather, 4 row
                                     gather fed by bulk copies (TMA) through a
-                                    ring of stages                           */
+                                    ring of stages, 5 two node rows per warp
+                                    sharing the FP64 add instructions        */
 #define FE_KNOB_GATHER_BATCH 1   /* incidences per register batch: 4 or 8   */
 #define FE_KNOB_GATHER_WARPS 2   /* warps per block of the gather: 1..8      */
 #define FE_KNOB_ATOMIC_KERNEL 3  /* FE_ATOMIC: 1 register warp-per-element,

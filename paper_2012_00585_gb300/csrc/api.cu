@@ -220,6 +220,14 @@ int fe_alloc(fe_ctx *ctx, void **p, size_t bytes, cudaStream_t s)
 {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (ctx->pool_limit) {  // the context's bound on its pool (bytes handed out, not yet freed)
+        uint64_t used = 0;
+        if (cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess ||
+            used + bytes > ctx->pool_limit) {
+            cudaGetLastError();
+            return FE_ERR_OOM;
+        }
+    }
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, s);
     if (e != cudaSuccess) {
         fe_set_last_cuda_error(e, "cudaMallocFromPoolAsync", __LINE__);
@@ -273,6 +281,11 @@ uint64_t fe_kernel_launches(void) { return g_launches.load(std::memory_order_rel
 
 int fe_create(fe_ctx **out, int device, size_t hbm_budget_bytes)
 {
+    return fe_create_ex(out, device, hbm_budget_bytes, 0);
+}
+
+int fe_create_ex(fe_ctx **out, int device, size_t hbm_budget_bytes, size_t pool_limit_bytes)
+{
     if (!out) return FE_ERR_INVALID_ARG;
     *out = nullptr;
     int n_dev = 0;
@@ -307,6 +320,7 @@ int fe_create(fe_ctx **out, int device, size_t hbm_budget_bytes)
         hbm_budget_bytes = (size_t)(0.9 * (double)free_b);
     }
     ctx->hbm_budget = hbm_budget_bytes;
+    ctx->pool_limit = pool_limit_bytes;
     *out = ctx;
     return FE_OK;
 }
@@ -328,7 +342,7 @@ int fe_tune_set(fe_ctx *ctx, int knob, int value)
     if (!ctx || knob < 0 || knob >= FE_KNOB_COUNT) return FE_ERR_INVALID_ARG;
     int lo = 0, hi = 0;
     switch (knob) {
-    case FE_KNOB_GATHER_KERNEL: hi = 4; break;
+    case FE_KNOB_GATHER_KERNEL: hi = 5; break;
     case FE_KNOB_GATHER_BATCH: hi = 8; break;
     case FE_KNOB_GATHER_WARPS: hi = 8; break;
     case FE_KNOB_ATOMIC_KERNEL: hi = 2; break;

@@ -33,6 +33,7 @@ struct fe_ctx {
     int device = 0;
     int num_sms = 0;
     size_t hbm_budget = 0;
+    size_t pool_limit = 0;  // fe_create_ex: bound on the pool's bytes in use (0 = none)
     cudaMemPool_t pool = nullptr;
     int *d_status = nullptr;  // device status word: first FE_ERR_* a kernel recorded
     int knob[FE_KNOB_COUNT] = {};  // schedule choices (0 = library default)

@@ -235,6 +235,131 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
     }
 }
 
+// Two node rows per warp (nodes 2p and 2p+1, each with its own accumulator):
+// the slices of incidence s of both rows share one pass of the lanes, so
+// 2 x CHK entries take ceil(2 CHK / 32) FP64 add instructions instead of
+// 2 ceil(CHK / 32) (72-entry slices: 5 instead of 6).  The two rows never
+// share an accumulator slot, so lanes of both rows add in the same
+// instruction; within a row the incidences stay in ascending element order
+// (bit-identical to the sequential sum).  Adjacent nodes also read adjacent
+// slices of their shared elements.
+template <int NLN, int BB, typename MT, bool CRAC, int U>
+__global__ void __launch_bounds__(256) k_gather_pair(const double *__restrict__ K, int64_t n_nodes, Geo g,
+                                                     const MT *__restrict__ map, const MT *__restrict__ mapc, int cap,
+                                                     int accumulate, double *values)
+{
+    constexpr int NLOC = NLN * BB;
+    constexpr int NN = NLOC * NLOC;
+    constexpr int CHK = BB * NLOC;
+    constexpr int IT = (2 * CHK + 31) / 32;
+    extern __shared__ double acc_all[];
+    const int lane = threadIdx.x & 31;
+    double *acc0 = acc_all + (size_t)(threadIdx.x >> 5) * 2 * cap;
+    double *acc1 = acc0 + cap;
+    // per lane slot: row of the pair, block row jr, column c
+    int row_[IT], jr_[IT], c_[IT], ku[IT], offu[IT];
+#pragma unroll
+    for (int j = 0; j < IT; ++j) {
+        const int q = lane + 32 * j;
+        const int qq = q < 2 * CHK ? q : 0;
+        row_[j] = qq / CHK;
+        const int qr = qq - row_[j] * CHK;
+        jr_[j] = qr / NLOC;
+        c_[j] = qr % NLOC;
+        ku[j] = 0;
+        offu[j] = 0;
+        if (CRAC && g.uniform_R) run_of(g.run_mask[0], c_[j] / BB, ku[j], offu[j]);
+    }
+    const int64_t n_pairs = (n_nodes + 1) / 2;
+    for (int64_t pr = fe_warp_id(); pr < n_pairs; pr += fe_warps()) {
+        const int64_t v0 = 2 * pr, v1 = 2 * pr + 1;
+        const bool has1 = v1 < n_nodes;
+        int64_t rb0, RL0, rb1 = 0, RL1 = 0;
+        if (!CRAC) {
+            rb0 = g.row_ptr[BB * v0];
+            RL0 = g.row_ptr[BB * v0 + 1] - rb0;
+            if (has1) {
+                rb1 = g.row_ptr[BB * v1];
+                RL1 = g.row_ptr[BB * v1 + 1] - rb1;
+            }
+        } else {
+            rb0 = crac_row_base(g, BB * v0);
+            RL0 = crac_row_base(g, BB * v0 + 1) - rb0;
+            if (has1) {
+                rb1 = crac_row_base(g, BB * v1);
+                RL1 = crac_row_base(g, BB * v1 + 1) - rb1;
+            }
+        }
+        const int total0 = (int)(BB * RL0), total1 = (int)(BB * RL1);
+        for (int k = lane; k < total0; k += 32) acc0[k] = accumulate ? values[rb0 + k] : 0.0;
+        for (int k = lane; k < total1; k += 32) acc1[k] = accumulate ? values[rb1 + k] : 0.0;
+        __syncwarp();
+        const int64_t a0 = g.adj_ptr[v0], b0 = g.adj_ptr[v0 + 1];
+        const int64_t a1 = has1 ? g.adj_ptr[v1] : 0, b1 = has1 ? g.adj_ptr[v1 + 1] : 0;
+        const int64_t steps = max(b0 - a0, b1 - a1);
+        for (int64_t s0 = 0; s0 < steps; s0 += U) {
+            double kv[U][IT];
+            int rel[U][IT];
+            uint32_t have = 0;  // bit 2u + r: incidence s0+u of row r exists
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool h0 = a0 + s0 + u < b0, h1 = a1 + s0 + u < b1;
+                have |= (h0 ? 1u : 0u) << (2 * u) | (h1 ? 1u : 0u) << (2 * u + 1);
+                const uint32_t t0 = h0 ? g.adj[a0 + s0 + u] : 0u;
+                const uint32_t t1 = h1 ? g.adj[a1 + s0 + u] : 0u;
+#pragma unroll
+                for (int j = 0; j < IT; ++j) {
+                    const int q = lane + 32 * j;
+                    const int r = row_[j];
+                    const bool h = r == 0 ? h0 : h1;
+                    kv[u][j] = 0.0;
+                    rel[u][j] = 0;
+                    if (q < 2 * CHK && h) {
+                        const uint32_t t = r == 0 ? t0 : t1;
+                        const uint32_t e = t / NLN;
+                        const int kr = (int)(t - e * NLN);
+                        kv[u][j] = __ldcs(K + (int64_t)e * NN + (int64_t)kr * CHK + (q - r * CHK));
+                        const int kc = c_[j] / BB;
+                        int pos;
+                        if (!CRAC) {
+                            pos = (int)map[(int64_t)t * NLN + kc];
+                        } else {
+                            int64_t rp;
+                            int nr;
+                            int k = ku[j], off = offu[j];
+                            if (g.uniform_R) {
+                                nr = g.uniform_R;
+                                rp = (int64_t)e * nr;
+                            } else {
+                                rp = g.run_ptr[e];
+                                nr = (int)(g.run_ptr[e + 1] - rp);
+                                run_of(g.run_mask[e], kc, k, off);
+                            }
+                            pos = (int)mapc[rp * NLN + (int64_t)kr * nr + k] + off;
+                        }
+                        rel[u][j] = jr_[j] * (int)(r == 0 ? RL0 : RL1) + BB * pos + c_[j] % BB;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                for (int j = 0; j < IT; ++j) {
+                    const int r = row_[j];
+                    if (lane + 32 * j < 2 * CHK && (have >> (2 * u + r) & 1u)) {
+                        double *acc = r == 0 ? acc0 : acc1;
+                        acc[rel[u][j]] += kv[u][j];
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int k = lane; k < total0; k += 32) values[rb0 + k] = acc0[k];
+        for (int k = lane; k < total1; k += 32) values[rb1 + k] = acc1[k];
+        __syncwarp();
+    }
+}
+
 // Any element shape.  A unit is R of the B DOF rows of a node (R chosen by
 // the host so that the accumulator, R x row length doubles, stays small for
 // large B); the rows of a node have the same length and are contiguous in
@@ -1076,6 +1201,22 @@ int launch_gather(const fe_pattern *p, const double *K, double *values, int accu
     int W = ctx->knob[FE_KNOB_GATHER_WARPS];
     if constexpr (NLN > 0) {
         constexpr int CHK = BB * NLN * BB;
+        if (kind == 5) {
+            constexpr int UP = 2;
+            int Wp = (W > 0 && W <= 8) ? W : 2;
+            while (Wp > 1 && (size_t)Wp * 2 * cap * 8 > 64 * 1024) Wp >>= 1;
+            const size_t psm = (size_t)Wp * 2 * cap * 8;
+            if (psm <= 200 * 1024) {
+                FE_TRY(configure_smem(k_gather_pair<NLN, BB, MT, CRAC, UP>, psm));
+                const int pgrid = fe_grid_resident(k_gather_pair<NLN, BB, MT, CRAC, UP>, (p->n_nodes + 1) / 2 * 32,
+                                                   Wp * 32, sms, psm);
+                k_gather_pair<NLN, BB, MT, CRAC, UP><<<pgrid, Wp * 32, psm, s>>>(
+                    K, p->n_nodes, g, (const MT *)p->map_csr, (const MT *)p->map_crac, cap, accumulate, values);
+                fe_note_launch();
+                FE_CUDA(cudaGetLastError());
+                return FE_OK;
+            }
+        }
         if (kind == 4 && tma_ok(p, K, CHK)) {
             constexpr int UB = 8;
             int S = ctx->knob[FE_KNOB_GATHER_STAGES] > 0 ? ctx->knob[FE_KNOB_GATHER_STAGES] : 4;

@@ -145,6 +145,7 @@ def load():
         pp = ctypes.POINTER(vp)
         sig = {
             "fe_create": (i, [pp, i, ctypes.c_size_t]),
+            "fe_create_ex": (i, [pp, i, ctypes.c_size_t, ctypes.c_size_t]),
             "fe_destroy": (i, [vp]),
             "fe_strerror": (ctypes.c_char_p, [i]),
             "fe_last_cuda_error": (ctypes.c_char_p, []),
@@ -262,6 +263,13 @@ def fe_tune_get(ctx, knob: int) -> int:
 def fe_create(device: int = 0, hbm_budget_bytes: int = 0):
     out = ctypes.c_void_p()
     _check(load().fe_create(ctypes.byref(out), int(device), int(hbm_budget_bytes)), "fe_create")
+    return out
+
+
+def fe_create_ex(device: int = 0, hbm_budget_bytes: int = 0, pool_limit_bytes: int = 0):
+    out = ctypes.c_void_p()
+    _check(load().fe_create_ex(ctypes.byref(out), int(device), int(hbm_budget_bytes), int(pool_limit_bytes)),
+           "fe_create_ex")
     return out
 
 

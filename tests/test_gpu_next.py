@@ -149,3 +149,34 @@ def test_pattern_free_async_is_stream_ordered(ctx):
         s.synchronize()
         assert np.array_equal(v.cpu().numpy().view(np.uint64), exp.view(np.uint64))
     assert feasm.fe_device_status(ctx) == 0
+
+
+def test_allocation_failure_is_reported():
+    """Host-side fault injection: a context whose memory pool is bounded to
+    8 MiB.  A mesh whose pattern needs more fails with FE_ERR_OOM; what the
+    build had allocated is released, the context stays usable, and a small
+    mesh still builds and assembles exactly."""
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = feasm.fe_create_ex(0, 0, 8 << 20)
+    try:
+        D, n_dofs = wl.hex_q1_grid(24, 3)  # needs well over 8 MiB of pattern and workspace
+        Dd = torch.from_numpy(D).cuda()
+        for _ in range(2):
+            with pytest.raises(feasm.FeError) as ei:
+                feasm.fe_pattern_build(c, D.shape[0], D.shape[1], n_dofs, Dd, feasm.FE_PATTERN_ALL)
+            assert ei.value.code == feasm.FE_ERR_OOM
+        Ds, n_s = wl.hex_q1_grid(3, 3)
+        K = wl.random_matrices(Ds.shape[0], Ds.shape[1], seed=31)
+        p = feasm.fe_pattern_build(c, Ds.shape[0], Ds.shape[1], n_s, torch.from_numpy(Ds).cuda(), feasm.FE_PATTERN_ALL)
+        v = torch.empty(feasm.fe_pattern_info_get(p)["nnz"], dtype=torch.float64, device="cuda")
+        feasm.fe_assemble_csr(c, p, torch.from_numpy(K).cuda(), v, feasm.FE_DETERMINISTIC, 0)
+        torch.cuda.synchronize()
+        rp, ci = oracle.csr_pattern(Ds, n_s)
+        assert np.array_equal(v.cpu().numpy().view(np.uint64), oracle.assemble_csr(Ds, K, rp, ci).view(np.uint64))
+        feasm.fe_pattern_free(p)
+        assert feasm.fe_device_status(c) == 0
+    finally:
+        feasm.fe_destroy(c)

@@ -362,7 +362,7 @@ def test_c3_full_size_sampled_rows(ctx):
     g.free()
 
 
-@pytest.mark.parametrize("gkind", [1, 2, 3, 4])
+@pytest.mark.parametrize("gkind", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("akind", [1, 2])
 def test_every_kernel_variant(ctx, gkind, akind):
     """Each schedule knob value gives the same results: deterministic
