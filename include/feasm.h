@@ -153,6 +153,11 @@ int fe_hbm_probe_bulk(fe_ctx *ctx, const double *src, int64_t n, void *stream);
  * the launches inside it. */
 uint64_t fe_kernel_launches(void);
 
+/* 1 when this library was built with its device index checks (-DFE_DEBUG;
+ * an index outside its array then records FE_ERR_DEVICE in the context's
+ * status word and the access is skipped), 0 for the release build. */
+int fe_debug_checks(void);
+
 /* ---- schedule knobs ------------------------------------------------------
  * Kernel and launch-shape choices of the numeric phase, per context.  0 means
  * the library's default; an autotuner may set them.  Results do not depend on

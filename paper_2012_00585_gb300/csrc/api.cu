@@ -279,6 +279,15 @@ const char *fe_last_cuda_error(void) { return g_last_cuda; }
 
 uint64_t fe_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int fe_debug_checks(void)
+{
+#ifdef FE_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 int fe_create(fe_ctx **out, int device, size_t hbm_budget_bytes)
 {
     return fe_create_ex(out, device, hbm_budget_bytes, 0);

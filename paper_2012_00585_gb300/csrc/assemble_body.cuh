@@ -18,6 +18,8 @@ struct Geo {
     const uint32_t *adj;
     int uniform_R;  // > 0 when every element has this many runs and the same mask
     int mask_words;
+    int64_t nnz;    // values length (index checks of debug builds)
+    int *status;    // the context's device status word
 };
 
 __device__ __forceinline__ int64_t crac_row_base(const Geo &g, int64_t i) { return g.col_align[g.crac_ptr[i] + 1]; }
@@ -50,7 +52,8 @@ __device__ __forceinline__ void run_of_multi(const uint32_t *m, int kc, int &k, 
 inline Geo geo_of(const fe_pattern *p)
 {
     return Geo{p->node_dofs, p->row_ptr,  p->crac_ptr, p->col_align, p->run_mask,
-               p->run_ptr,   p->adj_ptr, p->adj,      p->uniform_runs ? p->runs_per_elem : 0, p->mask_words};
+               p->run_ptr,   p->adj_ptr, p->adj,      p->uniform_runs ? p->runs_per_elem : 0, p->mask_words,
+               p->nnz,       p->ctx->d_status};
 }
 
 // One element of NLN blocks of BB DOFs (NLN*BB <= 32), the warp cooperating:
@@ -112,7 +115,7 @@ __device__ __forceinline__ void atomic_element(const double *__restrict__ K, int
                     const int off = __shfl_sync(0xffffffffu, koff, kc);
                     pos = (int)mapc[rp * NLN + (r / BB) * nr + k] + off;
                 }
-                if (q < NN) {
+                if (q < NN && FE_IN_BOUNDS(b + (int64_t)BB * pos + c % BB, g.nnz, g.status)) {
                     double *dst = values + b + (int64_t)BB * pos + c % BB;
                     if (PLAIN) *dst = *dst + kv[u];
                     else atomicAdd(dst, kv[u]);
@@ -152,6 +155,7 @@ __device__ __forceinline__ void atomic_element_generic(const double *__restrict_
         int pos;
         if (!CRAC) pos = (int)map[(e * nln + r / B) * nln + kc];
         else pos = (int)mapc[rp * nln + (int64_t)(r / B) * nr + k_s[kc]] + off_s[kc];
+        if (!FE_IN_BOUNDS(base_s[r] + (int64_t)B * pos + c % B, g.nnz, g.status)) continue;
         double *dst = values + base_s[r] + (int64_t)B * pos + c % B;
         if (PLAIN) *dst = *dst + __ldcs(Ke + q);
         else atomicAdd(dst, __ldcs(Ke + q));
@@ -193,6 +197,7 @@ __device__ __forceinline__ void gather_row(const double *__restrict__ K, int64_t
         RL = crac_row_base(g, i0 + 1) - rb;
     }
     const int total = (int)(BB * RL);
+    if (total > 0 && !FE_IN_BOUNDS(rb + total - 1, g.nnz, g.status)) return;
     for (int k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
     __syncwarp();
     const int64_t a = g.adj_ptr[v], b = g.adj_ptr[v + 1];
@@ -243,7 +248,8 @@ __device__ __forceinline__ void gather_row(const double *__restrict__ K, int64_t
         for (int u = 0; u < U; ++u) {
 #pragma unroll
             for (int j = 0; j < IT; ++j)
-                if (s0 + u < b && lane + 32 * j < CHK) acc[rel[u][j]] += kv[u][j];
+                if (s0 + u < b && lane + 32 * j < CHK && FE_IN_BOUNDS(rel[u][j], total, g.status))
+                    acc[rel[u][j]] += kv[u][j];
             __syncwarp();
         }
     }
@@ -270,6 +276,7 @@ __device__ __forceinline__ void gather_row_generic(const double *__restrict__ K,
         RL = crac_row_base(g, i0 + 1) - rb;
     }
     const int64_t total = B * RL;
+    if (total > 0 && !FE_IN_BOUNDS(rb + total - 1, g.nnz, g.status)) return;
     for (int64_t k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
     __syncwarp();
     for (int64_t s = g.adj_ptr[v]; s < g.adj_ptr[v + 1]; ++s) {
@@ -294,7 +301,8 @@ __device__ __forceinline__ void gather_row_generic(const double *__restrict__ K,
                 run_of_multi(g.run_mask + e * g.mask_words, kc, k, off);
                 pos = (int)mapc[rp * nln + (int64_t)kr * nr + k] + off;
             }
-            acc[jr * RL + (int64_t)B * pos + c % B] += chunk[q];
+            if (FE_IN_BOUNDS(jr * RL + (int64_t)B * pos + c % B, total, g.status))
+                acc[jr * RL + (int64_t)B * pos + c % B] += chunk[q];
         }
         __syncwarp();
     }

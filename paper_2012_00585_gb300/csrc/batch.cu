@@ -154,7 +154,8 @@ __device__ __noinline__ bool staged_tile(const BatchItemDev *__restrict__ it, in
                     const int kw = kk_s[kc];
                     pos = pos_s[(r / BB) * (kw >> 16) + (kw & 0xffff)] + off_s[kc];
                 }
-                atomicAdd(values + base_s[r] + BB * pos + c % BB, stg[q]);
+                if (FE_IN_BOUNDS(base_s[r] + BB * pos + c % BB, g.nnz, g.status))
+                    atomicAdd(values + base_s[r] + BB * pos + c % BB, stg[q]);
             }
         }
         __syncwarp();
@@ -316,7 +317,8 @@ __global__ void __launch_bounds__(SCHED_THREADS) k_batch(const BatchItemDev *__r
                         pos = (it.map_bytes == 1 ? (int)((const uint8_t *)it.mapc)[mi]
                                                  : (int)((const uint16_t *)it.mapc)[mi]) + off_s[kc];
                     }
-                    atomicAdd(it.values + base_s[r] + (int64_t)B * pos + c % B, __ldcs(it.K + e * NN + q));
+                    if (FE_IN_BOUNDS(base_s[r] + (int64_t)B * pos + c % B, it.g.nnz, it.g.status))
+                        atomicAdd(it.values + base_s[r] + (int64_t)B * pos + c % B, __ldcs(it.K + e * NN + q));
                 }
                 __syncthreads();
             }
@@ -394,7 +396,7 @@ __global__ void __launch_bounds__(SCHED_THREADS) k_batch(const BatchItemDev *__r
                     const int q = (int)(x - e * NN);
                     const int64_t slot = it.map_bytes == 1 ? entry_slot<uint8_t, CRAC>(it, e, q)
                                                            : entry_slot<uint16_t, CRAC>(it, e, q);
-                    atomicAdd(it.values + slot, __ldcs(it.K + x));
+                    if (FE_IN_BOUNDS(slot, it.g.nnz, it.g.status)) atomicAdd(it.values + slot, __ldcs(it.K + x));
                 }
             }
         }

@@ -99,6 +99,22 @@ void fe_free_async(void *p, cudaStream_t s);
 int fe_scan_i32_to_i64(fe_ctx *ctx, const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
 int fe_scan_i64(fe_ctx *ctx, const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
 
+// Debug builds (-DFE_DEBUG) check device indices before the accesses that
+// use FE_IN_BOUNDS: an index outside [0, n) records FE_ERR_DEVICE in the
+// context's status word and the access is skipped (nothing traps).  Release
+// builds compile the checks away.
+#ifdef FE_DEBUG
+__device__ __forceinline__ bool fe_in_bounds(int64_t i, int64_t n, int *status)
+{
+    if (i >= 0 && i < n) return true;
+    if (status) atomicCAS(status, 0, FE_ERR_DEVICE);
+    return false;
+}
+#define FE_IN_BOUNDS(i, n, st) fe_in_bounds((int64_t)(i), (int64_t)(n), (st))
+#else
+#define FE_IN_BOUNDS(i, n, st) true
+#endif
+
 static inline int fe_grid_for(int64_t work, int threads, int num_sms, int per_sm = 8)
 {
     int64_t blocks = (work + threads - 1) / threads;

@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
             RL = crac_row_base(g, i0 + 1) - rb;
         }
         const int total = (int)(BB * RL);
+        if (total > 0 && (!FE_IN_BOUNDS(rb + total - 1, g.nnz, g.status) || !FE_IN_BOUNDS(total - 1, cap, g.status)))
+            continue;
         for (int k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
         __syncwarp();
         const int64_t a = g.adj_ptr[v], b = g.adj_ptr[v + 1];
@@ -226,7 +228,8 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
             for (int u = 0; u < U; ++u) {
 #pragma unroll
                 for (int j = 0; j < IT; ++j)
-                    if (s0 + u < b && lane + 32 * j < CHK) acc[rel[u][j]] += kv[u][j];
+                    if (s0 + u < b && lane + 32 * j < CHK && FE_IN_BOUNDS(rel[u][j], total, g.status))
+                        acc[rel[u][j]] += kv[u][j];
                 __syncwarp();
             }
         }
@@ -395,6 +398,8 @@ __global__ void __launch_bounds__(256) k_gather_generic(const double *__restrict
         rb += j0 * RL;
         const int64_t total = nr_rows * RL;
         const int chk = nr_rows * n_loc;
+        if (total > 0 && (!FE_IN_BOUNDS(rb + total - 1, g.nnz, g.status) || !FE_IN_BOUNDS(total - 1, cap, g.status)))
+            continue;
         for (int64_t k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
         __syncwarp();
         for (int64_t s = g.adj_ptr[v]; s < g.adj_ptr[v + 1]; ++s) {
@@ -421,7 +426,8 @@ __global__ void __launch_bounds__(256) k_gather_generic(const double *__restrict
                         run_of_multi(g.run_mask + e * g.mask_words, kc, k, off);
                         pos = (int)mapc[rp * nln + (int64_t)kr * nr + k] + off;
                     }
-                    acc[jr * RL + (int64_t)B * pos + c % B] += chunk[q];
+                    if (FE_IN_BOUNDS(jr * RL + (int64_t)B * pos + c % B, total, g.status))
+                        acc[jr * RL + (int64_t)B * pos + c % B] += chunk[q];
                 }
             } else {
                 for (int q0 = lane; q0 < chk; q0 += 128) {
@@ -449,7 +455,7 @@ __global__ void __launch_bounds__(256) k_gather_generic(const double *__restrict
                     }
 #pragma unroll
                     for (int w = 0; w < 4; ++w)
-                        if (slot[w] >= 0) acc[slot[w]] += kv[w];
+                        if (slot[w] >= 0 && FE_IN_BOUNDS(slot[w], total, g.status)) acc[slot[w]] += kv[w];
                 }
             }
             __syncwarp();
@@ -1119,7 +1125,8 @@ __global__ void __launch_bounds__(128) k_atomic_tma(const double *__restrict__ K
                     const int kw = kk_s[kc];
                     pos = pos_s[(r / BB) * (kw >> 16) + (kw & 0xffff)] + off_s[kc];
                 }
-                atomicAdd(values + base_s[r] + BB * pos + c % BB, stg[q]);
+                if (FE_IN_BOUNDS(base_s[r] + BB * pos + c % BB, g.nnz, g.status))
+                    atomicAdd(values + base_s[r] + BB * pos + c % BB, stg[q]);
             }
         }
         __syncwarp();

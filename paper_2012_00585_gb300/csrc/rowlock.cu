@@ -75,8 +75,10 @@ __global__ void __launch_bounds__(256) k_rowlock(const double *__restrict__ K, i
                 int pos;
                 if (!CRAC) pos = (int)map[(e * NLN + r / BB) * NLN + kc];
                 else pos = (int)mapc[rp * NLN + (r / BB) * nr + k_c] + off_c;
-                double *dst = values + base + (int64_t)BB * pos + c % BB;
-                __stcg(dst, __ldcg(dst) + __ldcs(Ke + r * NLOC + c));
+                if (FE_IN_BOUNDS(base + (int64_t)BB * pos + c % BB, g.nnz, g.status)) {
+                    double *dst = values + base + (int64_t)BB * pos + c % BB;
+                    __stcg(dst, __ldcg(dst) + __ldcs(Ke + r * NLOC + c));
+                }
             }
             __syncwarp();
             if (lane == 0) {
@@ -139,6 +141,7 @@ __global__ void __launch_bounds__(256) k_rowlock_generic(const double *__restric
                 int pos;
                 if (!CRAC) pos = (int)map[(e * nln + r / B) * nln + kc];
                 else pos = (int)mapc[rp * nln + (int64_t)(r / B) * nr + k_s[w][kc]] + off_s[w][kc];
+                if (!FE_IN_BOUNDS(base + (int64_t)B * pos + c % B, g.nnz, g.status)) continue;
                 double *dst = values + base + (int64_t)B * pos + c % B;
                 __stcg(dst, __ldcg(dst) + __ldcs(Ke + (int64_t)r * n_loc + c));
             }

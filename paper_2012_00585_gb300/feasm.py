@@ -128,7 +128,7 @@ class fe_server_stats(ctypes.Structure):
 
 
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if os.environ.get("FEASM_DEBUG") == "1" else _build.LIB
 
 
 def load():
@@ -137,7 +137,8 @@ def load():
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.build()
+        # FEASM_DEBUG=1: the build with every device index check compiled in
+        path = _build.build(debug=os.environ.get("FEASM_DEBUG") == "1")
         if not os.path.exists(path):
             raise RuntimeError(f"libfeasm not found at {path}; the CUDA path has no fallback")
         lib = ctypes.CDLL(path)
@@ -150,6 +151,7 @@ def load():
             "fe_strerror": (ctypes.c_char_p, [i]),
             "fe_last_cuda_error": (ctypes.c_char_p, []),
             "fe_kernel_launches": (ctypes.c_uint64, []),
+            "fe_debug_checks": (i, []),
             "fe_device_status": (i, [vp, vp]),
             "fe_tune_set": (i, [vp, i, i]),
             "fe_hbm_probe": (i, [vp, vp, vp, i64, vp]),
@@ -233,6 +235,10 @@ def fe_last_cuda_error() -> str:
 
 def fe_kernel_launches() -> int:
     return int(load().fe_kernel_launches())
+
+
+def fe_debug_checks() -> bool:
+    return bool(load().fe_debug_checks())
 
 
 def fe_device_status(ctx, stream=None) -> int:
