@@ -322,7 +322,13 @@ def run_gpu(args, rank, world, local_rank):
                 "kernel": f"fe_assemble_{fmt} {mode_name} (one call)", "alg_bytes_per_launch": B,
                 "kernel_ms": round(kern_ms, 4),
                 "live_probe_GBps": probe,
-                "frac_of_read_bound": round((8 * N_ent + 4 * n_e * n_loc) / (kern_ms * 1e-3) / 1e9 / probe["read"], 4)}
+                "frac_of_read_bound": round((8 * N_ent + 4 * n_e * n_loc) / (kern_ms * 1e-3) / 1e9 / probe["read"], 4),
+                # the kernel's other bound: one FP64 add per K entry at GB300's FP64 rate
+                # (nominal 1.25 TFLOP/s = 0.625e12 add lane-operations/s at one add per
+                # lane-operation as for a fused multiply-add); no measured FP64 peak exists
+                "fp64": {"adds_per_launch": N_ent, "peak_adds_per_s": 0.625e12, "peak_source": "nominal",
+                         "floor_ms": round(N_ent / 0.625e12 * 1e3, 4),
+                         "frac": round(N_ent / 0.625e12 / (kern_ms * 1e-3), 4)}}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
