@@ -165,22 +165,51 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
         offu[j] = 0;
         if (CRAC && g.uniform_R) run_of(g.run_mask[0], c_[j] / BB, ku[j], offu[j]);
     }
-    for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
-        const int64_t i0 = (int64_t)BB * v;
-        int64_t rb, RL;
-        if (!CRAC) {
-            rb = g.row_ptr[i0];
-            RL = g.row_ptr[i0 + 1] - rb;
+    // CSR rows of 3+ DOF blocks: the next row's pointers and adjacency range
+    // are loaded one row ahead (one dependent load fewer on each row's path;
+    // measured faster there, slower where the registers cost occupancy)
+    constexpr bool PF = !CRAC && BB >= 3;
+    const int64_t W = fe_warps();
+    int64_t p0 = 0, p1 = 0, q0 = 0, q1 = 0;
+    if (PF) {
+        const int64_t v = fe_warp_id();
+        if (v < n_nodes) {
+            p0 = g.row_ptr[(int64_t)BB * v];
+            p1 = g.row_ptr[(int64_t)BB * v + 1];
+            q0 = g.adj_ptr[v];
+            q1 = g.adj_ptr[v + 1];
+        }
+    }
+    for (int64_t v = fe_warp_id(); v < n_nodes; v += W) {
+        int64_t rb, RL, a, b;
+        if constexpr (PF) {
+            rb = p0;
+            RL = p1 - p0;
+            a = q0;
+            b = q1;
+            if (v + W < n_nodes) {
+                p0 = g.row_ptr[(int64_t)BB * (v + W)];
+                p1 = g.row_ptr[(int64_t)BB * (v + W) + 1];
+                q0 = g.adj_ptr[v + W];
+                q1 = g.adj_ptr[v + W + 1];
+            }
         } else {
-            rb = crac_row_base(g, i0);
-            RL = crac_row_base(g, i0 + 1) - rb;
+            const int64_t i0 = (int64_t)BB * v;
+            if (!CRAC) {
+                rb = g.row_ptr[i0];
+                RL = g.row_ptr[i0 + 1] - rb;
+            } else {
+                rb = crac_row_base(g, i0);
+                RL = crac_row_base(g, i0 + 1) - rb;
+            }
+            a = g.adj_ptr[v];
+            b = g.adj_ptr[v + 1];
         }
         const int total = (int)(BB * RL);
         if (total > 0 && (!FE_IN_BOUNDS(rb + total - 1, g.nnz, g.status) || !FE_IN_BOUNDS(total - 1, cap, g.status)))
             continue;
         for (int k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
         __syncwarp();
-        const int64_t a = g.adj_ptr[v], b = g.adj_ptr[v + 1];
         for (int64_t s0 = a; s0 < b; s0 += U) {
             double kv[U][IT];
             int rel[U][IT];
