@@ -162,12 +162,16 @@ int fe_debug_checks(void);
  * Kernel and launch-shape choices of the numeric phase, per context.  0 means
  * the library's default; an autotuner may set them.  Results do not depend on
  * them (FE_DETERMINISTIC stays bit-identical), only speed does. */
-#define FE_KNOB_GATHER_KERNEL 0  /* FE_DETERMINISTIC: 1 register-batched row gather
-                                    (default), 2 shared-memory-staged row
+#define FE_KNOB_GATHER_KERNEL 0  /* FE_DETERMINISTIC: 0 default (6 for one-DOF
+                                    shapes of 4 or 8 nodes, else 1), 1
+                                    register-batched row gather, 2
+                                    shared-memory-staged row
                                     gather, 3 pipelined staged gather, 4 row
                                     gather fed by bulk copies (TMA) through a
                                     ring of stages, 5 two node rows per warp
-                                    sharing the FP64 add instructions        */
+                                    sharing the FP64 add instructions, 6
+                                    one-DOF elements of <= 16 nodes: 4, 8 or
+                                    16 lanes per node row                    */
 #define FE_KNOB_GATHER_BATCH 1   /* incidences per register batch: 4 or 8   */
 #define FE_KNOB_GATHER_WARPS 2   /* warps per block of the gather: 1..8      */
 #define FE_KNOB_ATOMIC_KERNEL 3  /* FE_ATOMIC: 1 register warp-per-element,

@@ -351,7 +351,7 @@ int fe_tune_set(fe_ctx *ctx, int knob, int value)
     if (!ctx || knob < 0 || knob >= FE_KNOB_COUNT) return FE_ERR_INVALID_ARG;
     int lo = 0, hi = 0;
     switch (knob) {
-    case FE_KNOB_GATHER_KERNEL: hi = 5; break;
+    case FE_KNOB_GATHER_KERNEL: hi = 6; break;
     case FE_KNOB_GATHER_BATCH: hi = 8; break;
     case FE_KNOB_GATHER_WARPS: hi = 8; break;
     case FE_KNOB_ATOMIC_KERNEL: hi = 2; break;

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "assemble_body.cuh"
+#include "gather_small.cuh"
 #include "internal.cuh"
 #include "tma.cuh"
 
@@ -194,6 +195,37 @@ __device__ __noinline__ void gather_row_call(const BatchItemDev *__restrict__ it
     const Geo g = it->g;
     gather_row<NLN, BB, MT, CRAC, 4>(it->K, v, g, (const MT *)it->map, (const MT *)it->mapc, acc, accumulate,
                                      it->values, lane);
+}
+
+// The node rows [u0, u1) of a one-DOF item, RPW at a time with G lanes per
+// row (one call per tile).  The warp's accumulator region (cap doubles, cap
+// >= RPW x the item's longest row by the plan) is split into RPW per-row
+// parts of cap / RPW.
+template <int NLN, typename MT, bool CRAC>
+__device__ __noinline__ void gather_tile_small(const BatchItemDev *__restrict__ it, int64_t u0, int64_t u1,
+                                               double *acc, int cap, int accumulate, int lane)
+{
+    constexpr int RPW = SmallRows<NLN>::RPW;
+    const Geo g = it->g;
+    const double *K = it->K;
+    double *values = it->values;
+    const MT *map = (const MT *)it->map, *mapc = (const MT *)it->mapc;
+    for (int64_t v0 = u0; v0 < u1; v0 += RPW)
+        gather_rows_small<NLN, MT, CRAC, 4>(K, v0, 1, u1, g, map, mapc, acc, cap / RPW, accumulate, values, lane);
+}
+
+// The node rows [u0, u1) of an item with a specialised shape, one call per
+// tile (the item's geometry is read once per tile, not once per row).
+template <int NLN, int BB, typename MT, bool CRAC>
+__device__ __noinline__ void gather_tile_node(const BatchItemDev *__restrict__ it, int64_t u0, int64_t u1,
+                                              double *acc, int accumulate, int lane)
+{
+    const Geo g = it->g;
+    const double *K = it->K;
+    double *values = it->values;
+    const MT *map = (const MT *)it->map, *mapc = (const MT *)it->mapc;
+    for (int64_t v = u0; v < u1; ++v)
+        gather_row<NLN, BB, MT, CRAC, 4>(K, v, g, map, mapc, acc, accumulate, values, lane);
 }
 
 template <typename MT, bool CRAC>
@@ -379,9 +411,28 @@ __global__ void __launch_bounds__(SCHED_THREADS) k_batch(const BatchItemDev *__r
             const BatchItemDev &it = items[find_item(items, n_items, (int64_t)t)];
             const int64_t u0 = ((int64_t)t - it.tile_begin) * tile, u1 = min(u0 + tile, it.units);
             if (SCHED == FE_SCHED_WARP_PER_ROW) {
-                for (int64_t v = u0; v < u1; ++v) {
-                    if (it.map_bytes == 1) gather_row_any<uint8_t, CRAC>(&it, it.shape, v, acc, accumulate, lane);
-                    else gather_row_any<uint16_t, CRAC>(&it, it.shape, v, acc, accumulate, lane);
+                if (it.shape == SH_4_1 || it.shape == SH_8_1) {
+                    // one-DOF rows: several per warp (gather_small.cuh)
+                    if (it.shape == SH_4_1) {
+                        if (it.map_bytes == 1) gather_tile_small<4, uint8_t, CRAC>(&it, u0, u1, acc, cap, accumulate, lane);
+                        else gather_tile_small<4, uint16_t, CRAC>(&it, u0, u1, acc, cap, accumulate, lane);
+                    } else {
+                        if (it.map_bytes == 1) gather_tile_small<8, uint8_t, CRAC>(&it, u0, u1, acc, cap, accumulate, lane);
+                        else gather_tile_small<8, uint16_t, CRAC>(&it, u0, u1, acc, cap, accumulate, lane);
+                    }
+                } else if (it.shape == SH_8_3 || it.shape == SH_10_3) {
+                    if (it.shape == SH_8_3) {
+                        if (it.map_bytes == 1) gather_tile_node<8, 3, uint8_t, CRAC>(&it, u0, u1, acc, accumulate, lane);
+                        else gather_tile_node<8, 3, uint16_t, CRAC>(&it, u0, u1, acc, accumulate, lane);
+                    } else {
+                        if (it.map_bytes == 1) gather_tile_node<10, 3, uint8_t, CRAC>(&it, u0, u1, acc, accumulate, lane);
+                        else gather_tile_node<10, 3, uint16_t, CRAC>(&it, u0, u1, acc, accumulate, lane);
+                    }
+                } else {
+                    for (int64_t v = u0; v < u1; ++v) {
+                        if (it.map_bytes == 1) gather_row_any<uint8_t, CRAC>(&it, it.shape, v, acc, accumulate, lane);
+                        else gather_row_any<uint16_t, CRAC>(&it, it.shape, v, acc, accumulate, lane);
+                    }
                 }
             } else if (SCHED == FE_SCHED_WARP_PER_ELEMENT) {
                 for (int64_t e = u0; e < u1; ++e) {
@@ -456,6 +507,9 @@ int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
         if (d.staged) plan.stage = std::max(plan.stage, (nn + 1) & ~1);
         plan.total_tiles += (d.units + tile - 1) / tile;
         plan.cap = std::max(plan.cap, p->B * p->max_row_len);
+        // one-DOF rows of 4 or 8 nodes: SmallRows<>::RPW accumulators per warp
+        if (d.shape == SH_4_1) plan.cap = std::max(plan.cap, SmallRows<4>::RPW * p->max_row_len);
+        if (d.shape == SH_8_1) plan.cap = std::max(plan.cap, SmallRows<8>::RPW * p->max_row_len);
     }
     return FE_OK;
 }

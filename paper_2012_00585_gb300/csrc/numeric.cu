@@ -21,6 +21,7 @@
 #include "assemble_body.cuh"
 #include "internal.cuh"
 #include "tma.cuh"
+#include "gather_small.cuh"
 
 namespace {
 
@@ -265,6 +266,22 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
         for (int k = lane; k < total; k += 32) values[rb + k] = acc[k];
         __syncwarp();
     }
+}
+
+// One-DOF elements with at most 16 local nodes: 32 / G consecutive node rows
+// per warp, G lanes per row (gather_small.cuh).
+template <int NLN, typename MT, bool CRAC, int U>
+__global__ void __launch_bounds__(256) k_gather_small(const double *__restrict__ K, int64_t n_nodes, Geo g,
+                                                      const MT *__restrict__ map, const MT *__restrict__ mapc,
+                                                      int cap, int accumulate, double *values)
+{
+    constexpr int RPW = SmallRows<NLN>::RPW;
+    extern __shared__ double acc_all[];
+    const int lane = threadIdx.x & 31;
+    double *accw = acc_all + (size_t)(threadIdx.x >> 5) * RPW * cap;
+    const int64_t W = fe_warps();
+    for (int64_t v0 = fe_warp_id() * RPW; v0 < n_nodes; v0 += W * RPW)
+        gather_rows_small<NLN, MT, CRAC, U>(K, v0, 1, n_nodes, g, map, mapc, accw, cap, accumulate, values, lane);
 }
 
 // Two node rows per warp (nodes 2p and 2p+1, each with its own accumulator):
@@ -1237,6 +1254,23 @@ int launch_gather(const fe_pattern *p, const double *K, double *values, int accu
     int W = ctx->knob[FE_KNOB_GATHER_WARPS];
     if constexpr (NLN > 0) {
         constexpr int CHK = BB * NLN * BB;
+        if constexpr (BB == 1 && NLN <= 16) {
+            if (kind == 0 || kind == 6) {  // the default for these shapes
+                constexpr int RPW = SmallRows<NLN>::RPW;
+                const int Ws = (W > 0 && W <= 8) ? W : 4;
+                const size_t ssm = (size_t)Ws * RPW * cap * 8;
+                if (ssm <= 200 * 1024) {
+                    FE_TRY(configure_smem(k_gather_small<NLN, MT, CRAC, 4>, ssm));
+                    const int sgrid = fe_grid_resident(k_gather_small<NLN, MT, CRAC, 4>,
+                                                       (p->n_nodes + RPW - 1) / RPW * 32, Ws * 32, sms, ssm);
+                    k_gather_small<NLN, MT, CRAC, 4><<<sgrid, Ws * 32, ssm, s>>>(
+                        K, p->n_nodes, g, (const MT *)p->map_csr, (const MT *)p->map_crac, cap, accumulate, values);
+                    fe_note_launch();
+                    FE_CUDA(cudaGetLastError());
+                    return FE_OK;
+                }
+            }
+        }
         if (kind == 5) {
             constexpr int UP = 2;
             int Wp = (W > 0 && W <= 8) ? W : 2;

@@ -362,7 +362,7 @@ def test_c3_full_size_sampled_rows(ctx):
     g.free()
 
 
-@pytest.mark.parametrize("gkind", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("gkind", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("akind", [1, 2])
 def test_every_kernel_variant(ctx, gkind, akind):
     """Each schedule knob value gives the same results: deterministic
@@ -379,6 +379,8 @@ def test_every_kernel_variant(ctx, gkind, akind):
             (*wl.tet_p2_kuhn(3, d=3, seed=8), None),
             (*wl.hex_q1_grid(6, 1), None),
             (*wl.quad_q1_grid(9, 2), None),
+            (*wl.quad_q1_grid(11, 1), None),
+            (*wl.quad_qp_grid(3, 3, 1), None),
         ]:
             K = wl.random_matrices(D.shape[0], D.shape[1], seed=gkind * 10 + akind)
             g = gu.GpuAssembly(ctx, D, n_dofs)
