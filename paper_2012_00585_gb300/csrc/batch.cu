@@ -8,8 +8,11 @@
 // (assemble_body.cuh), so a batched result equals the per-mesh result: bit
 // for bit in FE_DETERMINISTIC.
 //
-// Schedules: FE_ATOMIC  -- warp per element, thread per entry, block per element
-//            FE_DETERMINISTIC -- warp per node row
+// Schedules: FE_ATOMIC  -- warp per element (K from global memory, or staged
+//                          by bulk copies: the default), thread per entry,
+//                          block per element
+//            FE_DETERMINISTIC -- warp per node row (one-DOF rows of 4 or 8
+//                          nodes: several rows per warp)
 // An autotuner times the candidates on the caller's batch and caches the
 // fastest per batch signature in the context; a batch can also be captured
 // once into a CUDA graph and replayed.
@@ -188,15 +191,6 @@ __device__ __noinline__ void atomic_elem_generic_call(const BatchItemDev *__rest
                                      it->values, base_s, k_s, off_s, lane);
 }
 
-template <int NLN, int BB, typename MT, bool CRAC>
-__device__ __noinline__ void gather_row_call(const BatchItemDev *__restrict__ it, int64_t v, double *acc,
-                                             int accumulate, int lane)
-{
-    const Geo g = it->g;
-    gather_row<NLN, BB, MT, CRAC, 4>(it->K, v, g, (const MT *)it->map, (const MT *)it->mapc, acc, accumulate,
-                                     it->values, lane);
-}
-
 // The node rows [u0, u1) of a one-DOF item, RPW at a time with G lanes per
 // row (one call per tile).  The warp's accumulator region (cap doubles, cap
 // >= RPW x the item's longest row by the plan) is split into RPW per-row
@@ -251,16 +245,10 @@ __device__ __forceinline__ void atomic_elem_any(const BatchItemDev *it, int shap
 }
 
 template <typename MT, bool CRAC>
-__device__ __forceinline__ void gather_row_any(const BatchItemDev *it, int shape, int64_t v, double *acc,
-                                               int accumulate, int lane)
+__device__ __forceinline__ void gather_row_any(const BatchItemDev *it, int64_t v, double *acc, int accumulate, int lane)
 {
-    switch (shape) {
-    case SH_4_1: gather_row_call<4, 1, MT, CRAC>(it, v, acc, accumulate, lane); break;
-    case SH_8_1: gather_row_call<8, 1, MT, CRAC>(it, v, acc, accumulate, lane); break;
-    case SH_8_3: gather_row_call<8, 3, MT, CRAC>(it, v, acc, accumulate, lane); break;
-    case SH_10_3: gather_row_call<10, 3, MT, CRAC>(it, v, acc, accumulate, lane); break;
-    default: gather_row_generic_call<MT, CRAC>(it, v, acc, accumulate, lane);
-    }
+    // shapes without a specialised per-tile path
+    gather_row_generic_call<MT, CRAC>(it, v, acc, accumulate, lane);
 }
 
 // Slot of entry q of element e for any shape (thread-per-entry schedule).
@@ -430,8 +418,8 @@ __global__ void __launch_bounds__(SCHED_THREADS) k_batch(const BatchItemDev *__r
                     }
                 } else {
                     for (int64_t v = u0; v < u1; ++v) {
-                        if (it.map_bytes == 1) gather_row_any<uint8_t, CRAC>(&it, it.shape, v, acc, accumulate, lane);
-                        else gather_row_any<uint16_t, CRAC>(&it, it.shape, v, acc, accumulate, lane);
+                        if (it.map_bytes == 1) gather_row_any<uint8_t, CRAC>(&it, v, acc, accumulate, lane);
+                        else gather_row_any<uint16_t, CRAC>(&it, v, acc, accumulate, lane);
                     }
                 }
             } else if (SCHED == FE_SCHED_WARP_PER_ELEMENT) {

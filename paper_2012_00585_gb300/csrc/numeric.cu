@@ -18,6 +18,14 @@
 // each element (the compressed DOF array of §2.1): one map entry per
 // (element, row block, run), the column's offset inside its run, and the
 // row start read from the CRAC pairs (Listing 5's contiguous slices).
+//
+// Kernels (defaults first; the others are schedule knobs, every one
+// parity-tested): atomic -- k_atomic_tma (K_e staged by a bulk copy),
+// k_atomic_elem, k_atomic_generic; deterministic -- k_gather_node (3-DOF
+// and other specialised shapes), k_gather_small (one-DOF rows of 4 or 8
+// nodes, several rows per warp), k_gather_generic (any shape), and the
+// variants k_gather_async, k_gather_pipe, k_gather_bulk, k_gather_pair.
+// FE_COLOURED and FE_ROWLOCK are in colour.cu and rowlock.cu.
 #include "assemble_body.cuh"
 #include "internal.cuh"
 #include "tma.cuh"
