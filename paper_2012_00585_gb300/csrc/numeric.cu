@@ -146,6 +146,27 @@ __global__ void __launch_bounds__(256) k_atomic_generic(const double *__restrict
 // One warp per block row; the B rows of the node are contiguous in values.
 // Incidences are taken U at a time: their K slices and slots are loaded
 // first, then added strictly in ascending element order.
+//
+// Packed slices (CRAC rows, gather_packs): when a slice is not a multiple of
+// 32 entries (3 x 24 for trilinear hexes), the U slices are laid end to end
+// over the lanes -- slot s = 32 i + lane holds entry s % CHK of incidence
+// s / CHK -- so U x 72 entries take ceil(72 U / 32) load, add and store
+// instructions instead of 3 U (9 instead of 12 for U = 4).  One instruction
+// then holds the tail of one slice and the head of the next; the two never
+// meet in an accumulator slot: entries of one slot share their block row, so
+// in the concatenation they lie at least CHK - NLOC + 1 >= 32 slots apart,
+// i.e. in different instructions, the earlier incidence first.  The per-slot
+// order is unchanged and the result bit-identical.  Measured on the 64^3
+// elasticity mesh: CRAC rows 615 -> 582 us (the unpacked instance spilled);
+// CSR rows 413 -> 447 us (the extra shuffles and index arithmetic cost more
+// than the saved lanes), so CSR rows stay unpacked.
+template <int NLN, int BB, bool CRAC, int U>
+constexpr bool gather_packs()
+{
+    constexpr int NLOC = NLN * BB, CHK = BB * NLOC;
+    return CRAC && NLN > 0 && (BB - 1) * NLOC + 1 >= 32 && (U * CHK + 31) / 32 < U * ((CHK + 31) / 32) && U <= 32;
+}
+
 template <int NLN, int BB, typename MT, bool CRAC, int U>
 __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_gather_node(const double *__restrict__ K, int64_t n_nodes, Geo g,
                                                      const MT *__restrict__ map, const MT *__restrict__ mapc, int cap,
@@ -155,6 +176,8 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
     constexpr int NN = NLOC * NLOC;
     constexpr int CHK = BB * NLOC;  // doubles of one incidence (B contiguous K rows)
     constexpr int IT = (CHK + 31) / 32;
+    constexpr int ITP = (U * CHK + 31) / 32;  // slot rows of U packed slices
+    constexpr bool PACK = gather_packs<NLN, BB, CRAC, U>();
     extern __shared__ double acc_all[];
     const int lane = threadIdx.x & 31;
     double *acc = acc_all + (size_t)(threadIdx.x >> 5) * cap;
@@ -220,55 +243,124 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
         for (int k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
         __syncwarp();
         for (int64_t s0 = a; s0 < b; s0 += U) {
-            double kv[U][IT];
-            int rel[U][IT];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool have = s0 + u < b;
-                const uint32_t t = have ? g.adj[s0 + u] : 0u;
-                const uint32_t e = t / NLN;
-                const int kr = (int)(t - e * NLN);
-                const double *chunk = K + (int64_t)e * NN + (int64_t)kr * CHK;
-                int64_t rp = 0;
-                int nr = 0;
-                uint32_t m = 0;
-                if (CRAC && have) {
-                    if (g.uniform_R) {
-                        nr = g.uniform_R;
-                        rp = (int64_t)e * nr;
-                    } else {
-                        rp = g.run_ptr[e];
-                        nr = (int)(g.run_ptr[e + 1] - rp);
-                        m = g.run_mask[e];
+            if constexpr (PACK) {
+                // lane u < nu holds incidence s0 + u; slot 32 i + lane reads it
+                // by shuffle (its slice starts at K + t * CHK: e NN + kr CHK)
+                const int nu = (int)(b - s0 < U ? b - s0 : U);
+                uint32_t t_l = 0, m_l = 0;
+                int64_t rp_l = 0;
+                int nr_l = 0;
+                if (lane < nu) {
+                    t_l = g.adj[s0 + lane];
+                    if (CRAC && !g.uniform_R) {
+                        const uint32_t e = t_l / NLN;
+                        rp_l = g.run_ptr[e];
+                        nr_l = (int)(g.run_ptr[e + 1] - rp_l);
+                        m_l = g.run_mask[e];
                     }
                 }
+                double kv[ITP];
+                int rel[ITP];
+                // the lane id read afresh each group: the slot constants below are
+                // recomputed instead of held in registers across the row loop
+                int ln;
+                asm volatile("mov.u32 %0, %%laneid;" : "=r"(ln));
 #pragma unroll
-                for (int j = 0; j < IT; ++j) {
-                    const int q = lane + 32 * j;
-                    kv[u][j] = 0.0;
-                    rel[u][j] = 0;
-                    if (have && q < CHK) {
-                        kv[u][j] = __ldcs(chunk + q);
-                        const int kc = c_[j] / BB;
+                for (int i = 0; i < ITP; ++i) {
+                    const int lo = (32 * i) / CHK;  // slot row i spans incidences lo and lo + 1
+                    const int sl = ln + 32 * i;
+                    const int u = lo + (sl >= (lo + 1) * CHK ? 1 : 0);
+                    const int q = sl - u * CHK;
+                    const uint32_t t = __shfl_sync(0xffffffffu, t_l, u & 31);
+                    int64_t rp = 0;
+                    int nr = 0;
+                    uint32_t m = 0;
+                    if (CRAC && !g.uniform_R) {
+                        rp = __shfl_sync(0xffffffffu, rp_l, u & 31);
+                        nr = __shfl_sync(0xffffffffu, nr_l, u & 31);
+                        m = __shfl_sync(0xffffffffu, m_l, u & 31);
+                    }
+                    kv[i] = 0.0;
+                    rel[i] = -1;
+                    if (u < nu) {
+                        const int jr = q / NLOC, c = q - jr * NLOC;
+                        const int kc = c / BB, cb = c - kc * BB;
+                        kv[i] = __ldcs(K + (int64_t)t * CHK + q);
                         int pos;
                         if (!CRAC) {
                             pos = (int)map[(int64_t)t * NLN + kc];
                         } else {
-                            int k = ku[j], off = offu[j];
-                            if (!g.uniform_R) run_of(m, kc, k, off);
+                            const uint32_t e = t / NLN;
+                            const int kr = (int)(t - e * NLN);
+                            int k, off;
+                            if (g.uniform_R) {
+                                nr = g.uniform_R;
+                                rp = (int64_t)e * nr;
+                                run_of(g.run_mask[0], kc, k, off);
+                            } else {
+                                run_of(m, kc, k, off);
+                            }
                             pos = (int)mapc[rp * NLN + (int64_t)kr * nr + k] + off;
                         }
-                        rel[u][j] = jr_[j] * (int)RL + BB * pos + c_[j] % BB;
+                        rel[i] = jr * (int)RL + BB * pos + cb;
                     }
                 }
-            }
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
+                for (int i = 0; i < ITP; ++i) {
+                    if (rel[i] >= 0 && FE_IN_BOUNDS(rel[i], total, g.status)) acc[rel[i]] += kv[i];
+                    __syncwarp();
+                }
+            } else {
+                double kv[U][IT];
+                int rel[U][IT];
 #pragma unroll
-                for (int j = 0; j < IT; ++j)
-                    if (s0 + u < b && lane + 32 * j < CHK && FE_IN_BOUNDS(rel[u][j], total, g.status))
-                        acc[rel[u][j]] += kv[u][j];
-                __syncwarp();
+                for (int u = 0; u < U; ++u) {
+                    const bool have = s0 + u < b;
+                    const uint32_t t = have ? g.adj[s0 + u] : 0u;
+                    const uint32_t e = t / NLN;
+                    const int kr = (int)(t - e * NLN);
+                    const double *chunk = K + (int64_t)e * NN + (int64_t)kr * CHK;
+                    int64_t rp = 0;
+                    int nr = 0;
+                    uint32_t m = 0;
+                    if (CRAC && have) {
+                        if (g.uniform_R) {
+                            nr = g.uniform_R;
+                            rp = (int64_t)e * nr;
+                        } else {
+                            rp = g.run_ptr[e];
+                            nr = (int)(g.run_ptr[e + 1] - rp);
+                            m = g.run_mask[e];
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < IT; ++j) {
+                        const int q = lane + 32 * j;
+                        kv[u][j] = 0.0;
+                        rel[u][j] = 0;
+                        if (have && q < CHK) {
+                            kv[u][j] = __ldcs(chunk + q);
+                            const int kc = c_[j] / BB;
+                            int pos;
+                            if (!CRAC) {
+                                pos = (int)map[(int64_t)t * NLN + kc];
+                            } else {
+                                int k = ku[j], off = offu[j];
+                                if (!g.uniform_R) run_of(m, kc, k, off);
+                                pos = (int)mapc[rp * NLN + (int64_t)kr * nr + k] + off;
+                            }
+                            rel[u][j] = jr_[j] * (int)RL + BB * pos + c_[j] % BB;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+#pragma unroll
+                    for (int j = 0; j < IT; ++j)
+                        if (s0 + u < b && lane + 32 * j < CHK && FE_IN_BOUNDS(rel[u][j], total, g.status))
+                            acc[rel[u][j]] += kv[u][j];
+                    __syncwarp();
+                }
             }
         }
         for (int k = lane; k < total; k += 32) values[rb + k] = acc[k];
@@ -1348,7 +1440,12 @@ int launch_gather(const fe_pattern *p, const double *K, double *values, int accu
             }
         }
     }
-    if (W <= 0) W = 2;  // fastest in sweeps of 1..8 warps per block on the 64^3 elasticity mesh
+    // fastest in sweeps of 1..8 warps per block on the 64^3 elasticity mesh:
+    // 2 for the unpacked rows, 4 for packed CRAC rows
+    if constexpr (NLN > 0) {
+        if (W <= 0) W = gather_packs<NLN, BB, CRAC, 4>() ? 4 : 2;
+    }
+    if (W <= 0) W = 2;
     while (W > 1 && (size_t)W * cap * 8 > 64 * 1024) W >>= 1;
     const size_t smem = (size_t)W * cap * 8;
     if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;

@@ -171,3 +171,47 @@ def test_batch_staged_schedule_with_unaligned_matrices(ctx, batch, fmt):
     feasm.fe_assemble_batch(ctx, items, fmt, feasm.FE_ATOMIC, 0, (feasm.FE_SCHED_WARP_PER_ELEMENT_TMA, 8))
     _check(batch, feasm.FE_ATOMIC)
     assert feasm.fe_device_status(ctx) == 0
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_full_size_sampled(ctx, mode):
+    """The batched workload at full size in the bench's launch configuration
+    (256 hex meshes, n ~ logU[8, 48], half Q1 Laplace and half Q1 elasticity,
+    autotuned schedule, one CUDA-graph launch): sampled meshes -- the two
+    largest and the two smallest of each kind -- against the oracle."""
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    sizes = wl.batched_mesh_sizes(256, seed=0)
+    rows = []
+    for k, (n, d) in enumerate(sizes):
+        D, n_dofs = wl.hex_q1_grid(n, d)
+        Kr = wl.laplace_q1_hex(1.0 / n) if d == 1 else wl.elasticity_q1_hex(1.0 / n)
+        Kd = wl.scaled_matrices(Kr, D.shape[0], seed=k, device="cuda")
+        pat = feasm.Pattern(ctx, torch.from_numpy(D).cuda(), n_dofs)
+        v = torch.empty(pat.info["nnz"], dtype=torch.float64, device="cuda")
+        rows.append((k, n, d, D, n_dofs, Kd, pat, v))
+    items = [(r[6], r[5], r[7]) for r in rows]
+    feasm.fe_batch_autotune(ctx, items, feasm.FE_FORMAT_CSR, mode)
+    g = feasm.fe_batch_graph_create(ctx, items, feasm.FE_FORMAT_CSR, mode)
+    for _, _, _, _, _, _, _, v in rows:
+        v.fill_(float("nan"))
+    feasm.fe_batch_graph_launch(g)
+    torch.cuda.synchronize()
+    assert feasm.fe_device_status(ctx) == 0
+    picks = []
+    for d in (1, 3):
+        kind = sorted((r for r in rows if r[2] == d), key=lambda r: r[1])
+        picks += kind[:2] + kind[-2:]
+    for k, n, d, D, n_dofs, Kd, pat, v in picks:
+        K = Kd.cpu().numpy()
+        rp, ci = oracle.csr_pattern(D, n_dofs)
+        exp = oracle.assemble_csr(D, K, rp, ci)
+        got = v.cpu().numpy()
+        if mode == feasm.FE_DETERMINISTIC:
+            assert np.array_equal(got.view(np.uint64), exp.view(np.uint64)), (k, n, d)
+        else:
+            gu.assert_within_row_tol(rp, got, exp, gu.row_tolerance(rp, exp, gu.contribution_abs_row_sums(D, K, n_dofs)))
+    feasm.fe_batch_graph_destroy(g)
+    for r in rows:
+        r[6].free()
