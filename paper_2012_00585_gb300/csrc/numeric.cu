@@ -22,8 +22,8 @@
 // Kernels (defaults first; the others are schedule knobs, every one
 // parity-tested): atomic -- k_atomic_tma (K_e staged by a bulk copy),
 // k_atomic_elem, k_atomic_generic; deterministic -- k_gather_node (3-DOF
-// and other specialised shapes), k_gather_small (one-DOF rows of 4 or 8
-// nodes, several rows per warp), k_gather_generic (any shape), and the
+// and other specialised shapes), k_gather_small (slices of at most 16
+// entries, several rows per warp), k_gather_generic (any shape), and the
 // variants k_gather_async, k_gather_pipe, k_gather_bulk, k_gather_pair.
 // FE_COLOURED and FE_ROWLOCK are in colour.cu and rowlock.cu.
 #include "assemble_body.cuh"
@@ -178,6 +178,8 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
     constexpr int IT = (CHK + 31) / 32;
     constexpr int ITP = (U * CHK + 31) / 32;  // slot rows of U packed slices
     constexpr bool PACK = gather_packs<NLN, BB, CRAC, U>();
+    // run-start masks are read as one 32-bit word per element (run_of)
+    static_assert(NLN >= 1 && NLN <= 32, "k_gather_node: at most 32 nodes per element");
     extern __shared__ double acc_all[];
     const int lane = threadIdx.x & 31;
     double *acc = acc_all + (size_t)(threadIdx.x >> 5) * cap;
@@ -368,20 +370,21 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
     }
 }
 
-// One-DOF elements with at most 16 local nodes: 32 / G consecutive node rows
-// per warp, G lanes per row (gather_small.cuh).
-template <int NLN, typename MT, bool CRAC, int U>
+// Node rows whose incidence slices hold at most 16 entries (one-DOF elements
+// of up to 16 nodes, 4-node elements with 2 DOFs per node): 32 / G
+// consecutive node rows per warp, G lanes per row (gather_small.cuh).
+template <int NLN, typename MT, bool CRAC, int U, int BB = 1>
 __global__ void __launch_bounds__(256) k_gather_small(const double *__restrict__ K, int64_t n_nodes, Geo g,
                                                       const MT *__restrict__ map, const MT *__restrict__ mapc,
                                                       int cap, int accumulate, double *values)
 {
-    constexpr int RPW = SmallRows<NLN>::RPW;
+    constexpr int RPW = SmallRows<NLN, BB>::RPW;
     extern __shared__ double acc_all[];
     const int lane = threadIdx.x & 31;
     double *accw = acc_all + (size_t)(threadIdx.x >> 5) * RPW * cap;
     const int64_t W = fe_warps();
     for (int64_t v0 = fe_warp_id() * RPW; v0 < n_nodes; v0 += W * RPW)
-        gather_rows_small<NLN, MT, CRAC, U>(K, v0, 1, n_nodes, g, map, mapc, accw, cap, accumulate, values, lane);
+        gather_rows_small<NLN, MT, CRAC, U, BB>(K, v0, 1, n_nodes, g, map, mapc, accw, cap, accumulate, values, lane);
 }
 
 // Two node rows per warp (nodes 2p and 2p+1, each with its own accumulator):
@@ -1343,7 +1346,16 @@ int launch_atomic(const fe_pattern *p, const double *K, double *values, cudaStre
     return FE_OK;
 }
 
-template <int NLN, int BB, typename MT, bool CRAC>
+// lean instances take incidences two at a time above this slice size
+// (measured on the Q1 d-benchmark, 192^2: d = 5..8 CSR 68 / 77 / 109 / 138
+// -> 56 / 66 / 95 / 101 us, CRAC d = 6..8 -> 83 / 130 / 130 us, d <= 4
+// unchanged)
+constexpr int LEAN_U2_CHK = 64;
+
+// VARIANTS = false: only the default kernels of the shape are instantiated
+// (no schedule-knob variants, no U = 8), for shapes added to keep their rows
+// off the generic kernel at little compile-time cost.
+template <int NLN, int BB, typename MT, bool CRAC, bool VARIANTS = true>
 int launch_gather(const fe_pattern *p, const double *K, double *values, int accumulate, cudaStream_t s)
 {
     const Geo g = geo_of(p);
@@ -1354,16 +1366,16 @@ int launch_gather(const fe_pattern *p, const double *K, double *values, int accu
     int W = ctx->knob[FE_KNOB_GATHER_WARPS];
     if constexpr (NLN > 0) {
         constexpr int CHK = BB * NLN * BB;
-        if constexpr (BB == 1 && NLN <= 16) {
+        if constexpr (CHK <= 16) {
             if (kind == 0 || kind == 6) {  // the default for these shapes
-                constexpr int RPW = SmallRows<NLN>::RPW;
+                constexpr int RPW = SmallRows<NLN, BB>::RPW;
                 const int Ws = (W > 0 && W <= 8) ? W : 4;
                 const size_t ssm = (size_t)Ws * RPW * cap * 8;
                 if (ssm <= 200 * 1024) {
-                    FE_TRY(configure_smem(k_gather_small<NLN, MT, CRAC, 4>, ssm));
-                    const int sgrid = fe_grid_resident(k_gather_small<NLN, MT, CRAC, 4>,
+                    FE_TRY(configure_smem(k_gather_small<NLN, MT, CRAC, 4, BB>, ssm));
+                    const int sgrid = fe_grid_resident(k_gather_small<NLN, MT, CRAC, 4, BB>,
                                                        (p->n_nodes + RPW - 1) / RPW * 32, Ws * 32, sms, ssm);
-                    k_gather_small<NLN, MT, CRAC, 4><<<sgrid, Ws * 32, ssm, s>>>(
+                    k_gather_small<NLN, MT, CRAC, 4, BB><<<sgrid, Ws * 32, ssm, s>>>(
                         K, p->n_nodes, g, (const MT *)p->map_csr, (const MT *)p->map_crac, cap, accumulate, values);
                     fe_note_launch();
                     FE_CUDA(cudaGetLastError());
@@ -1371,7 +1383,7 @@ int launch_gather(const fe_pattern *p, const double *K, double *values, int accu
                 }
             }
         }
-        if (kind == 5) {
+        if constexpr (VARIANTS) if (kind == 5) {
             constexpr int UP = 2;
             int Wp = (W > 0 && W <= 8) ? W : 2;
             while (Wp > 1 && (size_t)Wp * 2 * cap * 8 > 64 * 1024) Wp >>= 1;
@@ -1387,7 +1399,7 @@ int launch_gather(const fe_pattern *p, const double *K, double *values, int accu
                 return FE_OK;
             }
         }
-        if (kind == 4 && tma_ok(p, K, CHK)) {
+        if constexpr (VARIANTS) if (kind == 4 && tma_ok(p, K, CHK)) {
             constexpr int UB = 8;
             int S = ctx->knob[FE_KNOB_GATHER_STAGES] > 0 ? ctx->knob[FE_KNOB_GATHER_STAGES] : 4;
             int Wb = (W > 0 && W <= 4) ? W : 4;  // launch bound: 128 threads
@@ -1410,7 +1422,7 @@ int launch_gather(const fe_pattern *p, const double *K, double *values, int accu
                 return FE_OK;
             }
         }
-        if (kind == 3 && tma_ok(p, K, CHK)) {
+        if constexpr (VARIANTS) if (kind == 3 && tma_ok(p, K, CHK)) {
             if (W <= 0 || W > 4) W = 4;
             const size_t psmem = (size_t)W * pipe_warp_bytes(CHK, cap);
             if (psmem <= 200 * 1024) {
@@ -1425,7 +1437,7 @@ int launch_gather(const fe_pattern *p, const double *K, double *values, int accu
             }
             W = ctx->knob[FE_KNOB_GATHER_WARPS];
         }
-        if (kind == 2 && tma_ok(p, K, CHK)) {
+        if constexpr (VARIANTS) if (kind == 2 && tma_ok(p, K, CHK)) {
             if (W <= 0 || W > 4) W = 4;  // launch bound of the staged kernel: 128 threads
             const size_t tsmem = (size_t)W * gather_warp_bytes(CHK, cap);
             if (tsmem <= 200 * 1024) {
@@ -1451,13 +1463,18 @@ int launch_gather(const fe_pattern *p, const double *K, double *values, int accu
     if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
     const int grid = fe_grid_for(p->n_nodes * 32, W * 32, sms, std::max(1, 64 / W));
     if constexpr (NLN > 0) {
-        if (ctx->knob[FE_KNOB_GATHER_BATCH] == 8) {
-            FE_TRY(configure_smem(k_gather_node<NLN, BB, MT, CRAC, 8>, smem));
-            k_gather_node<NLN, BB, MT, CRAC, 8><<<grid, W * 32, smem, s>>>(
-                K, p->n_nodes, g, (const MT *)p->map_csr, (const MT *)p->map_crac, cap, accumulate, values);
+        bool u8 = false;
+        if constexpr (VARIANTS) u8 = ctx->knob[FE_KNOB_GATHER_BATCH] == 8;
+        if (u8) {
+            if constexpr (VARIANTS) {
+                FE_TRY(configure_smem(k_gather_node<NLN, BB, MT, CRAC, 8>, smem));
+                k_gather_node<NLN, BB, MT, CRAC, 8><<<grid, W * 32, smem, s>>>(
+                    K, p->n_nodes, g, (const MT *)p->map_csr, (const MT *)p->map_crac, cap, accumulate, values);
+            }
         } else {
-            FE_TRY(configure_smem(k_gather_node<NLN, BB, MT, CRAC, 4>, smem));
-            k_gather_node<NLN, BB, MT, CRAC, 4><<<grid, W * 32, smem, s>>>(
+            constexpr int UL = (!VARIANTS && BB * NLN * BB > LEAN_U2_CHK) ? 2 : 4;
+            FE_TRY(configure_smem(k_gather_node<NLN, BB, MT, CRAC, UL>, smem));
+            k_gather_node<NLN, BB, MT, CRAC, UL><<<grid, W * 32, smem, s>>>(
                 K, p->n_nodes, g, (const MT *)p->map_csr, (const MT *)p->map_crac, cap, accumulate, values);
         }
     } else {
@@ -1507,6 +1524,21 @@ int dispatch(const fe_pattern *p, const double *K, double *values, int mode, int
     if (nln == 8 && B == 1) return launch_gather<8, 1, MT, CRAC>(p, K, values, accumulate, s);
     if (nln == 8 && B == 3) return launch_gather<8, 3, MT, CRAC>(p, K, values, accumulate, s);
     if (nln == 10 && B == 3) return launch_gather<10, 3, MT, CRAC>(p, K, values, accumulate, s);
+    if constexpr (std::is_same<MT, uint8_t>::value) {
+        // Q2..Q4 scalar quads and Q1 quads with 2..8 DOFs per node: the
+        // several-rows-per-warp and batched-incidence row kernels instead of
+        // the generic one, which loads one incidence at a time
+        if (nln == 9 && B == 1) return launch_gather<9, 1, MT, CRAC, false>(p, K, values, accumulate, s);
+        if (nln == 16 && B == 1) return launch_gather<16, 1, MT, CRAC, false>(p, K, values, accumulate, s);
+        if (nln == 25 && B == 1) return launch_gather<25, 1, MT, CRAC, false>(p, K, values, accumulate, s);
+        if (nln == 4 && B == 2) return launch_gather<4, 2, MT, CRAC, false>(p, K, values, accumulate, s);
+        if (nln == 4 && B == 3) return launch_gather<4, 3, MT, CRAC, false>(p, K, values, accumulate, s);
+        if (nln == 4 && B == 4) return launch_gather<4, 4, MT, CRAC, false>(p, K, values, accumulate, s);
+        if (nln == 4 && B == 5) return launch_gather<4, 5, MT, CRAC, false>(p, K, values, accumulate, s);
+        if (nln == 4 && B == 6) return launch_gather<4, 6, MT, CRAC, false>(p, K, values, accumulate, s);
+        if (nln == 4 && B == 7) return launch_gather<4, 7, MT, CRAC, false>(p, K, values, accumulate, s);
+        if (nln == 4 && B == 8) return launch_gather<4, 8, MT, CRAC, false>(p, K, values, accumulate, s);
+    }
     return launch_gather<0, 0, MT, CRAC>(p, K, values, accumulate, s);
 }
 

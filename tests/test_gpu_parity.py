@@ -182,8 +182,9 @@ def test_all_ones_atomic_is_exact(ctx):
 @pytest.mark.parametrize("case", ["qp3_d1", "qp2_d4", "hex_d2", "q8_rows_over_256", "d20_quad",
                                   "scattered", "single", "unused_dofs"])
 def test_generic_sizes_and_layouts(ctx, case):
-    """Element sizes without a specialised kernel (9, 36, 16, 81, 80, ...),
-    rows longer than 256 (16-bit slot maps), scattered DOFs, empty rows."""
+    """Element sizes and layouts beyond the specialised shapes (36, 16 with
+    2 DOFs per node, 81, 80, ...), rows longer than 256 (16-bit slot maps),
+    scattered DOFs, empty rows."""
     rng = np.random.default_rng(0)
     if case == "qp3_d1":
         D, n_dofs = wl.quad_qp_grid(5, 3, 1)          # n_loc 16
@@ -207,6 +208,22 @@ def test_generic_sizes_and_layouts(ctx, case):
     g = gu.GpuAssembly(ctx, D, n_dofs)
     if case == "q8_rows_over_256":
         assert g.pattern.info["map_bytes"] == 2
+    pat = _check_pattern(g, D, n_dofs)
+    _run_all_modes(g, D, K, n_dofs, *pat)
+    g.free()
+
+
+@pytest.mark.parametrize("p,d", [(2, 1), (3, 1), (4, 1), (1, 2), (1, 3), (1, 4), (1, 5), (1, 6), (1, 7), (1, 8)])
+def test_quad_shapes_permuted_nodes(ctx, p, d):
+    """The quad shapes with their own row kernels (Q2..Q4 scalar, Q1 with
+    2..8 DOFs per node) on a mesh whose node numbers are shuffled: irregular
+    rows and CRAC runs that differ from element to element."""
+    D, n_dofs = wl.quad_qp_grid(6, p, d)
+    perm = np.random.default_rng(100 * p + d).permutation(n_dofs // d)
+    D = (perm[D // d] * d + D % d).astype(np.int32)
+    K = wl.random_matrices(D.shape[0], D.shape[1], seed=p + 10 * d)
+    g = gu.GpuAssembly(ctx, D, n_dofs)
+    assert g.pattern.adjacency()[0] == d
     pat = _check_pattern(g, D, n_dofs)
     _run_all_modes(g, D, K, n_dofs, *pat)
     g.free()
