@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
     constexpr int IT = (CHK + 31) / 32;
     constexpr int ITP = (U * CHK + 31) / 32;  // slot rows of U packed slices
     constexpr bool PACK = gather_packs<NLN, BB, CRAC, U>();
-    // run-start masks are read as one 32-bit word per element (run_of)
-    static_assert(NLN >= 1 && NLN <= 32, "k_gather_node: at most 32 nodes per element");
+    // CRAC rows read the run-start mask as one 32-bit word per element (run_of)
+    static_assert(NLN >= 1 && (!CRAC || NLN <= 32), "k_gather_node: CRAC rows of at most 32 nodes per element");
     extern __shared__ double acc_all[];
     const int lane = threadIdx.x & 31;
     double *acc = acc_all + (size_t)(threadIdx.x >> 5) * cap;
@@ -1525,9 +1525,10 @@ int dispatch(const fe_pattern *p, const double *K, double *values, int mode, int
     if (nln == 8 && B == 3) return launch_gather<8, 3, MT, CRAC>(p, K, values, accumulate, s);
     if (nln == 10 && B == 3) return launch_gather<10, 3, MT, CRAC>(p, K, values, accumulate, s);
     if constexpr (std::is_same<MT, uint8_t>::value) {
-        // Q2..Q4 scalar quads and Q1 quads with 2..8 DOFs per node: the
-        // several-rows-per-warp and batched-incidence row kernels instead of
-        // the generic one, which loads one incidence at a time
+        // Q2..Q7 scalar quads, Q1 quads with 2..8 DOFs per node and Q2..Q4
+        // quads with 4: the several-rows-per-warp and batched-incidence row
+        // kernels instead of the generic one, which loads one incidence at a
+        // time
         if (nln == 9 && B == 1) return launch_gather<9, 1, MT, CRAC, false>(p, K, values, accumulate, s);
         if (nln == 16 && B == 1) return launch_gather<16, 1, MT, CRAC, false>(p, K, values, accumulate, s);
         if (nln == 25 && B == 1) return launch_gather<25, 1, MT, CRAC, false>(p, K, values, accumulate, s);
@@ -1538,7 +1539,17 @@ int dispatch(const fe_pattern *p, const double *K, double *values, int mode, int
         if (nln == 4 && B == 6) return launch_gather<4, 6, MT, CRAC, false>(p, K, values, accumulate, s);
         if (nln == 4 && B == 7) return launch_gather<4, 7, MT, CRAC, false>(p, K, values, accumulate, s);
         if (nln == 4 && B == 8) return launch_gather<4, 8, MT, CRAC, false>(p, K, values, accumulate, s);
+        if (nln == 9 && B == 4) return launch_gather<9, 4, MT, CRAC, false>(p, K, values, accumulate, s);
+        if (nln == 16 && B == 4) return launch_gather<16, 4, MT, CRAC, false>(p, K, values, accumulate, s);
+        if (nln == 25 && B == 4) return launch_gather<25, 4, MT, CRAC, false>(p, K, values, accumulate, s);
+        if constexpr (!CRAC) {  // more than 32 nodes: CSR rows only (multi-word run masks)
+            if (nln == 36 && B == 1) return launch_gather<36, 1, MT, CRAC, false>(p, K, values, accumulate, s);
+            if (nln == 49 && B == 1) return launch_gather<49, 1, MT, CRAC, false>(p, K, values, accumulate, s);
+            if (nln == 64 && B == 1) return launch_gather<64, 1, MT, CRAC, false>(p, K, values, accumulate, s);
+        }
     }
+    if constexpr (!CRAC)  // Q8 scalar quads: rows of up to 289 nodes, 16-bit slot maps
+        if (nln == 81 && B == 1) return launch_gather<81, 1, MT, CRAC, false>(p, K, values, accumulate, s);
     return launch_gather<0, 0, MT, CRAC>(p, K, values, accumulate, s);
 }
 

@@ -213,11 +213,13 @@ def test_generic_sizes_and_layouts(ctx, case):
     g.free()
 
 
-@pytest.mark.parametrize("p,d", [(2, 1), (3, 1), (4, 1), (1, 2), (1, 3), (1, 4), (1, 5), (1, 6), (1, 7), (1, 8)])
+@pytest.mark.parametrize("p,d", [(2, 1), (3, 1), (4, 1), (5, 1), (8, 1), (1, 2), (1, 3), (1, 4), (1, 5), (1, 6),
+                                 (1, 7), (1, 8), (2, 4), (4, 4)])
 def test_quad_shapes_permuted_nodes(ctx, p, d):
-    """The quad shapes with their own row kernels (Q2..Q4 scalar, Q1 with
-    2..8 DOFs per node) on a mesh whose node numbers are shuffled: irregular
-    rows and CRAC runs that differ from element to element."""
+    """The quad shapes with their own row kernels (Q2..Q8 scalar, Q1 with
+    2..8 DOFs per node, Q2..Q4 with 4) on a mesh whose node numbers are
+    shuffled: irregular rows and CRAC runs that differ from element to
+    element (Q8: rows over 256 nodes, 16-bit slot maps)."""
     D, n_dofs = wl.quad_qp_grid(6, p, d)
     perm = np.random.default_rng(100 * p + d).permutation(n_dofs // d)
     D = (perm[D // d] * d + D % d).astype(np.int32)
