@@ -164,7 +164,7 @@ template <int NLN, int BB, bool CRAC, int U>
 constexpr bool gather_packs()
 {
     constexpr int NLOC = NLN * BB, CHK = BB * NLOC;
-    return CRAC && NLN > 0 && (BB - 1) * NLOC + 1 >= 32 && (U * CHK + 31) / 32 < U * ((CHK + 31) / 32) && U <= 32;
+    return CRAC && NLN > 0 && NLN <= 32 && (BB - 1) * NLOC + 1 >= 32 && (U * CHK + 31) / 32 < U * ((CHK + 31) / 32) && U <= 32;
 }
 
 template <int NLN, int BB, typename MT, bool CRAC, int U>
@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
     constexpr int IT = (CHK + 31) / 32;
     constexpr int ITP = (U * CHK + 31) / 32;  // slot rows of U packed slices
     constexpr bool PACK = gather_packs<NLN, BB, CRAC, U>();
-    // CRAC rows read the run-start mask as one 32-bit word per element (run_of)
-    static_assert(NLN >= 1 && (!CRAC || NLN <= 32), "k_gather_node: CRAC rows of at most 32 nodes per element");
+    static_assert(NLN >= 1 && (!PACK || NLN <= 32), "packed slices: one run-mask word per element");
+    constexpr int MW = (NLN + 31) / 32;  // run-start mask words per element
     extern __shared__ double acc_all[];
     const int lane = threadIdx.x & 31;
     double *acc = acc_all + (size_t)(threadIdx.x >> 5) * cap;
@@ -197,7 +197,10 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
     for (int j = 0; j < IT; ++j) {
         ku[j] = 0;
         offu[j] = 0;
-        if (CRAC && g.uniform_R) run_of(g.run_mask[0], c_[j] / BB, ku[j], offu[j]);
+        if (CRAC && g.uniform_R) {
+            if constexpr (MW == 1) run_of(g.run_mask[0], c_[j] / BB, ku[j], offu[j]);
+            else run_of_multi(g.run_mask, c_[j] / BB, ku[j], offu[j]);
+        }
     }
     // CSR rows of 3+ DOF blocks: the next row's pointers and adjacency range
     // are loaded one row ahead (one dependent load fewer on each row's path;
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
                         } else {
                             rp = g.run_ptr[e];
                             nr = (int)(g.run_ptr[e + 1] - rp);
-                            m = g.run_mask[e];
+                            if constexpr (MW == 1) m = g.run_mask[e];
                         }
                     }
 #pragma unroll
@@ -348,7 +351,10 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
                                 pos = (int)map[(int64_t)t * NLN + kc];
                             } else {
                                 int k = ku[j], off = offu[j];
-                                if (!g.uniform_R) run_of(m, kc, k, off);
+                                if (!g.uniform_R) {
+                                    if constexpr (MW == 1) run_of(m, kc, k, off);
+                                    else run_of_multi(g.run_mask + (int64_t)e * MW, kc, k, off);
+                                }
                                 pos = (int)mapc[rp * NLN + (int64_t)kr * nr + k] + off;
                             }
                             rel[u][j] = jr_[j] * (int)RL + BB * pos + c_[j] % BB;
@@ -1528,7 +1534,7 @@ int dispatch(const fe_pattern *p, const double *K, double *values, int mode, int
         // Q2..Q7 scalar quads, Q1 quads with 2..8 DOFs per node and Q2..Q4
         // quads with 4: the several-rows-per-warp and batched-incidence row
         // kernels instead of the generic one, which loads one incidence at a
-        // time
+        // time (elements of more than 32 nodes: multi-word run masks)
         if (nln == 9 && B == 1) return launch_gather<9, 1, MT, CRAC, false>(p, K, values, accumulate, s);
         if (nln == 16 && B == 1) return launch_gather<16, 1, MT, CRAC, false>(p, K, values, accumulate, s);
         if (nln == 25 && B == 1) return launch_gather<25, 1, MT, CRAC, false>(p, K, values, accumulate, s);
@@ -1542,14 +1548,12 @@ int dispatch(const fe_pattern *p, const double *K, double *values, int mode, int
         if (nln == 9 && B == 4) return launch_gather<9, 4, MT, CRAC, false>(p, K, values, accumulate, s);
         if (nln == 16 && B == 4) return launch_gather<16, 4, MT, CRAC, false>(p, K, values, accumulate, s);
         if (nln == 25 && B == 4) return launch_gather<25, 4, MT, CRAC, false>(p, K, values, accumulate, s);
-        if constexpr (!CRAC) {  // more than 32 nodes: CSR rows only (multi-word run masks)
-            if (nln == 36 && B == 1) return launch_gather<36, 1, MT, CRAC, false>(p, K, values, accumulate, s);
-            if (nln == 49 && B == 1) return launch_gather<49, 1, MT, CRAC, false>(p, K, values, accumulate, s);
-            if (nln == 64 && B == 1) return launch_gather<64, 1, MT, CRAC, false>(p, K, values, accumulate, s);
-        }
+        if (nln == 36 && B == 1) return launch_gather<36, 1, MT, CRAC, false>(p, K, values, accumulate, s);
+        if (nln == 49 && B == 1) return launch_gather<49, 1, MT, CRAC, false>(p, K, values, accumulate, s);
+        if (nln == 64 && B == 1) return launch_gather<64, 1, MT, CRAC, false>(p, K, values, accumulate, s);
     }
-    if constexpr (!CRAC)  // Q8 scalar quads: rows of up to 289 nodes, 16-bit slot maps
-        if (nln == 81 && B == 1) return launch_gather<81, 1, MT, CRAC, false>(p, K, values, accumulate, s);
+    // Q8 scalar quads: rows of up to 289 nodes, 16-bit slot maps
+    if (nln == 81 && B == 1) return launch_gather<81, 1, MT, CRAC, false>(p, K, values, accumulate, s);
     return launch_gather<0, 0, MT, CRAC>(p, K, values, accumulate, s);
 }
 
