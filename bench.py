@@ -320,6 +320,8 @@ def run_gpu(args, rank, world, local_rank):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": recorded_traffic(kkey),
                 "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.8 TB/s",
+                # context: GB300's nominal HBM3e bandwidth
+                "nominal_GBps": 7900.0, "frac_of_nominal": round(achieved / 7900.0, 4),
                 "kernel": f"fe_assemble_{fmt} {mode_name} (one call)", "alg_bytes_per_launch": B,
                 "kernel_ms": round(kern_ms, 4),
                 "live_probe_GBps": probe,
@@ -946,6 +948,7 @@ def run_served(args, local_rank):
             fe.fe_release(sv, t)
         tickets = [None] * n_req
         lat = [None] * n_req
+        lat_asm = [None] * n_req  # issued to the GPU -> completion seen (no queueing before it)
         done = threading.Event()
 
         def collect():
@@ -955,6 +958,7 @@ def run_served(args, local_rank):
                 r = fe.fe_wait(sv, tickets[k], 600)
                 if r["state"] == fe.FE_STATE_DONE:
                     lat[k] = (r["t_done_us"] - r["t_submit_us"]) * 1e-3
+                    lat_asm[k] = (r["t_done_us"] - r["t_start_us"]) * 1e-3
                 fe.fe_release(sv, tickets[k])
             done.set()
 
@@ -987,6 +991,8 @@ def run_served(args, local_rank):
                 "p99_ms_small_warm": pct(sel(lambda lg, wm: not lg and wm), 99),
                 "p50_ms_large": pct(sel(lambda lg, wm: lg), 50), "p99_ms_large": pct(sel(lambda lg, wm: lg), 99),
                 "p99_ms_cold": pct(sel(lambda lg, wm: not wm), 99),
+                "assembly_p50_ms": pct([x for x in lat_asm if x is not None], 50),
+                "assembly_p99_ms": pct([x for x in lat_asm if x is not None], 99),
                 "launches": stats["launches"], "patterns_built": stats["patterns_built"],
                 "evictions": stats["evictions"]}
 

@@ -522,12 +522,15 @@ __global__ void k_map_node(const int32_t *__restrict__ N, int32_t nln, int64_t n
 // first block in row v, found by Listing 1's block search over the CRAC
 // pairs of DOF row B*v, read with the row's own bound: the last block of
 // the row is taken when no later block starts at or before the column.
+// uniform_R > 0: every element has element 0's runs (uniform_R of them), so
+// the run starts come from element 0's mask (cache-resident, independent of
+// the adjacency) and the element's map offset is e * uniform_R.
 template <typename MT>
 __global__ void k_map_runs(const int32_t *__restrict__ N, int32_t nln, int64_t n_nodes, int32_t B, int mask_words,
                            const int64_t *__restrict__ adj_ptr, const uint32_t *__restrict__ adj,
                            const int64_t *__restrict__ crac_ptr, const int32_t *__restrict__ col_align,
                            const uint32_t *__restrict__ run_mask, const int64_t *__restrict__ run_ptr, int cap,
-                           int rmax, MT *__restrict__ mapc, int64_t *sc)
+                           int rmax, int uniform_R, MT *__restrict__ mapc, int64_t *sc)
 {
     extern __shared__ int32_t sbuf[];
     const int lane = threadIdx.x & 31;
@@ -553,7 +556,7 @@ __global__ void k_map_runs(const int32_t *__restrict__ N, int32_t nln, int64_t n
             const uint32_t t = adj[a + s];
             const int64_t e = t / (uint32_t)nln;
             const int k = (int)(t - (uint32_t)(e * nln));
-            const uint32_t *m = run_mask + e * mask_words;
+            const uint32_t *m = uniform_R ? run_mask : run_mask + e * mask_words;
             // position of the ri-th set bit of the element's run-start mask
             int kc = -1, seen = 0;
             for (int w = 0; w < mask_words && kc < 0; ++w) {
@@ -566,8 +569,15 @@ __global__ void k_map_runs(const int32_t *__restrict__ N, int32_t nln, int64_t n
                 seen += cnt;
             }
             if (kc < 0) continue;  // the element has fewer runs
-            const int64_t rp = run_ptr[e];
-            const int nr = (int)(run_ptr[e + 1] - rp);
+            int64_t rp;
+            int nr;
+            if (uniform_R) {
+                nr = uniform_R;
+                rp = e * uniform_R;
+            } else {
+                rp = run_ptr[e];
+                nr = (int)(run_ptr[e + 1] - rp);
+            }
             const int32_t j = B * N[e * nln + kc];
             int p = 0;
             while (p + 2 < np) {
@@ -824,12 +834,14 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
                 FE_TRY(configure_smem(k_map_runs<uint8_t>, smem));
                 FE_LAUNCH((k_map_runs<uint8_t><<<fe_grid_for(n_nodes * 32, WM * 32, sms, 8), WM * 32, smem, s>>>(
                     p->node_dofs, nln, n_nodes, B, p->mask_words, p->adj_ptr, p->adj, p->crac_ptr, p->col_align,
-                    p->run_mask, p->run_ptr, cap, p->uniform_runs ? p->runs_per_elem : nln, (uint8_t *)p->map_crac, sc)));
+                    p->run_mask, p->run_ptr, cap, p->uniform_runs ? p->runs_per_elem : nln,
+                    p->uniform_runs ? p->runs_per_elem : 0, (uint8_t *)p->map_crac, sc)));
             } else {
                 FE_TRY(configure_smem(k_map_runs<uint16_t>, smem));
                 FE_LAUNCH((k_map_runs<uint16_t><<<fe_grid_for(n_nodes * 32, WM * 32, sms, 8), WM * 32, smem, s>>>(
                     p->node_dofs, nln, n_nodes, B, p->mask_words, p->adj_ptr, p->adj, p->crac_ptr, p->col_align,
-                    p->run_mask, p->run_ptr, cap, p->uniform_runs ? p->runs_per_elem : nln, (uint16_t *)p->map_crac, sc)));
+                    p->run_mask, p->run_ptr, cap, p->uniform_runs ? p->runs_per_elem : nln,
+                    p->uniform_runs ? p->runs_per_elem : 0, (uint16_t *)p->map_crac, sc)));
             }
             FE_CUDA(cudaGetLastError());
         }
