@@ -57,6 +57,7 @@ def parse():
                          "d-benchmarks on structured Q_p quads, every assembly mode; tet96: the 96^3 "
                          "Kuhn-split P2 tet mesh with permuted node ids (30x30 SPD K)")
     ap.add_argument("--meshes", type=int, default=256, help="batched workload: number of meshes")
+    ap.add_argument("--tet-n", type=int, default=96, help="tet96 workload: hex grid side (96 = the 96^3 workload)")
     ap.add_argument("--rate", type=float, default=2000.0, help="served workload: mean arrivals per second")
     ap.add_argument("--duration", type=float, default=2.0, help="served workload: seconds of arrivals")
     return ap.parse_args()
@@ -836,7 +837,7 @@ def run_tet(args, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
     ctx = fe.fe_create(local_rank)
-    n = 96
+    n = args.tet_n
     D, n_dofs = wl.tet_p2_kuhn(n, d=3, seed=0)
     n_e, n_loc = D.shape
     N_ent = n_e * n_loc * n_loc

@@ -20,6 +20,10 @@ struct Geo {
     int mask_words;
     int64_t nnz;    // values length (index checks of debug builds)
     int *status;    // the context's device status word
+    // per node incidence s, when built (non-uniform runs): the incidence's
+    // map_crac row offset and its element's run-start mask
+    const int32_t *inc_off = nullptr;
+    const uint32_t *inc_mask = nullptr;
 };
 
 __device__ __forceinline__ int64_t crac_row_base(const Geo &g, int64_t i) { return g.col_align[g.crac_ptr[i] + 1]; }
@@ -53,7 +57,7 @@ inline Geo geo_of(const fe_pattern *p)
 {
     return Geo{p->node_dofs, p->row_ptr,  p->crac_ptr, p->col_align, p->run_mask,
                p->run_ptr,   p->adj_ptr, p->adj,      p->uniform_runs ? p->runs_per_elem : 0, p->mask_words,
-               p->nnz,       p->ctx->d_status};
+               p->nnz,       p->ctx->d_status, p->inc_off, p->inc_mask};
 }
 
 // One element of NLN blocks of BB DOFs (NLN*BB <= 32), the warp cooperating:

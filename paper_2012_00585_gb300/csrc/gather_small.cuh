@@ -83,18 +83,19 @@ __device__ __forceinline__ void gather_rows_small(const double *__restrict__ K, 
                 if (!CRAC) {
                     rel[u] = (int)(jr * RL) + BB * (int)map[(int64_t)t * NLN + kc] + cb;
                 } else {
-                    int64_t rp;
-                    int nr;
+                    int64_t mb;  // the incidence's row of the run map
                     int k = ku, off = offu;
                     if (g.uniform_R) {
-                        nr = g.uniform_R;
-                        rp = (int64_t)e * nr;
+                        mb = (int64_t)t * g.uniform_R;  // e R NLN + kr R
+                    } else if (g.inc_off) {
+                        mb = g.inc_off[a + s0 + u];
+                        run_of(g.inc_mask[a + s0 + u], kc, k, off);
                     } else {
-                        rp = g.run_ptr[e];
-                        nr = (int)(g.run_ptr[e + 1] - rp);
+                        const int64_t rp = g.run_ptr[e];
+                        mb = rp * NLN + (int64_t)kr * (g.run_ptr[e + 1] - rp);
                         run_of(g.run_mask[e], kc, k, off);
                     }
-                    rel[u] = (int)(jr * RL) + BB * ((int)mapc[rp * NLN + (int64_t)kr * nr + k] + off) + cb;
+                    rel[u] = (int)(jr * RL) + BB * ((int)mapc[mb + k] + off) + cb;
                 }
             }
         }

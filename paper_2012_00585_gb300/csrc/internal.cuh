@@ -77,6 +77,10 @@ struct fe_pattern {
     uint32_t *run_mask = nullptr;  // [n_e * mask_words] run starts over the element's blocks
     int64_t *run_ptr = nullptr;    // [n_e + 1]
     void *map_crac = nullptr;      // [n_runs * nln] uint8/uint16: run start position in block row
+    // non-uniform runs, one mask word: per node incidence s (adjacency order),
+    // the offset of its row of map_crac and its element's run-start mask
+    int32_t *inc_off = nullptr;    // [n_e * nln]
+    uint32_t *inc_mask = nullptr;  // [n_e * nln]
     struct fe_colouring *colouring = nullptr;  // greedy element colouring (fe_pattern_colour)
 };
 

@@ -253,15 +253,19 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
                 // by shuffle (its slice starts at K + t * CHK: e NN + kr CHK)
                 const int nu = (int)(b - s0 < U ? b - s0 : U);
                 uint32_t t_l = 0, m_l = 0;
-                int64_t rp_l = 0;
-                int nr_l = 0;
+                int64_t mb_l = 0;  // the incidence's row of the run map (non-uniform runs)
                 if (lane < nu) {
                     t_l = g.adj[s0 + lane];
                     if (CRAC && !g.uniform_R) {
-                        const uint32_t e = t_l / NLN;
-                        rp_l = g.run_ptr[e];
-                        nr_l = (int)(g.run_ptr[e + 1] - rp_l);
-                        m_l = g.run_mask[e];
+                        if (g.inc_off) {
+                            mb_l = g.inc_off[s0 + lane];
+                            m_l = g.inc_mask[s0 + lane];
+                        } else {
+                            const uint32_t e = t_l / NLN;
+                            const int64_t rp = g.run_ptr[e];
+                            mb_l = rp * NLN + (int64_t)(t_l - e * NLN) * (g.run_ptr[e + 1] - rp);
+                            m_l = g.run_mask[e];
+                        }
                     }
                 }
                 double kv[ITP];
@@ -277,12 +281,10 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
                     const int u = lo + (sl >= (lo + 1) * CHK ? 1 : 0);
                     const int q = sl - u * CHK;
                     const uint32_t t = __shfl_sync(0xffffffffu, t_l, u & 31);
-                    int64_t rp = 0;
-                    int nr = 0;
+                    int64_t mb = 0;
                     uint32_t m = 0;
                     if (CRAC && !g.uniform_R) {
-                        rp = __shfl_sync(0xffffffffu, rp_l, u & 31);
-                        nr = __shfl_sync(0xffffffffu, nr_l, u & 31);
+                        mb = __shfl_sync(0xffffffffu, mb_l, u & 31);
                         m = __shfl_sync(0xffffffffu, m_l, u & 31);
                     }
                     kv[i] = 0.0;
@@ -295,17 +297,14 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
                         if (!CRAC) {
                             pos = (int)map[(int64_t)t * NLN + kc];
                         } else {
-                            const uint32_t e = t / NLN;
-                            const int kr = (int)(t - e * NLN);
                             int k, off;
                             if (g.uniform_R) {
-                                nr = g.uniform_R;
-                                rp = (int64_t)e * nr;
+                                mb = (int64_t)t * g.uniform_R;  // e R NLN + kr R
                                 run_of(g.run_mask[0], kc, k, off);
                             } else {
                                 run_of(m, kc, k, off);
                             }
-                            pos = (int)mapc[rp * NLN + (int64_t)kr * nr + k] + off;
+                            pos = (int)mapc[mb + k] + off;
                         }
                         rel[i] = jr * (int)RL + BB * pos + cb;
                     }
@@ -325,16 +324,17 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
                     const uint32_t e = t / NLN;
                     const int kr = (int)(t - e * NLN);
                     const double *chunk = K + (int64_t)e * NN + (int64_t)kr * CHK;
-                    int64_t rp = 0;
-                    int nr = 0;
+                    int64_t mb = 0;  // this incidence's row of the run map
                     uint32_t m = 0;
                     if (CRAC && have) {
                         if (g.uniform_R) {
-                            nr = g.uniform_R;
-                            rp = (int64_t)e * nr;
+                            mb = (int64_t)t * g.uniform_R;  // e R NLN + kr R
+                        } else if (MW == 1 && g.inc_off) {
+                            mb = g.inc_off[s0 + u];
+                            m = g.inc_mask[s0 + u];
                         } else {
-                            rp = g.run_ptr[e];
-                            nr = (int)(g.run_ptr[e + 1] - rp);
+                            const int64_t rp = g.run_ptr[e];
+                            mb = rp * NLN + (int64_t)kr * (g.run_ptr[e + 1] - rp);
                             if constexpr (MW == 1) m = g.run_mask[e];
                         }
                     }
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(256, (CRAC && BB == 3 && U == 4) ? 4 : 0) k_ga
                                     if constexpr (MW == 1) run_of(m, kc, k, off);
                                     else run_of_multi(g.run_mask + (int64_t)e * MW, kc, k, off);
                                 }
-                                pos = (int)mapc[rp * NLN + (int64_t)kr * nr + k] + off;
+                                pos = (int)mapc[mb + k] + off;
                             }
                             rel[u][j] = jr_[j] * (int)RL + BB * pos + c_[j] % BB;
                         }

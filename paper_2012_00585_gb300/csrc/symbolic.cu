@@ -596,6 +596,24 @@ __global__ void k_map_runs(const int32_t *__restrict__ N, int32_t nln, int64_t n
     }
 }
 
+// Per node incidence s (t = adj[s] = e * nln + kr): the offset of the
+// incidence's row of element e's run map, run_ptr[e] * nln + kr * runs(e),
+// and e's run-start mask, laid out in adjacency order so that the CRAC
+// gather reads them with the incidence itself instead of after it.
+__global__ void k_inc_runs(const uint32_t *__restrict__ adj, int64_t n_inc, int32_t nln,
+                           const int64_t *__restrict__ run_ptr, const uint32_t *__restrict__ run_mask,
+                           int32_t *__restrict__ inc_off, uint32_t *__restrict__ inc_mask)
+{
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_inc; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = adj[s];
+        const int64_t e = t / (uint32_t)nln;
+        const int64_t kr = t - e * nln;
+        const int64_t rp = run_ptr[e];
+        inc_off[s] = (int32_t)(rp * nln + kr * (run_ptr[e + 1] - rp));
+        inc_mask[s] = run_mask[e];
+    }
+}
+
 struct Scratch {
     cudaStream_t s;
     void *p[12] = {};
@@ -610,8 +628,8 @@ struct Scratch {
 void pattern_release(fe_pattern *p, cudaStream_t s)
 {
     fe_colouring_free(p, s);
-    void *ptrs[] = {p->node_dofs, p->row_ptr, p->col_idx, p->crac_ptr, p->col_align, p->adj_ptr,
-                    p->adj,       p->map_csr, p->run_mask, p->run_ptr, p->map_crac};
+    void *ptrs[] = {p->node_dofs, p->row_ptr, p->col_idx, p->crac_ptr, p->col_align, p->adj_ptr, p->adj,
+                    p->map_csr,   p->run_mask, p->run_ptr, p->map_crac, p->inc_off, p->inc_mask};
     for (void *x : ptrs) fe_free_async(x, s);
     delete p;
 }
@@ -845,6 +863,16 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
             }
             FE_CUDA(cudaGetLastError());
         }
+    }
+    // non-uniform runs of one mask word: the run tables in adjacency order
+    if ((p->flags & FE_PATTERN_MAP_CRAC) && !p->uniform_runs && p->mask_words == 1 && n_ninc > 0 &&
+        p->n_runs * nln < INT32_MAX) {
+        FE_TRY(alloc_into(p, (void **)&p->inc_off, sizeof(int32_t) * (size_t)n_ninc, s));
+        FE_TRY(alloc_into(p, (void **)&p->inc_mask, sizeof(uint32_t) * (size_t)n_ninc, s));
+        FE_LAUNCH((k_inc_runs<<<fe_grid_for(n_ninc, 256, sms, 16), 256, 0, s>>>(p->adj, n_ninc, nln, p->run_ptr,
+                                                                                 p->run_mask, p->inc_off,
+                                                                                 p->inc_mask)));
+        FE_CUDA(cudaGetLastError());
     }
     if (!(p->flags & FE_PATTERN_CRAC) && !(p->flags & FE_PATTERN_MAP_CRAC)) {
         // CRAC was only scaffolding for this pattern
