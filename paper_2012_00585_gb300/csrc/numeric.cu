@@ -156,15 +156,18 @@ __global__ void __launch_bounds__(256) k_atomic_generic(const double *__restrict
 // meet in an accumulator slot: entries of one slot share their block row, so
 // in the concatenation they lie at least CHK - NLOC + 1 >= 32 slots apart,
 // i.e. in different instructions, the earlier incidence first.  The per-slot
-// order is unchanged and the result bit-identical.  Measured on the 64^3
-// elasticity mesh: CRAC rows 615 -> 582 us (the unpacked instance spilled);
-// CSR rows 413 -> 447 us (the extra shuffles and index arithmetic cost more
-// than the saved lanes), so CSR rows stay unpacked.
+// order is unchanged and the result bit-identical.  CRAC rows take the packed
+// form whenever it needs no more instruction rows than the unpacked one: it
+// holds no per-lane slot tables, which the unpacked CRAC instances spilled
+// (64^3 elasticity 615 -> 582 us; P2 tets, 90-entry slices, same row count:
+// 7.12 -> 6.25 ms at 64^3).  CSR rows stay unpacked: there the extra shuffles
+// and index arithmetic cost more than the saved lanes (413 -> 447 us).
 template <int NLN, int BB, bool CRAC, int U>
 constexpr bool gather_packs()
 {
     constexpr int NLOC = NLN * BB, CHK = BB * NLOC;
-    return CRAC && NLN > 0 && NLN <= 32 && (BB - 1) * NLOC + 1 >= 32 && (U * CHK + 31) / 32 < U * ((CHK + 31) / 32) && U <= 32;
+    return CRAC && NLN > 0 && NLN <= 32 && (BB - 1) * NLOC + 1 >= 32 && (U * CHK + 31) / 32 <= U * ((CHK + 31) / 32) &&
+           U <= 32;
 }
 
 template <int NLN, int BB, typename MT, bool CRAC, int U>
