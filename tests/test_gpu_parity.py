@@ -231,6 +231,45 @@ def test_quad_shapes_permuted_nodes(ctx, p, d):
     g.free()
 
 
+@pytest.mark.parametrize("case", ["hex_d16", "quad_d32", "scattered_128"])
+def test_largest_elements(ctx, case):
+    """Elements of FE_MAX_NLOC = 128 DOFs, the largest the library takes: 16
+    DOFs per hex node (the generic row kernel), 32 per quad node (the largest
+    DOF block), and unblocked elements of 128 scattered DOFs (run-start masks
+    of four words, rows over 256 entries: 16-bit slot maps).  Every mode
+    against the oracle: deterministic and coloured bit-exact (the coloured
+    sum in colour order), atomic and row-locked within the row tolerance."""
+    from paper_2012_00585_gb300 import feasm
+    if case == "hex_d16":
+        D, n_dofs = wl.hex_q1_grid(3, 16)
+    elif case == "quad_d32":
+        D, n_dofs = wl.quad_q1_grid(4, 32)
+    else:
+        rng = np.random.default_rng(11)
+        D = np.stack([rng.choice(600, size=128, replace=False) for _ in range(40)]).astype(np.int32)
+        n_dofs = 600
+    assert D.shape[1] == feasm.FE_MAX_NLOC
+    K = wl.random_matrices(D.shape[0], D.shape[1], seed=12)
+    g = gu.GpuAssembly(ctx, D, n_dofs)
+    if case == "scattered_128":
+        assert g.pattern.info["map_bytes"] == 2
+    pat = _check_pattern(g, D, n_dofs)
+    v_o, _ = _run_all_modes(g, D, K, n_dofs, *pat)
+    rp_o, ci_o = pat[0], pat[1]
+    tau = gu.row_tolerance(rp_o, v_o, gu.contribution_abs_row_sums(D, K, n_dofs))
+    for fmt in ("csr", "crac"):
+        gu.assert_within_row_tol(rp_o, g.assemble(K, fmt, feasm.FE_ROWLOCK).cpu().numpy(), v_o, tau)
+    feasm.fe_pattern_colour(ctx, g.pattern.handle)
+    _, colour = oracle.greedy_colouring(D, n_dofs)
+    order = np.lexsort((np.arange(D.shape[0]), colour))
+    exp_c = oracle.assemble_csr(D, K, rp_o, ci_o, order=order)
+    for fmt in ("csr", "crac"):
+        got = g.assemble(K, fmt, feasm.FE_COLOURED).cpu().numpy()
+        assert np.array_equal(got.view(np.uint64), exp_c.view(np.uint64)), fmt
+    assert feasm.fe_device_status(ctx) == 0
+    g.free()
+
+
 def test_accumulate_both_modes(ctx):
     from paper_2012_00585_gb300 import feasm
     D, n_dofs = wl.tet_p2_kuhn(2, d=3, seed=9)
