@@ -37,7 +37,7 @@ VARIANTS = ("csr-atomic", "crac-atomic", "csr-det", "crac-det")
 EXTRA_VARIANTS = ("csr-coloured", "crac-coloured", "csr-rowlock", "crac-rowlock")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--tet-n", type=int, default=96, help="tet96 workload: hex grid side (96 = the 96^3 workload)")
     ap.add_argument("--rate", type=float, default=2000.0, help="served workload: mean arrivals per second")
     ap.add_argument("--duration", type=float, default=2.0, help="served workload: seconds of arrivals")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def b_alg(n_e, n_loc, nnz):
@@ -175,6 +175,16 @@ class ClockSampler:
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def step_config(args, n_dofs, n_e, N_ent, nnz, n_ca, world):
+    """The `config` of the default step, shared by both arms."""
+    return {"workload": f"hex Q1 {args.n}^3 elasticity, 3 DOF/node ({n_dofs} DOFs, {n_e} elements, 24x24 FP64 K)"
+                        f"; step = pattern build + {N_ASSEMBLIES} numeric assemblies ({args.variant})",
+            "global_batch": world, "entries_per_assembly": N_ent, "nnz": nnz, "n_ca": n_ca,
+            "l2": "inputs larger than L2 (K = %.2f GB per assembly)" % (8 * N_ent / 1e9),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            **({"knobs": args.knob} if args.knob else {})}
 
 
 # ------------------------------------------------------------------ GPU arm --
@@ -315,7 +325,7 @@ def run_gpu(args, rank, world, local_rank):
                       dist)
 
     hbm, src = measured_peaks()
-    probe = hbm_probe(ctx, feasm, dev, stream)
+    probe = hbm_probe(dev, stream)
     achieved = B / (kern_ms * 1e-3) / 1e9
     kkey = f"hex{n}_d3_{args.variant}"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
@@ -338,12 +348,7 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": round(ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"hex Q1 {n}^3 elasticity, 3 DOF/node ({n_dofs} DOFs, {n_e} elements, 24x24 FP64 K)"
-                               f"; step = pattern build + {N_ASSEMBLIES} numeric assemblies ({args.variant})",
-                   "global_batch": world, "entries_per_assembly": N_ent, "nnz": nnz, "n_ca": info["n_ca"],
-                   "l2": "inputs larger than L2 (K = %.2f GB per assembly)" % (8 * N_ent / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   **({"knobs": args.knob} if args.knob else {})},
+        "config": step_config(args, n_dofs, n_e, N_ent, nnz, info["n_ca"], world),
         "roofline": roofline,
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps,
@@ -403,15 +408,25 @@ def c1_latency(ctx, feasm, dev, stream):
     return out
 
 
-def hbm_probe(ctx, feasm, dev, stream):
-    """Live bandwidth of this GPU (2 GiB streamed, best of 6): read-only by
-    the SMs' loads, copy, and read-only by bulk copies (TMA).  The copy rate
+def hbm_probe(dev, stream):
+    """Live bandwidth of this GPU (2 GiB streamed, best of 6), from the
+    benchmark's probe library (not the assembly library): read-only by the
+    SMs' loads, copy, and read-only by bulk copies (TMA).  The copy rate
     matches the measured peak; loads alone stream about half of what bulk
     copies do."""
+    import ctypes
+
     import torch
+    from paper_2012_00585_gb300 import _build
+    lib = ctypes.CDLL(_build.build_probe())
+    vp = ctypes.c_void_p
+    lib.feprobe_stream.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+    lib.feprobe_stream_bulk.argtypes = [vp, ctypes.c_int64, vp, vp, vp]
     n = 1 << 28
     a = torch.ones(n, dtype=torch.float64, device=dev)
     b = torch.empty(n, dtype=torch.float64, device=dev)
+    sink = torch.zeros(1, dtype=torch.float64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
     out = {}
     for name, dst, mult in (("read", None, 1), ("copy", b, 2), ("read_bulk", None, 1)):
         best = 1e30
@@ -419,13 +434,16 @@ def hbm_probe(ctx, feasm, dev, stream):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             if name == "read_bulk":
-                feasm.fe_hbm_probe_bulk(ctx, a, n, stream)
+                rc = lib.feprobe_stream_bulk(a.data_ptr(), n, sink.data_ptr(), status.data_ptr(), stream.cuda_stream)
             else:
-                feasm.fe_hbm_probe(ctx, a, dst, n, stream)
+                rc = lib.feprobe_stream(a.data_ptr(), None if dst is None else dst.data_ptr(), n, sink.data_ptr(),
+                                        stream.cuda_stream)
+            assert rc == 0, name
             e1.record(stream)
             e1.synchronize()
             best = min(best, e0.elapsed_time(e1))
         out[name] = round(mult * 8 * n / (best * 1e-3) / 1e9, 1)
+    assert int(status.item()) == 0, "bulk-copy probe wait ran out"
     del a, b
     torch.cuda.empty_cache()
     return out
@@ -602,35 +620,44 @@ def cpu_baseline(n):
 
 
 def run_reference(args):
-    """The oracle as the reference arm: each step is a bounded sample (a
-    16^3 mesh of the same family: pattern + 10 assemblies)."""
+    """The oracle as the reference arm, on the bench's own workload (the
+    n^3 elasticity mesh of the default step, same config).  Each step is a
+    bounded sample of that step: the pattern (CSR + CRAC) built once and 2
+    numeric assemblies timed, the step's time extrapolated to pattern +
+    10 assemblies (every assembly of the step does the same work)."""
     import oracle
     import workloads as wl
-    n = 16
+    n = args.n
     D, n_dofs = wl.hex_q1_grid(n, 3)
-    K = wl.broadcast_matrices(wl.elasticity_q1_hex(1.0 / n), D.shape[0])
+    n_e, n_loc = D.shape
+    K = wl.broadcast_matrices(wl.elasticity_q1_hex(1.0 / n), n_e)
+    info = {}
 
     def step():
+        t = time.perf_counter()
         rp, ci = oracle.csr_pattern(D, n_dofs)
-        oracle.crac_from_csr(rp, ci, n_dofs)
-        for _ in range(N_ASSEMBLIES):
+        _, ca = oracle.crac_from_csr(rp, ci, n_dofs)
+        t_pat = time.perf_counter() - t
+        t = time.perf_counter()
+        for _ in range(2):
             oracle.assemble_csr(D, K, rp, ci)
+        t_num = (time.perf_counter() - t) / 2
+        info.update(nnz=int(rp[-1]), n_ca=int(ca.shape[0]))
+        return t_pat + N_ASSEMBLIES * t_num
 
     with OneCore():
         for _ in range(args.warmup):
             step()
-        t = time.perf_counter()
-        for _ in range(args.steps):
-            step()
-        sec = (time.perf_counter() - t) / args.steps
-    value = N_ASSEMBLIES * K.size / sec
-    sample = f"hex Q1 {n}^3 elasticity (3 DOF/node, {D.shape[0]} elements): serial oracle pinned to one core, " \
-             f"pattern + CRAC + {N_ASSEMBLIES} assemblies per step"
+        sec = statistics.mean(step() for _ in range(args.steps))
+    N_ent = n_e * n_loc * n_loc
+    value = N_ASSEMBLIES * N_ent / sec
+    sample = f"the step's own mesh (hex Q1 {n}^3 elasticity): serial oracle pinned to one core; per step the " \
+             f"pattern + CRAC built once and 2 numeric assemblies timed, step time = pattern + " \
+             f"{N_ASSEMBLIES} x numeric"
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"hex Q1 {args.n}^3 elasticity, 3 DOF/node; step = pattern build + "
-                                   f"{N_ASSEMBLIES} numeric assemblies", "sample": sample},
+            "config": step_config(args, n_dofs, n_e, N_ent, info["nnz"], info["n_ca"], 1),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                              "host": host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

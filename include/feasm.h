@@ -136,18 +136,6 @@ const char *fe_last_cuda_error(void);
  * incomplete. */
 int fe_device_status(fe_ctx *ctx, void *stream);
 
-/* HBM calibration (not part of the method): stream n doubles of device
- * memory `src` (16-byte aligned) on `stream`, read only (dst = NULL) or copied
- * into dst.  Callers time it to get the read-only and copy bandwidth that
- * bound a read-dominated or a balanced kernel. */
-int fe_hbm_probe(fe_ctx *ctx, const double *src, double *dst, int64_t n, void *stream);
-
-/* The read-only stream of fe_hbm_probe moved by the bulk-copy (TMA) engine
- * into shared memory instead of by the SMs' loads (n even, src 16-byte
- * aligned): the two rates differ by about two on GB300, which is why the
- * read-dominated kernels are compared with both. */
-int fe_hbm_probe_bulk(fe_ctx *ctx, const double *src, int64_t n, void *stream);
-
 /* Number of kernels this library has launched in this process so far (all
  * contexts and threads); a caller brackets a region with two reads to count
  * the launches inside it. */
@@ -162,23 +150,18 @@ int fe_debug_checks(void);
  * Kernel and launch-shape choices of the numeric phase, per context.  0 means
  * the library's default; an autotuner may set them.  Results do not depend on
  * them (FE_DETERMINISTIC stays bit-identical), only speed does. */
-#define FE_KNOB_GATHER_KERNEL 0  /* FE_DETERMINISTIC: 0 default (6 for one-DOF
-                                    shapes of 4 or 8 nodes, else 1), 1
-                                    register-batched row gather, 2
-                                    shared-memory-staged row
-                                    gather, 3 pipelined staged gather, 4 row
-                                    gather fed by bulk copies (TMA) through a
-                                    ring of stages, 5 two node rows per warp
-                                    sharing the FP64 add instructions, 6
-                                    one-DOF elements of <= 16 nodes: 4, 8 or
-                                    16 lanes per node row                    */
+#define FE_KNOB_GATHER_KERNEL 0  /* FE_DETERMINISTIC: 0 default (2 for node
+                                    rows whose incidence slices hold <= 16
+                                    entries, else 1), 1 one warp per node
+                                    row, incidences batched in registers, 2
+                                    several node rows per warp (4, 8 or 16
+                                    lanes each; slices of <= 16 entries)    */
 #define FE_KNOB_GATHER_BATCH 1   /* incidences per register batch: 4 or 8   */
 #define FE_KNOB_GATHER_WARPS 2   /* warps per block of the gather: 1..8      */
 #define FE_KNOB_ATOMIC_KERNEL 3  /* FE_ATOMIC: 1 register warp-per-element,
                                     2 bulk-copy (TMA) staged warp-per-element */
 #define FE_KNOB_ATOMIC_WARPS 4   /* warps per block of the staged kernel     */
-#define FE_KNOB_GATHER_STAGES 5  /* ring stages per warp of gather kernel 4:
-                                    2..8 (0: 4)                              */
+/* knob 5 is reserved */
 #define FE_KNOB_SPMV_LANES 7     /* lanes per row of fe_spmv_*: 2, 4, 8 or 16
                                     (0: 4)                                   */
 #define FE_KNOB_LOCK_SPIN 6      /* FE_ROWLOCK: a lock is given up after
@@ -235,16 +218,28 @@ int fe_pattern_build(fe_ctx *ctx, int64_t n_elem, int32_t dofs_per_elem, int64_t
  *   col_idx     device, int32 [col_capacity], written when nnz <= capacity.
  *   nnz         host, receives the number of pattern entries (also when the
  *               capacity was too small, so the caller can retry).
- *   stream      work is ordered on it; the call returns after a stream sync.
- * Works on the current CUDA device.  The first call on a device looks up the
- * array's device address; make that first call before any stream capture.
+ *   stream      work is ordered on it.  The call waits for `stream` three
+ *               times (it reads sizes back to the host) and returns after the
+ *               last wait, with the outputs complete.
+ * Works on the current CUDA device.  The first call on a device does the
+ * set-up: it looks up the array's device address (once per device; the
+ * address is kept for the life of the process, so after cudaDeviceReset the
+ * library must be reloaded before this call is used again).  Make that first
+ * call before any stream capture begins.
  * All calls share the one array (its contents persist between calls; this
  * call clears what must start at zero), so calls whose work overlaps on the
  * GPU, from different streams or threads, race: serialise them.
+ * Limit: the working arrays are laid out after the DOF block size B is known
+ * (see fe_pattern_info.block); they take about 4*n_elem*(dofs_per_elem/B)^2
+ * bytes for the row candidates plus 8*n_elem*dofs_per_elem/B bytes of
+ * node connectivity and adjacency, 8 bytes per element and 36 bytes per node
+ * plus 8 per DOF, which must fit in 16 MiB: e.g. about 39,000 trilinear hexes
+ * with 3 DOFs per node (a 34^3 mesh) or 110,000 bilinear quads with one DOF
+ * per node (a 330^2 mesh).
  * Errors: FE_ERR_UNSUPPORTED when the mesh needs more than the 16 MiB of
- * scratch (roughly n_elem * dofs_per_elem^2 * 4 bytes plus 60 bytes per DOF)
- * or dofs_per_elem > FE_MAX_NLOC; FE_ERR_INVALID_ARG when col_capacity < nnz;
- * FE_ERR_DOF_RANGE / FE_ERR_DUP_DOF for bad connectivity; FE_ERR_OVERFLOW.
+ * scratch or dofs_per_elem > FE_MAX_NLOC; FE_ERR_INVALID_ARG when
+ * col_capacity < nnz; FE_ERR_DOF_RANGE / FE_ERR_DUP_DOF for bad connectivity
+ * (checked first, whatever the size); FE_ERR_OVERFLOW.
  */
 int fe_pattern_csr_noalloc(int64_t n_elem, int32_t dofs_per_elem, int64_t n_dofs, const int32_t *elem_dofs,
                            int64_t *row_ptr, int32_t *col_idx, int64_t col_capacity, int64_t *nnz,
@@ -429,6 +424,12 @@ typedef struct fe_request {
     int32_t mode;              /* FE_ATOMIC / FE_DETERMINISTIC                          */
     int32_t reserved;
     void *ready_event;         /* cudaEvent_t the assembly waits for (NULL = none)     */
+    double deadline_s;         /* 0 = none; else the request must be launched on the
+                                  GPU within this many seconds of its submission: the
+                                  server's watchdog fails a request still queued after
+                                  that (pending, or admitted and waiting for its
+                                  launch) with FE_ERR_TIMEOUT and returns its memory.
+                                  Work already launched always completes.             */
 } fe_request;
 
 typedef struct fe_result {
@@ -447,7 +448,20 @@ typedef struct fe_server_stats {
     int64_t submitted, admitted, completed, failed, cancelled;
     int64_t launches, batched_requests, patterns_built, evictions;
     int64_t bytes_in_use, budget_bytes, cached_patterns;
+    int64_t rebuilds;  /* builds of a key whose pattern had been evicted       */
+    int64_t expired;   /* requests failed by the watchdog (deadline passed)    */
 } fe_server_stats;
+
+/* One span of device work seen by the server: a launched group of requests
+ * (element generation + batched assembly) on one of its streams, or a pattern
+ * build on its build stream (stream = -1).  Times are in ms after the server
+ * started, from CUDA events recorded on the span's own stream (so start_ms is
+ * when that stream reached the work, end_ms when it finished it). */
+typedef struct fe_span {
+    double start_ms, end_ms;
+    int32_t stream;            /* launch stream index, or -1 for a pattern build  */
+    int32_t n_requests;        /* requests in the group (1 for a build)           */
+} fe_span;
 
 typedef struct fe_server fe_server;
 
@@ -474,6 +488,12 @@ int fe_cancel(fe_server *server, uint64_t ticket);
 /* Free a finished ticket's values and unpin its pattern. */
 int fe_release(fe_server *server, uint64_t ticket);
 int fe_server_stats_get(fe_server *server, fe_server_stats *out);
+/* Copy spans [first, first + cap) of the server's device timeline (completed
+ * groups and builds, in completion order; at most 2^21 are kept) into out;
+ * *n_total (may be NULL) receives the number recorded so far.  Callers derive
+ * from it how much of the time requests' work from two or more streams was
+ * on the device at once. */
+int fe_server_timeline(fe_server *server, int64_t first, int64_t cap, fe_span *out, int64_t *n_total);
 
 /* K_e = alpha_e * K_ref for n_elem elements (the generator the server uses
  * for requests without elem_mats), on `stream`. */

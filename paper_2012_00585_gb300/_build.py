@@ -17,6 +17,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfeasm.so")
 # debug build: every FE_IN_BOUNDS index check compiled in (-DFE_DEBUG)
 LIB_DEBUG = os.path.join(BUILD, "debug", "libfeasm_debug.so")
+# HBM calibration probes used by the benchmark only (not part of libfeasm)
+PROBE_SRC = os.path.join(CSRC, "probe", "hbm_probe.cu")
+LIB_PROBE = os.path.join(BUILD, "probe", "libfeprobe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -73,6 +76,24 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), debug: boo
     run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread"])
     os.replace(tmp, lib)
     return lib
+
+
+def build_probe(force: bool = False) -> str:
+    """The benchmark's HBM probe library (one translation unit)."""
+    deps = [PROBE_SRC, os.path.join(CSRC, "tma.cuh"), os.path.abspath(__file__)]
+    if not force and os.path.exists(LIB_PROBE) and all(os.path.getmtime(d) <= os.path.getmtime(LIB_PROBE)
+                                                       for d in deps):
+        return LIB_PROBE
+    os.makedirs(os.path.dirname(LIB_PROBE), exist_ok=True)
+    tmp = LIB_PROBE + f".tmp{os.getpid()}"
+    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-shared", "-cudart", "static", PROBE_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        print(" ".join(cmd))
+        print(r.stdout + r.stderr)
+        raise RuntimeError("nvcc failed on the probe library")
+    os.replace(tmp, LIB_PROBE)
+    return LIB_PROBE
 
 
 if __name__ == "__main__":

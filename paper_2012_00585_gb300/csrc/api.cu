@@ -89,76 +89,6 @@ __global__ void k_tile_scan(const T *__restrict__ in, int64_t *__restrict__ out,
 
 __global__ void k_set_zero_i64(int64_t *p) { *p = 0; }
 
-// HBM calibration: stream n doubles (read only, or copy to dst), 8
-// independent 16-byte accesses in flight per thread.
-__global__ void k_hbm_probe(const double2 *__restrict__ src, double2 *__restrict__ dst, int64_t n2, double *sink)
-{
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += 8 * stride) {
-        double2 v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = i + u * stride < n2 ? __ldcs(src + i + u * stride) : make_double2(0.0, 0.0);
-        if (dst) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (i + u * stride < n2) __stcs(dst + i + u * stride, v[u]);
-        } else {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) s += v[u].x + v[u].y;
-        }
-    }
-    if (s == 1.2345e300) *sink = s;  // keeps the loads alive
-}
-
-// The same read-only stream moved by the bulk-copy (TMA) engine: chunks of
-// PROBE_CHUNK bytes into a ring of PROBE_STAGES shared-memory stages per
-// block (one mbarrier each).  Waits are bounded: a wait that runs out records
-// FE_ERR_TIMEOUT, waits (bounded) for the other copies and ends the block.
-constexpr int PROBE_CHUNK = 16384, PROBE_STAGES = 4;
-
-__global__ void __launch_bounds__(128) k_hbm_probe_bulk(const char *__restrict__ src, int64_t nbytes, double *sink,
-                                                        int *status)
-{
-    extern __shared__ __align__(128) unsigned char probe_smem[];
-    __shared__ uint64_t bar[PROBE_STAGES];
-    const int64_t n_chunks = (nbytes + PROBE_CHUNK - 1) / PROBE_CHUNK;
-    const uint64_t pol = fe_policy_evict_first();
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < PROBE_STAGES; ++st) fe_mbar_init(&bar[st], 1);
-        fe_fence_mbar_init();
-    }
-    __syncthreads();
-    auto issue = [&](int st, int64_t c) {
-        const uint32_t bytes = (uint32_t)min((int64_t)PROBE_CHUNK, nbytes - c * PROBE_CHUNK);
-        fe_fence_proxy_async();
-        fe_mbar_expect_tx(&bar[st], bytes);
-        fe_bulk_g2s(probe_smem + st * PROBE_CHUNK, src + c * PROBE_CHUNK, bytes, &bar[st], pol);
-    };
-    if (threadIdx.x == 0)
-        for (int st = 0; st < PROBE_STAGES; ++st) {
-            const int64_t c = blockIdx.x + (int64_t)st * gridDim.x;
-            if (c < n_chunks) issue(st, c);
-        }
-    double acc = 0.0;
-    int64_t it = 0;
-    for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x, ++it) {
-        const int st = (int)(it % PROBE_STAGES);
-        const uint32_t parity = (uint32_t)((it / PROBE_STAGES) & 1);
-        if (!__syncthreads_and(fe_mbar_wait(&bar[st], parity))) {
-            if (threadIdx.x == 0) atomicCAS(status, 0, FE_ERR_TIMEOUT);
-            for (int64_t k = it, cc = c; cc < n_chunks && k < it + PROBE_STAGES; ++k, cc += gridDim.x)
-                fe_mbar_wait(&bar[k % PROBE_STAGES], (uint32_t)((k / PROBE_STAGES) & 1));
-            return;
-        }
-        acc += ((const double *)(probe_smem + st * PROBE_CHUNK))[threadIdx.x];  // touch the stage
-        __syncthreads();
-        const int64_t cn = c + (int64_t)PROBE_STAGES * gridDim.x;
-        if (threadIdx.x == 0 && cn < n_chunks) issue(st, cn);
-    }
-    if (acc == 1.2345e300) *sink = acc;  // keeps the reads alive
-}
-
 template <typename T>
 int scan_impl(fe_ctx *ctx, const T *in, int64_t *out, int64_t n, cudaStream_t s)
 {
@@ -351,19 +281,18 @@ int fe_tune_set(fe_ctx *ctx, int knob, int value)
     if (!ctx || knob < 0 || knob >= FE_KNOB_COUNT) return FE_ERR_INVALID_ARG;
     int lo = 0, hi = 0;
     switch (knob) {
-    case FE_KNOB_GATHER_KERNEL: hi = 6; break;
+    case FE_KNOB_GATHER_KERNEL: hi = 2; break;
     case FE_KNOB_GATHER_BATCH: hi = 8; break;
     case FE_KNOB_GATHER_WARPS: hi = 8; break;
     case FE_KNOB_ATOMIC_KERNEL: hi = 2; break;
     case FE_KNOB_ATOMIC_WARPS: hi = 8; break;
-    case FE_KNOB_GATHER_STAGES: hi = 8; break;
     case FE_KNOB_LOCK_SPIN: hi = 24; break;
     case FE_KNOB_SPMV_LANES: hi = 16; break;
     default: return FE_ERR_INVALID_ARG;
     }
     if (value < lo || value > hi) return FE_ERR_INVALID_ARG;
     if (knob == FE_KNOB_GATHER_BATCH && value != 0 && value != 4 && value != 8) return FE_ERR_INVALID_ARG;
-    if (knob == FE_KNOB_GATHER_STAGES && value == 1) return FE_ERR_INVALID_ARG;
+    if (knob == 5) return FE_ERR_INVALID_ARG;  // reserved
     if (knob == FE_KNOB_LOCK_SPIN && value != 0 && value < 4) return FE_ERR_INVALID_ARG;
     if (knob == FE_KNOB_SPMV_LANES && value != 0 && value != 2 && value != 4 && value != 8 && value != 16)
         return FE_ERR_INVALID_ARG;
@@ -406,31 +335,6 @@ int fe_resident_blocks(const void *kernel, int threads, size_t smem)
 }
 
 extern "C" {
-
-int fe_hbm_probe(fe_ctx *ctx, const double *src, double *dst, int64_t n, void *stream)
-{
-    if (!ctx || !src || n < 2 || ((uintptr_t)src & 15u) || ((uintptr_t)dst & 15u)) return FE_ERR_INVALID_ARG;
-    DeviceGuard g(ctx->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    k_hbm_probe<<<ctx->num_sms * 8, 256, 0, s>>>((const double2 *)src, (double2 *)dst, n / 2, (double *)ctx->d_status + 1);
-    fe_note_launch();
-    FE_CUDA(cudaGetLastError());
-    return FE_OK;
-}
-
-int fe_hbm_probe_bulk(fe_ctx *ctx, const double *src, int64_t n, void *stream)
-{
-    if (!ctx || !src || n < 2 || (n & 1) || ((uintptr_t)src & 15u)) return FE_ERR_INVALID_ARG;
-    DeviceGuard g(ctx->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    const size_t smem = (size_t)PROBE_CHUNK * PROBE_STAGES;
-    FE_CUDA(cudaFuncSetAttribute(k_hbm_probe_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_hbm_probe_bulk<<<ctx->num_sms * 2, 128, smem, s>>>((const char *)src, n * 8, (double *)ctx->d_status + 1,
-                                                         ctx->d_status);
-    fe_note_launch();
-    FE_CUDA(cudaGetLastError());
-    return FE_OK;
-}
 
 int fe_device_status(fe_ctx *ctx, void *stream)
 {

@@ -20,13 +20,18 @@ struct Geo {
     int mask_words;
     int64_t nnz;    // values length (index checks of debug builds)
     int *status;    // the context's device status word
-    // per node incidence s, when built (non-uniform runs): the incidence's
-    // map_crac row offset and its element's run-start mask
-    const int32_t *inc_off = nullptr;
-    const uint32_t *inc_mask = nullptr;
+    // row starts of the block-map kernels: 0 from row_ptr (CSR), 1 from the
+    // value position of each row's first CRAC pair (the CRAC gather)
+    int crac_rows = 0;
 };
 
 __device__ __forceinline__ int64_t crac_row_base(const Geo &g, int64_t i) { return g.col_align[g.crac_ptr[i] + 1]; }
+
+// Start of row i in the values array, from the format the kernel was given.
+__device__ __forceinline__ int64_t row_start(const Geo &g, int64_t i)
+{
+    return g.crac_rows ? crac_row_base(g, i) : g.row_ptr[i];
+}
 
 // Run index of block kc and kc's offset inside that run, for run-start bits m
 // (kc < 32, bit 0 always set).
@@ -57,7 +62,7 @@ inline Geo geo_of(const fe_pattern *p)
 {
     return Geo{p->node_dofs, p->row_ptr,  p->crac_ptr, p->col_align, p->run_mask,
                p->run_ptr,   p->adj_ptr, p->adj,      p->uniform_runs ? p->runs_per_elem : 0, p->mask_words,
-               p->nnz,       p->ctx->d_status, p->inc_off, p->inc_mask};
+               p->nnz,       p->ctx->d_status, p->crac_rows ? 1 : 0};
 }
 
 // One element of NLN blocks of BB DOFs (NLN*BB <= 32), the warp cooperating:

@@ -45,8 +45,8 @@ __device__ __forceinline__ void gather_rows_small(const double *__restrict__ K, 
     int64_t rb = 0, RL = 0, a = 0, b = 0;
     if (row_ok) {
         if (!CRAC) {
-            rb = g.row_ptr[BB * v];
-            RL = g.row_ptr[BB * v + 1] - rb;
+            rb = row_start(g, BB * v);
+            RL = row_start(g, BB * v + 1) - rb;
         } else {
             rb = crac_row_base(g, BB * v);
             RL = crac_row_base(g, BB * v + 1) - rb;
@@ -87,9 +87,6 @@ __device__ __forceinline__ void gather_rows_small(const double *__restrict__ K, 
                     int k = ku, off = offu;
                     if (g.uniform_R) {
                         mb = (int64_t)t * g.uniform_R;  // e R NLN + kr R
-                    } else if (g.inc_off) {
-                        mb = g.inc_off[a + s0 + u];
-                        run_of(g.inc_mask[a + s0 + u], kc, k, off);
                     } else {
                         const int64_t rp = g.run_ptr[e];
                         mb = rp * NLN + (int64_t)kr * (g.run_ptr[e + 1] - rp);

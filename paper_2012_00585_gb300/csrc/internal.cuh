@@ -77,10 +77,12 @@ struct fe_pattern {
     uint32_t *run_mask = nullptr;  // [n_e * mask_words] run starts over the element's blocks
     int64_t *run_ptr = nullptr;    // [n_e + 1]
     void *map_crac = nullptr;      // [n_runs * nln] uint8/uint16: run start position in block row
-    // non-uniform runs, one mask word: per node incidence s (adjacency order),
-    // the offset of its row of map_crac and its element's run-start mask
-    int32_t *inc_off = nullptr;    // [n_e * nln]
-    uint32_t *inc_mask = nullptr;  // [n_e * nln]
+    // [n_e * nln * nln] uint8/uint16: the CRAC run map expanded to one entry
+    // per column block (run start + offset in the run), for the CRAC gather
+    void *map_crac_blk = nullptr;
+    // set only on a numeric-phase view of the pattern: row starts are read
+    // from the CRAC pairs (the CRAC gather through map_crac_blk)
+    bool crac_rows = false;
     struct fe_colouring *colouring = nullptr;  // greedy element colouring (fe_pattern_colour)
 };
 

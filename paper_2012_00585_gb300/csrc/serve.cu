@@ -81,15 +81,22 @@ struct CacheEntry {
     fe_pattern *p = nullptr;
     size_t bytes = 0;
     int refs = 0;
+    int64_t uses = 0;  // requests admitted on this key so far
     uint64_t last_use = 0;
     bool building = false;
 };
 
 struct Group {
     std::vector<uint64_t> ids;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t t0 = nullptr;    // recorded before the group's first kernel
+    cudaEvent_t done = nullptr;  // recorded after its last
     int stream = 0;
 };
+
+// Keys of evicted patterns remembered to count rebuilds (bounded).
+constexpr size_t EVICTED_KEYS_MAX = 1 << 20;
+// Device spans kept for fe_server_timeline (bounded).
+constexpr size_t TIMELINE_MAX = 1 << 21;
 
 }  // namespace
 
@@ -112,6 +119,9 @@ struct fe_server {
     bool stop = false;
     std::thread sched, builder;
     fe_server_stats stats{};
+    cudaEvent_t t_ref = nullptr;               // origin of the timeline (server start)
+    std::vector<fe_span> timeline;             // device spans of launched groups and builds
+    std::unordered_set<uint64_t> evicted_keys; // for the rebuild count
 };
 
 namespace {
@@ -129,32 +139,43 @@ size_t values_estimate(const fe_request &r, const fe_pattern *p)
     return (size_t)r.n_elem * r.dofs_per_elem * r.dofs_per_elem * 8;  // nnz <= entries
 }
 
-// Evict unreferenced cached patterns, least recently used first, until
-// `need` more bytes fit.  A pattern that a queued request will use is kept:
-// evicting it would only make that request rebuild it.  Caller holds the
-// lock.
+// Evict unreferenced cached patterns until `need` more bytes fit.  Victims
+// are taken among patterns no request holds and no queued request will use
+// (evicting one of those would only make that request rebuild it): patterns
+// used by a single request so far first (one-off meshes), then the rest,
+// least recently used first within each class, so that a stream of one-off
+// meshes does not push out the meshes that are reassembled again and again.
+// No request holds a victim, so none of its device work is in flight (a
+// request drops its hold only after its completion event was seen, and the
+// builder waits for each build): its memory is released stream-ordered on the
+// build stream, without a host wait under the lock.  Caller holds the lock.
 void evict_for(fe_server *sv, size_t need)
 {
     std::unordered_set<uint64_t> wanted;
     for (uint64_t id : sv->pending) wanted.insert(sv->tickets[id].req.pattern_key);
     while (sv->in_use + need > sv->budget) {
         uint64_t victim = 0;
-        uint64_t oldest = UINT64_MAX;
-        for (auto &kv : sv->cache)
-            if (kv.second.refs == 0 && !kv.second.building && kv.second.last_use < oldest &&
-                !wanted.count(kv.first)) {
-                oldest = kv.second.last_use;
+        bool found = false;
+        std::pair<int, uint64_t> best{2, UINT64_MAX};
+        for (auto &kv : sv->cache) {
+            const CacheEntry &ce = kv.second;
+            if (ce.refs != 0 || ce.building || wanted.count(kv.first)) continue;
+            const std::pair<int, uint64_t> rank{ce.uses > 1 ? 1 : 0, ce.last_use};
+            if (rank < best) {
+                best = rank;
                 victim = kv.first;
+                found = true;
             }
-        if (oldest == UINT64_MAX) return;
+        }
+        if (!found) return;
         CacheEntry ce = sv->cache[victim];
         sv->cache.erase(victim);
-        sv->in_use -= ce.bytes;
+        sv->in_use -= std::min(ce.bytes, sv->in_use);
         sv->cache_bytes -= std::min(ce.bytes, sv->cache_bytes);
         ++sv->stats.evictions;
-        cudaStreamSynchronize(sv->build_stream);
-        for (cudaStream_t s : sv->streams) cudaStreamSynchronize(s);
-        fe_pattern_free(ce.p);
+        if (sv->evicted_keys.size() >= EVICTED_KEYS_MAX) sv->evicted_keys.clear();
+        sv->evicted_keys.insert(victim);
+        fe_pattern_free_async(ce.p, sv->build_stream);
     }
 }
 
@@ -166,6 +187,61 @@ void finish(fe_server *sv, Ticket &t, int status)
     t.t_done = now_us();
     if (status == FE_OK) ++sv->stats.completed; else ++sv->stats.failed;
     sv->cv_done.notify_all();
+}
+
+// Device span [t0, t1] of completed work, in ms after the server's start.
+void record_span(fe_server *sv, cudaEvent_t t0, cudaEvent_t t1, int32_t stream, int32_t n_requests)
+{
+    float a = 0.f, b = 0.f;
+    if (sv->timeline.size() >= TIMELINE_MAX || !t0 || !t1) return;
+    if (cudaEventElapsedTime(&a, sv->t_ref, t0) != cudaSuccess || cudaEventElapsedTime(&b, sv->t_ref, t1) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    sv->timeline.push_back(fe_span{(double)a, (double)b, stream, n_requests});
+}
+
+bool expired(const Ticket &t, double now)
+{
+    return t.req.deadline_s > 0 && now > t.t_submit + t.req.deadline_s * 1e6;
+}
+
+// The watchdog: requests whose deadline passed before they were launched
+// fail with FE_ERR_TIMEOUT; those already admitted give their memory and
+// their hold on the cached pattern back.  Requests waiting for a pattern
+// build are checked when the build completes.  Caller holds the lock.
+bool expire_overdue(fe_server *sv)
+{
+    const double now = now_us();
+    bool any = false;
+    for (auto it = sv->pending.begin(); it != sv->pending.end();) {
+        Ticket &t = sv->tickets[*it];
+        if (t.state == FE_STATE_PENDING && expired(t, now)) {
+            ++sv->stats.expired;
+            finish(sv, t, FE_ERR_TIMEOUT);
+            it = sv->pending.erase(it);
+            any = true;
+        } else {
+            ++it;
+        }
+    }
+    for (auto it = sv->ready.begin(); it != sv->ready.end();) {
+        Ticket &t = sv->tickets[*it];
+        if (t.state == FE_STATE_ADMITTED && expired(t, now)) {
+            sv->in_use -= std::min(t.foot, sv->in_use);
+            t.foot = 0;
+            auto ce = sv->cache.find(t.req.pattern_key);
+            if (ce != sv->cache.end() && ce->second.refs > 0) ce->second.refs--;
+            t.pattern = nullptr;
+            ++sv->stats.expired;
+            finish(sv, t, FE_ERR_TIMEOUT);
+            it = sv->ready.erase(it);
+            any = true;
+        } else {
+            ++it;
+        }
+    }
+    return any;
 }
 
 // Admission, launches and completions; runs on the scheduler thread.
@@ -183,6 +259,7 @@ void scheduler_loop(fe_server *sv)
                 continue;
             }
             const int st = q == cudaSuccess ? FE_OK : FE_ERR_DEVICE;
+            if (st == FE_OK) record_span(sv, it->t0, it->done, it->stream, (int32_t)it->ids.size());
             for (uint64_t id : it->ids) {
                 Ticket &t = sv->tickets[id];
                 if (t.K) {
@@ -193,11 +270,13 @@ void scheduler_loop(fe_server *sv)
                 }
                 finish(sv, t, st);
             }
+            cudaEventDestroy(it->t0);
             cudaEventDestroy(it->done);
             it = sv->inflight.erase(it);
             progress = true;
             sv->cv_done.notify_all();
         }
+        if (expire_overdue(sv)) progress = true;
         // admission (arrival order)
         while (!sv->pending.empty()) {
             const uint64_t id = sv->pending.front();
@@ -233,6 +312,7 @@ void scheduler_loop(fe_server *sv)
             progress = true;
             if (cached) {
                 ce->second.refs++;
+                ce->second.uses++;
                 ce->second.last_use = ++sv->clock;
                 if (ce->second.building) {
                     sv->to_build.push_back(id);  // the builder hands it on when the pattern exists
@@ -244,6 +324,7 @@ void scheduler_loop(fe_server *sv)
                 CacheEntry &ne = sv->cache[t.req.pattern_key];
                 ne.building = true;
                 ne.refs = 1;
+                ne.uses = 1;
                 ne.last_use = ++sv->clock;
                 t.cold = 1;
                 sv->to_build.push_back(id);
@@ -258,6 +339,11 @@ void scheduler_loop(fe_server *sv)
             g.stream = sv->next_stream;
             sv->next_stream = (sv->next_stream + 1) % (int)sv->streams.size();
             cudaStream_t s = sv->streams[g.stream];
+            if (cudaEventCreate(&g.t0) != cudaSuccess || cudaEventRecord(g.t0, s) != cudaSuccess) {
+                cudaGetLastError();
+                if (g.t0) cudaEventDestroy(g.t0);
+                g.t0 = nullptr;
+            }
             std::vector<fe_batch_item> items;
             for (auto it = sv->ready.begin(); it != sv->ready.end() && (int)items.size() < sv->max_batch;) {
                 Ticket &t = sv->tickets[*it];
@@ -298,13 +384,17 @@ void scheduler_loop(fe_server *sv)
                 g.ids.push_back(*it);
                 it = sv->ready.erase(it);
             }
-            if (items.empty()) continue;
+            if (items.empty()) {
+                if (g.t0) cudaEventDestroy(g.t0);
+                continue;
+            }
             int rc = fe_assemble_batch(sv->ctx, items.data(), (int32_t)items.size(), fmt, mode, 0, nullptr, s);
-            if (rc == FE_OK && cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess) rc = FE_ERR_DEVICE;
+            if (rc == FE_OK && cudaEventCreate(&g.done) != cudaSuccess) rc = FE_ERR_DEVICE;
             if (rc == FE_OK && cudaEventRecord(g.done, s) != cudaSuccess) rc = FE_ERR_DEVICE;
             if (rc != FE_OK) {
                 for (uint64_t id : g.ids) finish(sv, sv->tickets[id], rc);
                 if (g.done) cudaEventDestroy(g.done);
+                if (g.t0) cudaEventDestroy(g.t0);
                 continue;
             }
             ++sv->stats.launches;
@@ -349,13 +439,21 @@ void builder_loop(fe_server *sv)
         const fe_request req = sv->tickets[id].req;
         lk.unlock();
         fe_pattern *p = nullptr;
+        cudaEvent_t b0 = nullptr, b1 = nullptr;
+        if (cudaEventCreate(&b0) != cudaSuccess || cudaEventCreate(&b1) != cudaSuccess) cudaGetLastError();
+        if (b0) cudaEventRecord(b0, sv->build_stream);
         int rc = fe_pattern_build(sv->ctx, req.n_elem, req.dofs_per_elem, req.n_dofs, req.elem_dofs, FE_PATTERN_ALL,
                                   sv->build_stream, &p);
+        if (b1) cudaEventRecord(b1, sv->build_stream);
         if (rc == FE_OK) rc = cudaStreamSynchronize(sv->build_stream) == cudaSuccess ? FE_OK : FE_ERR_DEVICE;
         lk.lock();
+        if (rc == FE_OK && b0 && b1) record_span(sv, b0, b1, -1, 1);
+        if (b0) cudaEventDestroy(b0);
+        if (b1) cudaEventDestroy(b1);
         Ticket &t = sv->tickets[id];
         CacheEntry &ce = sv->cache[req.pattern_key];
         ++sv->stats.patterns_built;
+        if (sv->evicted_keys.erase(req.pattern_key)) ++sv->stats.rebuilds;
         if (rc != FE_OK) {
             sv->in_use -= std::min(t.foot, sv->in_use);
             t.foot = 0;
@@ -447,8 +545,13 @@ int fe_server_start(fe_ctx *ctx, int32_t n_streams, int32_t max_batch, size_t hb
     }
     if (rc == FE_OK && cudaStreamCreateWithFlags(&sv->build_stream, cudaStreamNonBlocking) != cudaSuccess)
         rc = FE_ERR_DEVICE;
+    if (rc == FE_OK && (cudaEventCreate(&sv->t_ref) != cudaSuccess || cudaEventRecord(sv->t_ref, sv->streams[0]) != cudaSuccess ||
+                        cudaEventSynchronize(sv->t_ref) != cudaSuccess))
+        rc = FE_ERR_DEVICE;
     if (rc != FE_OK) {
         for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
+        if (sv->build_stream) cudaStreamDestroy(sv->build_stream);
+        if (sv->t_ref) cudaEventDestroy(sv->t_ref);
         delete sv;
         if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
         return rc;
@@ -476,7 +579,10 @@ int fe_server_stop(fe_server *sv)
     if (prev != sv->ctx->device) cudaSetDevice(sv->ctx->device);
     for (cudaStream_t s : sv->streams) cudaStreamSynchronize(s);
     cudaStreamSynchronize(sv->build_stream);
-    for (auto &g : sv->inflight) cudaEventDestroy(g.done);
+    for (auto &g : sv->inflight) {
+        cudaEventDestroy(g.done);
+        if (g.t0) cudaEventDestroy(g.t0);
+    }
     for (auto &kv : sv->tickets) {
         if (kv.second.values) cudaFreeAsync(kv.second.values, sv->streams[0]);
         if (kv.second.K) cudaFreeAsync(kv.second.K, sv->streams[0]);
@@ -486,6 +592,7 @@ int fe_server_stop(fe_server *sv)
         if (kv.second.p) fe_pattern_free(kv.second.p);
     for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
     cudaStreamDestroy(sv->build_stream);
+    cudaEventDestroy(sv->t_ref);
     const int dev = sv->ctx->device;
     delete sv;
     if (prev >= 0 && prev != dev) cudaSetDevice(prev);
@@ -497,7 +604,7 @@ int fe_batch_submit(fe_server *sv, const fe_request *reqs, int32_t n, uint64_t *
     if (!sv || n < 0 || (n > 0 && (!reqs || !tickets))) return FE_ERR_INVALID_ARG;
     for (int k = 0; k < n; ++k) {
         const fe_request &r = reqs[k];
-        if (r.n_elem < 0 || r.dofs_per_elem <= 0 || r.n_dofs < 0 || (!r.elem_mats && !r.k_ref) ||
+        if (r.n_elem < 0 || r.dofs_per_elem <= 0 || r.n_dofs < 0 || (!r.elem_mats && !r.k_ref) || !(r.deadline_s >= 0) ||
             (r.format != FE_FORMAT_CSR && r.format != FE_FORMAT_CRAC) ||
             (r.mode != FE_ATOMIC && r.mode != FE_DETERMINISTIC))
             return FE_ERR_INVALID_ARG;
@@ -585,6 +692,16 @@ int fe_server_stats_get(fe_server *sv, fe_server_stats *out)
     out->bytes_in_use = (int64_t)sv->in_use;
     out->budget_bytes = (int64_t)sv->budget;
     out->cached_patterns = (int64_t)sv->cache.size();
+    return FE_OK;
+}
+
+int fe_server_timeline(fe_server *sv, int64_t first, int64_t cap, fe_span *out, int64_t *n_total)
+{
+    if (!sv || first < 0 || cap < 0 || (cap > 0 && !out)) return FE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    const int64_t n = (int64_t)sv->timeline.size();
+    if (n_total) *n_total = n;
+    for (int64_t k = first; k < n && k - first < cap; ++k) out[k - first] = sv->timeline[k];
     return FE_OK;
 }
 

@@ -20,6 +20,7 @@
 #include <mutex>
 #include <utility>
 
+#include "assemble_body.cuh"
 #include "internal.cuh"
 
 namespace {
@@ -596,21 +597,36 @@ __global__ void k_map_runs(const int32_t *__restrict__ N, int32_t nln, int64_t n
     }
 }
 
-// Per node incidence s (t = adj[s] = e * nln + kr): the offset of the
-// incidence's row of element e's run map, run_ptr[e] * nln + kr * runs(e),
-// and e's run-start mask, laid out in adjacency order so that the CRAC
-// gather reads them with the incidence itself instead of after it.
-__global__ void k_inc_runs(const uint32_t *__restrict__ adj, int64_t n_inc, int32_t nln,
-                           const int64_t *__restrict__ run_ptr, const uint32_t *__restrict__ run_mask,
-                           int32_t *__restrict__ inc_off, uint32_t *__restrict__ inc_mask)
+// The CRAC run map expanded to one entry per column block: entry
+// (e, kr, kc) = run_start(e, kr, run of kc) + offset of kc in its run, i.e.
+// the position of block kc of element e in block row D_e(kr), located once
+// per run by the CRAC block search (§2.2) when the run map was built.  Uniform
+// runs: every element has element 0's mask and R runs.
+template <typename MT>
+__global__ void k_expand_run_map(int64_t n_e, int32_t nln, int32_t mask_words, const uint32_t *__restrict__ run_mask,
+                                 const int64_t *__restrict__ run_ptr, int32_t uniform_R, const MT *__restrict__ map_crac,
+                                 MT *__restrict__ blk)
 {
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_inc; s += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = adj[s];
-        const int64_t e = t / (uint32_t)nln;
+    const int64_t n = n_e * nln * nln;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = x / nln;  // e * nln + kr
+        const int kc = (int)(x - t * nln);
+        const int64_t e = t / nln;
         const int64_t kr = t - e * nln;
-        const int64_t rp = run_ptr[e];
-        inc_off[s] = (int32_t)(rp * nln + kr * (run_ptr[e + 1] - rp));
-        inc_mask[s] = run_mask[e];
+        int64_t rp, nr;
+        const uint32_t *m;
+        if (uniform_R) {
+            rp = e * uniform_R;
+            nr = uniform_R;
+            m = run_mask;
+        } else {
+            rp = run_ptr[e];
+            nr = run_ptr[e + 1] - rp;
+            m = run_mask + e * mask_words;
+        }
+        int k, off;
+        fe_dev::run_of_multi(m, kc, k, off);
+        blk[x] = (MT)(map_crac[rp * nln + kr * nr + k] + off);
     }
 }
 
@@ -629,7 +645,7 @@ void pattern_release(fe_pattern *p, cudaStream_t s)
 {
     fe_colouring_free(p, s);
     void *ptrs[] = {p->node_dofs, p->row_ptr, p->col_idx, p->crac_ptr, p->col_align, p->adj_ptr, p->adj,
-                    p->map_csr,   p->run_mask, p->run_ptr, p->map_crac, p->inc_off, p->inc_mask};
+                    p->map_csr,   p->run_mask, p->run_ptr, p->map_crac, p->map_crac_blk};
     for (void *x : ptrs) fe_free_async(x, s);
     delete p;
 }
@@ -864,15 +880,22 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
             FE_CUDA(cudaGetLastError());
         }
     }
-    // non-uniform runs of one mask word: the run tables in adjacency order
-    if ((p->flags & FE_PATTERN_MAP_CRAC) && !p->uniform_runs && p->mask_words == 1 && n_ninc > 0 &&
-        p->n_runs * nln < INT32_MAX) {
-        FE_TRY(alloc_into(p, (void **)&p->inc_off, sizeof(int32_t) * (size_t)n_ninc, s));
-        FE_TRY(alloc_into(p, (void **)&p->inc_mask, sizeof(uint32_t) * (size_t)n_ninc, s));
-        FE_LAUNCH((k_inc_runs<<<fe_grid_for(n_ninc, 256, sms, 16), 256, 0, s>>>(p->adj, n_ninc, nln, p->run_ptr,
-                                                                                 p->run_mask, p->inc_off,
-                                                                                 p->inc_mask)));
-        FE_CUDA(cudaGetLastError());
+    // the CRAC gather's block map, expanded from the run map
+    if (p->flags & FE_PATTERN_MAP_CRAC) {
+        FE_TRY(alloc_into(p, &p->map_crac_blk, (size_t)(n_ninc * nln + 1) * p->map_bytes, s));
+        if (n_ninc > 0) {
+            const int g = fe_grid_for(n_ninc * nln, 256, sms, 16);
+            const int uR = p->uniform_runs ? p->runs_per_elem : 0;
+            if (p->map_bytes == 1)
+                FE_LAUNCH((k_expand_run_map<uint8_t><<<g, 256, 0, s>>>(n_e, nln, p->mask_words, p->run_mask, p->run_ptr,
+                                                                       uR, (const uint8_t *)p->map_crac,
+                                                                       (uint8_t *)p->map_crac_blk)));
+            else
+                FE_LAUNCH((k_expand_run_map<uint16_t><<<g, 256, 0, s>>>(n_e, nln, p->mask_words, p->run_mask,
+                                                                        p->run_ptr, uR, (const uint16_t *)p->map_crac,
+                                                                        (uint16_t *)p->map_crac_blk)));
+            FE_CUDA(cudaGetLastError());
+        }
     }
     if (!(p->flags & FE_PATTERN_CRAC) && !(p->flags & FE_PATTERN_MAP_CRAC)) {
         // CRAC was only scaffolding for this pattern
@@ -1134,29 +1157,16 @@ int noalloc_impl(unsigned char *scratch, int64_t n_e, int32_t n_loc, int64_t n_d
     int dev = 0, sms = 0;
     FE_CUDA(cudaGetDevice(&dev));
     FE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // layout for the largest case (block size 1): every array sized by DOFs
+    // Only the status words are taken before validation; the other arrays are
+    // carved once the block size B (and so the node count) is known, so that
+    // blocked meshes (3 DOFs per node: keys B^2 = 9 times smaller) may use the
+    // whole array.  Every array that must start at zero is cleared here: the
+    // array keeps the previous call's contents.
     Bump bump{scratch, 0, FE_NOALLOC_SCRATCH_BYTES};
-    const int64_t n_inc = n_e * n_loc;
     int64_t *sc = (int64_t *)bump.take(sizeof(int64_t) * S_COUNT);
-    int32_t *deg = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_dofs + 1));
-    int32_t *runs = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_e + 1));
-    int32_t *N = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_inc + 1));
-    uint32_t *run_mask = (uint32_t *)bump.take(sizeof(uint32_t) * (size_t)(n_e * ((n_loc + 31) / 32) + 1));
-    int64_t *adj_ptr = (int64_t *)bump.take(sizeof(int64_t) * (size_t)(n_dofs + 1));
-    uint32_t *adj = (uint32_t *)bump.take(sizeof(uint32_t) * (size_t)(n_inc + 1));
-    int32_t *node_len = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_dofs + 1));
-    int32_t *node_runs2 = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_dofs + 1));
-    int32_t *keys = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_inc * n_loc + 1));
-    int64_t *nrp = (int64_t *)bump.take(sizeof(int64_t) * (size_t)(n_dofs + 1));
-    int64_t *ncp = (int64_t *)bump.take(sizeof(int64_t) * (size_t)(n_dofs + 1));
-    int64_t *crac_ptr = (int64_t *)bump.take(sizeof(int64_t) * (size_t)(n_dofs + 1));
-    int64_t *tile_sums = (int64_t *)bump.take(sizeof(int64_t) * (size_t)NS_TILE);
-    if (!tile_sums) return FE_ERR_UNSUPPORTED;  // mesh too large for the fixed scratch
-
-    // everything that must start at zero (the array keeps the last call's data)
+    if (!sc) return FE_ERR_UNSUPPORTED;
     FE_CUDA(cudaMemsetAsync(sc, 0, sizeof(int64_t) * S_COUNT, s));
     FE_CUDA(cudaMemsetAsync(sc + S_BLOCKS, 0xff, sizeof(int64_t), s));
-    FE_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)(n_dofs + 1), s));
 
     int64_t h[S_COUNT];
     if (n_e > 0) {
@@ -1183,6 +1193,22 @@ int noalloc_impl(unsigned char *scratch, int64_t n_e, int32_t n_loc, int64_t n_d
     const int32_t nln = n_loc / B;
     const int64_t n_nodes = n_dofs / B, n_ninc = n_e * nln;
     const int mw = (nln + 31) / 32;
+    int32_t *deg = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_nodes + 1));
+    int32_t *runs = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_e + 1));
+    int32_t *N = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_ninc + 1));
+    uint32_t *run_mask = (uint32_t *)bump.take(sizeof(uint32_t) * (size_t)(n_e * mw + 1));
+    int64_t *adj_ptr = (int64_t *)bump.take(sizeof(int64_t) * (size_t)(n_nodes + 1));
+    uint32_t *adj = (uint32_t *)bump.take(sizeof(uint32_t) * (size_t)(n_ninc + 1));
+    int32_t *node_len = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_nodes + 1));
+    int32_t *node_runs2 = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_nodes + 1));
+    int32_t *keys = (int32_t *)bump.take(sizeof(int32_t) * (size_t)(n_ninc * nln + 1));
+    int64_t *nrp = (int64_t *)bump.take(sizeof(int64_t) * (size_t)(n_nodes + 1));
+    int64_t *ncp = (int64_t *)bump.take(sizeof(int64_t) * (size_t)(n_nodes + 1));
+    int64_t *crac_ptr = (int64_t *)bump.take(sizeof(int64_t) * (size_t)(n_dofs + 1));
+    int64_t *tile_sums = (int64_t *)bump.take(sizeof(int64_t) * (size_t)NS_TILE);
+    // the bump only grows, so the last array failing means the mesh does not fit
+    if (!tile_sums) return FE_ERR_UNSUPPORTED;
+    FE_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)(n_nodes + 1), s));
     if (n_e > 0) {
         FE_LAUNCH((k_node_conn<<<fe_grid_for(n_e * 32, 256, sms, 16), 256, 0, s>>>(elem_dofs, n_e, n_loc, B, nln, mw, N,
                                                                                 run_mask, runs, deg, sc)));

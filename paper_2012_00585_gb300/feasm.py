@@ -45,7 +45,6 @@ FE_KNOB_GATHER_BATCH = 1
 FE_KNOB_GATHER_WARPS = 2
 FE_KNOB_ATOMIC_KERNEL = 3
 FE_KNOB_ATOMIC_WARPS = 4
-FE_KNOB_GATHER_STAGES = 5
 FE_KNOB_LOCK_SPIN = 6
 FE_KNOB_SPMV_LANES = 7
 FE_KNOB_COUNT = 8
@@ -111,7 +110,8 @@ class fe_request(ctypes.Structure):
     _fields_ = [("pattern_key", ctypes.c_uint64), ("n_elem", ctypes.c_int64), ("dofs_per_elem", ctypes.c_int32),
                 ("format", ctypes.c_int32), ("n_dofs", ctypes.c_int64), ("elem_dofs", ctypes.c_void_p),
                 ("elem_mats", ctypes.c_void_p), ("k_ref", ctypes.c_void_p), ("seed", ctypes.c_uint64),
-                ("mode", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ready_event", ctypes.c_void_p)]
+                ("mode", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ready_event", ctypes.c_void_p),
+                ("deadline_s", ctypes.c_double)]
 
 
 class fe_result(ctypes.Structure):
@@ -124,7 +124,13 @@ class fe_result(ctypes.Structure):
 class fe_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "admitted", "completed", "failed", "cancelled",
                                               "launches", "batched_requests", "patterns_built", "evictions",
-                                              "bytes_in_use", "budget_bytes", "cached_patterns")]
+                                              "bytes_in_use", "budget_bytes", "cached_patterns", "rebuilds",
+                                              "expired")]
+
+
+class fe_span(ctypes.Structure):
+    _fields_ = [("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double), ("stream", ctypes.c_int32),
+                ("n_requests", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -154,8 +160,6 @@ def load():
             "fe_debug_checks": (i, []),
             "fe_device_status": (i, [vp, vp]),
             "fe_tune_set": (i, [vp, i, i]),
-            "fe_hbm_probe": (i, [vp, vp, vp, i64, vp]),
-            "fe_hbm_probe_bulk": (i, [vp, vp, i64, vp]),
             "fe_tune_get": (i, [vp, i, ctypes.POINTER(i)]),
             "fe_pattern_build": (i, [vp, i64, i32, i64, vp, u32, vp, pp]),
             "fe_pattern_free": (i, [vp]),
@@ -188,6 +192,7 @@ def load():
             "fe_release": (i, [vp, ctypes.c_uint64]),
             "fe_server_stats_get": (i, [vp, ctypes.POINTER(fe_server_stats)]),
             "fe_generate_scaled": (i, [vp, vp, i32, i64, ctypes.c_uint64, vp, vp]),
+            "fe_server_timeline": (i, [vp, i64, i64, ctypes.POINTER(fe_span), ctypes.POINTER(i64)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -244,16 +249,6 @@ def fe_debug_checks() -> bool:
 def fe_device_status(ctx, stream=None) -> int:
     """First error recorded by a kernel since the last call (0 = none); clears it."""
     return int(load().fe_device_status(ctx, _stream(stream)))
-
-
-def fe_hbm_probe(ctx, src, dst=None, n=None, stream=None):
-    n = src.numel() if n is None else n
-    _check(load().fe_hbm_probe(ctx, _addr(src), _addr(dst), int(n), _stream(stream)), "fe_hbm_probe")
-
-
-def fe_hbm_probe_bulk(ctx, src, n=None, stream=None):
-    n = src.numel() if n is None else n
-    _check(load().fe_hbm_probe_bulk(ctx, _addr(src), int(n), _stream(stream)), "fe_hbm_probe_bulk")
 
 
 def fe_tune_set(ctx, knob: int, value: int):
@@ -435,7 +430,7 @@ def fe_server_stop(server):
 
 
 def make_request(pattern_key, elem_dofs, n_dofs, *, elem_mats=None, k_ref=None, seed=0, fmt=FE_FORMAT_CSR,
-                 mode=FE_DETERMINISTIC, ready_event=None):
+                 mode=FE_DETERMINISTIC, ready_event=None, deadline_s=0.0):
     """An fe_request for a device connectivity tensor [n_elem, n_loc]."""
     r = fe_request()
     r.pattern_key = int(pattern_key)
@@ -449,6 +444,7 @@ def make_request(pattern_key, elem_dofs, n_dofs, *, elem_mats=None, k_ref=None, 
     r.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     r.mode = int(mode)
     r.ready_event = None if ready_event is None else int(ready_event.cuda_event)
+    r.deadline_s = float(deadline_s)
     return r
 
 
@@ -487,6 +483,16 @@ def fe_server_stats_get(server):
     st = fe_server_stats()
     _check(load().fe_server_stats_get(server, ctypes.byref(st)), "fe_server_stats_get")
     return {name: getattr(st, name) for name, _ in fe_server_stats._fields_}
+
+
+def fe_server_timeline(server):
+    """The server's device spans as a list of (start_ms, end_ms, stream,
+    n_requests); stream -1 marks a pattern build."""
+    n = ctypes.c_int64()
+    _check(load().fe_server_timeline(server, 0, 0, None, ctypes.byref(n)), "fe_server_timeline")
+    buf = (fe_span * max(n.value, 1))()
+    _check(load().fe_server_timeline(server, 0, n.value, buf, ctypes.byref(n)), "fe_server_timeline")
+    return [(buf[k].start_ms, buf[k].end_ms, buf[k].stream, buf[k].n_requests) for k in range(min(n.value, len(buf)))]
 
 
 def fe_generate_scaled(ctx, k_ref, n_loc, n_elem, seed, out, stream=None):

@@ -420,17 +420,16 @@ def test_c3_full_size_sampled_rows(ctx):
     g.free()
 
 
-@pytest.mark.parametrize("gkind", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("gkind", [1, 2])
 @pytest.mark.parametrize("akind", [1, 2])
 def test_every_kernel_variant(ctx, gkind, akind):
     """Each schedule knob value gives the same results: deterministic
-    variants bit-exact, atomic variants within the row tolerance; meshes with
-    rows of more than 8 incidences (tets) exercise the unstaged remainder."""
+    variants bit-exact, atomic variants within the row tolerance (gather
+    kernel 2 applies to the shapes with slices of at most 16 entries; the
+    others take kernel 1)."""
     from paper_2012_00585_gb300 import feasm
     feasm.fe_tune_set(ctx, feasm.FE_KNOB_GATHER_KERNEL, gkind)
     feasm.fe_tune_set(ctx, feasm.FE_KNOB_ATOMIC_KERNEL, akind)
-    # the bulk-copy gather with a 2-stage ring (more refills per row) when paired with akind 1
-    feasm.fe_tune_set(ctx, feasm.FE_KNOB_GATHER_STAGES, 2 if akind == 1 else 0)
     try:
         for D, n_dofs, K in [
             (*wl.hex_q1_grid(5, 3), None),
@@ -448,7 +447,6 @@ def test_every_kernel_variant(ctx, gkind, akind):
     finally:
         feasm.fe_tune_set(ctx, feasm.FE_KNOB_GATHER_KERNEL, 0)
         feasm.fe_tune_set(ctx, feasm.FE_KNOB_ATOMIC_KERNEL, 0)
-        feasm.fe_tune_set(ctx, feasm.FE_KNOB_GATHER_STAGES, 0)
 
 
 @pytest.mark.parametrize("fmt", ["csr", "crac"])
