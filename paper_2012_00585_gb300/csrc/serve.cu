@@ -111,13 +111,15 @@ struct fe_server {
     size_t budget = 0, in_use = 0;
     size_t cache_bytes = 0;  // bytes of the built patterns in the cache (part of in_use)
     std::vector<cudaStream_t> streams;
-    cudaStream_t build_stream = nullptr;
+    cudaStream_t build_stream = nullptr;       // = build_streams[0]; evicted patterns are freed on it
+    std::vector<cudaStream_t> build_streams;   // one per builder thread
     int next_stream = 0, max_batch = 64;
     uint64_t next_id = 1, clock = 0;
     int active = 0;            // admitted and not finished
     bool strict_fifo = false;  // one request at a time, end to end
     bool stop = false;
-    std::thread sched, builder;
+    std::thread sched;
+    std::vector<std::thread> builders;
     fe_server_stats stats{};
     cudaEvent_t t_ref = nullptr;               // origin of the timeline (server start)
     std::vector<fe_span> timeline;             // device spans of launched groups and builds
@@ -408,8 +410,13 @@ void scheduler_loop(fe_server *sv)
 
 // Cold requests: build the pattern, publish it in the cache, pass the
 // request (and any that waited for the same key) on to the ready queue.
-void builder_loop(fe_server *sv)
+// Several builder threads, each on its own stream, so that the builds of
+// different meshes (each waits on the host to size its arrays) overlap.
+constexpr int N_BUILDERS = 2;
+
+void builder_loop(fe_server *sv, int idx)
 {
+    cudaStream_t bs = sv->build_streams[idx];
     cudaSetDevice(sv->ctx->device);
     std::unique_lock<std::mutex> lk(sv->mu);
     while (!sv->stop) {
@@ -441,11 +448,11 @@ void builder_loop(fe_server *sv)
         fe_pattern *p = nullptr;
         cudaEvent_t b0 = nullptr, b1 = nullptr;
         if (cudaEventCreate(&b0) != cudaSuccess || cudaEventCreate(&b1) != cudaSuccess) cudaGetLastError();
-        if (b0) cudaEventRecord(b0, sv->build_stream);
+        if (b0) cudaEventRecord(b0, bs);
         int rc = fe_pattern_build(sv->ctx, req.n_elem, req.dofs_per_elem, req.n_dofs, req.elem_dofs, FE_PATTERN_ALL,
-                                  sv->build_stream, &p);
-        if (b1) cudaEventRecord(b1, sv->build_stream);
-        if (rc == FE_OK) rc = cudaStreamSynchronize(sv->build_stream) == cudaSuccess ? FE_OK : FE_ERR_DEVICE;
+                                  bs, &p);
+        if (b1) cudaEventRecord(b1, bs);
+        if (rc == FE_OK) rc = cudaStreamSynchronize(bs) == cudaSuccess ? FE_OK : FE_ERR_DEVICE;
         lk.lock();
         if (rc == FE_OK && b0 && b1) record_span(sv, b0, b1, -1, 1);
         if (b0) cudaEventDestroy(b0);
@@ -543,21 +550,25 @@ int fe_server_start(fe_ctx *ctx, int32_t n_streams, int32_t max_batch, size_t hb
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) rc = FE_ERR_DEVICE;
         else sv->streams.push_back(s);
     }
-    if (rc == FE_OK && cudaStreamCreateWithFlags(&sv->build_stream, cudaStreamNonBlocking) != cudaSuccess)
-        rc = FE_ERR_DEVICE;
+    for (int k = 0; k < N_BUILDERS && rc == FE_OK; ++k) {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) rc = FE_ERR_DEVICE;
+        else sv->build_streams.push_back(s);
+    }
+    if (rc == FE_OK) sv->build_stream = sv->build_streams[0];
     if (rc == FE_OK && (cudaEventCreate(&sv->t_ref) != cudaSuccess || cudaEventRecord(sv->t_ref, sv->streams[0]) != cudaSuccess ||
                         cudaEventSynchronize(sv->t_ref) != cudaSuccess))
         rc = FE_ERR_DEVICE;
     if (rc != FE_OK) {
         for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
-        if (sv->build_stream) cudaStreamDestroy(sv->build_stream);
+        for (cudaStream_t s : sv->build_streams) cudaStreamDestroy(s);
         if (sv->t_ref) cudaEventDestroy(sv->t_ref);
         delete sv;
         if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
         return rc;
     }
     sv->sched = std::thread(scheduler_loop, sv);
-    sv->builder = std::thread(builder_loop, sv);
+    for (int k = 0; k < N_BUILDERS; ++k) sv->builders.emplace_back(builder_loop, sv, k);
     *out = sv;
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
     return FE_OK;
@@ -573,12 +584,12 @@ int fe_server_stop(fe_server *sv)
     sv->cv.notify_all();
     sv->cv_build.notify_all();
     sv->sched.join();
-    sv->builder.join();
+    for (auto &t : sv->builders) t.join();
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != sv->ctx->device) cudaSetDevice(sv->ctx->device);
     for (cudaStream_t s : sv->streams) cudaStreamSynchronize(s);
-    cudaStreamSynchronize(sv->build_stream);
+    for (cudaStream_t s : sv->build_streams) cudaStreamSynchronize(s);
     for (auto &g : sv->inflight) {
         cudaEventDestroy(g.done);
         if (g.t0) cudaEventDestroy(g.t0);
@@ -591,7 +602,7 @@ int fe_server_stop(fe_server *sv)
     for (auto &kv : sv->cache)
         if (kv.second.p) fe_pattern_free(kv.second.p);
     for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
-    cudaStreamDestroy(sv->build_stream);
+    for (cudaStream_t s : sv->build_streams) cudaStreamDestroy(s);
     cudaEventDestroy(sv->t_ref);
     const int dev = sv->ctx->device;
     delete sv;
