@@ -212,29 +212,23 @@ int64_t or_crac_from_csr(int64_t n_rows, int64_t n_cols, const int64_t *row_ptr,
 }
 
 /*
- * Linear block search in CRAC, Listing 1.  Starting at the row's first pair,
- * step over pairs two ints at a time while the next block in the same row
- * starts at or before column c; then test whether c lies in the block that
- * was reached.  Block length = (next pair's value position) - (this pair's
- * value position).  The loop stays inside the row (the listing's bound,
- * "while i < row_end", would read the next row's pair at the row's last
- * block; the walk-through in §2.2 says that the last block of the row is
- * taken).  Returns the position in the values array, or -1 on a miss.
+ * Value position of column c in row `row` of a CRAC matrix, from the
+ * format's definition (§2.2, Fig. 1d).  The row's pairs (first column f_k,
+ * value position p_k) describe its runs of consecutive columns: run k covers
+ * the columns f_k .. f_k + (p_{k+1} - p_k) - 1, p_{k+1} being the value
+ * position of the pair that follows (for the row's last run, the next row's
+ * first pair or the final pair).  Column c sits at p_k + (c - f_k) in the run
+ * that covers it; -1 when no run of the row covers c.  Runs are sorted and
+ * disjoint, so this is the run the paper's block search stops at (the last
+ * run of the row that starts at or before c).
  */
 int64_t or_crac_lookup(const int64_t *crac_ptr, const int32_t *col_align, int64_t row, int32_t c)
 {
-    int64_t i = crac_ptr[row];
-    int64_t row_end = crac_ptr[row + 1];
-    if (i >= row_end) return -1; /* empty row */
-    while (i + 2 < row_end) {
-        if (col_align[i + 2] > c) break;
-        i += 2;
+    for (int64_t k = crac_ptr[row]; k < crac_ptr[row + 1]; k += 2) {
+        int64_t first = col_align[k];
+        int64_t len = (int64_t)col_align[k + 3] - col_align[k + 1];
+        if (c >= first && c < first + len) return col_align[k + 1] + (c - first);
     }
-    int64_t col_start = col_align[i];
-    int64_t val_start = col_align[i + 1];
-    int64_t val_end = col_align[i + 3];
-    int64_t col_end = col_start + (val_end - val_start);
-    if (c >= col_start && c < col_end) return val_start + (c - col_start);
     return -1;
 }
 

@@ -33,8 +33,8 @@ MUTANTS = [
      "for (int64_t t = 0; t < n_e; ++t) {", "for (int64_t t = 1; t < n_e; ++t) {"),
     ("row_candidates_not_deduplicated",
      "if (buf[k] != buf[w - 1]) buf[w++] = buf[k];", "buf[w++] = buf[k];"),
-    ("listing1_literal_loop_bound",
-     "while (i + 2 < row_end) {", "while (i < row_end) {"),
+    ("crac_lookup_skips_last_run",
+     "k < crac_ptr[row + 1]; k += 2)", "k + 2 < crac_ptr[row + 1]; k += 2)"),
     ("final_pair_column_off_by_one",
      "ca[w++] = (int32_t)n_cols;", "ca[w++] = (int32_t)(n_cols - 1);"),
     ("run_offset_dropped_in_crac_assembly",
