@@ -998,12 +998,13 @@ def serve_trace(ctx, traffic, arrivals, kinds, n_streams, max_batch, warm_s=0.0,
     """Serve one trace on a fresh server (n_streams streams, at most
     max_batch requests per launch; 1 and 1 = strict FIFO), deterministic
     CSR mode.  The cache is warmed first with one request per mesh class
-    (untimed).  Latency = submission to completion (the server's clock).
-    Requests arriving before warm_s are served but not counted.  With
-    verify > 0, that many completed requests (spread over the trace, the
-    first large ones included) are kept and compared after the trace, bit for
-    bit, with a standalone pattern build and single-mesh assembly of the same
-    element values."""
+    (untimed).  Latency = scheduled arrival to completion; requests due at
+    the same moment are submitted in one call.  Requests arriving before
+    warm_s are served but not counted.  With verify > 0, that many completed
+    requests (spread over the trace, the first large ones included) are kept
+    and compared after the trace, bit for bit, with a standalone pattern build
+    and single-mesh assembly of the same element values."""
+    import sys
     import threading
 
     fe = traffic.fe
@@ -1038,22 +1039,39 @@ def serve_trace(ctx, traffic, arrivals, kinds, n_streams, max_batch, warm_s=0.0,
                 fe.fe_release(sv, tickets[k])
         done.set()
 
-    th = threading.Thread(target=collect)
-    th.start()
     cold_key = 1 << 40
-    t0 = time.perf_counter()
+    reqs = []
     for k, ((n, d), is_large, is_warm) in enumerate(kinds):
-        gap = arrivals[k] - (time.perf_counter() - t0)
-        if gap > 0.002:
-            time.sleep(gap - 0.001)  # leave the interpreter to the collector meanwhile
-        while time.perf_counter() - t0 < arrivals[k]:
-            pass
         Dd, Krd, n_dofs, _ = traffic.classes[(n, d)]
         key = hot[(n, d)] if is_warm else cold_key + seed_base + k
-        tickets[k] = fe.fe_batch_submit(sv, [fe.make_request(key, Dd, n_dofs, k_ref=Krd, seed=seed_base + k,
-                                                              mode=fe.FE_DETERMINISTIC)])[0]
-    t_last_arrival = time.perf_counter() - t0
+        reqs.append(fe.make_request(key, Dd, n_dofs, k_ref=Krd, seed=seed_base + k, mode=fe.FE_DETERMINISTIC))
+    switch = sys.getswitchinterval()
+    sys.setswitchinterval(2e-4)  # the collector thread gets the interpreter back quickly
+    th = threading.Thread(target=collect)
+    th.start()
+    # the player submits every request whose arrival time has come, in one
+    # call; latencies are taken from the scheduled arrival (time.perf_counter
+    # and the server's clock are both CLOCK_MONOTONIC), so a player that falls
+    # behind cannot hide queueing
+    t0 = time.perf_counter()
+    k = 0
+    lag = 0.0
+    while k < m:
+        now = time.perf_counter() - t0
+        if now < arrivals[k]:
+            if arrivals[k] - now > 0.002:
+                time.sleep(arrivals[k] - now - 0.001)
+            continue
+        j = k
+        while j < m and arrivals[j] <= now:
+            j += 1
+        ts = fe.fe_batch_submit(sv, reqs[k:j])
+        lag = max(lag, time.perf_counter() - t0 - arrivals[k])
+        for i, t in enumerate(ts):
+            tickets[k + i] = t
+        k = j
     done.wait()
+    sys.setswitchinterval(switch)
     th.join()
     st = fe.fe_server_stats_get(sv)
     spans = fe.fe_server_timeline(sv)[spans0:]
@@ -1091,16 +1109,18 @@ def serve_trace(ctx, traffic, arrivals, kinds, n_streams, max_batch, warm_s=0.0,
 
     ok = [k for k in range(m) if res[k] and res[k][0] == fe.FE_STATE_DONE]
     cnt = [k for k in ok if arrivals[k] >= warm_s]
-    lat = [(res[k][3] - res[k][1]) * 1e-3 for k in cnt]
+    t0_us = t0 * 1e6
+    arr_us = lambda k: t0_us + arrivals[k] * 1e6  # scheduled arrival on the server's clock
+    lat = [(res[k][3] - arr_us(k)) * 1e-3 for k in cnt]
     asm = [(res[k][3] - res[k][2]) * 1e-3 for k in cnt]
-    sel = lambda f: [(res[k][3] - res[k][1]) * 1e-3 for k in cnt if f(kinds[k])]
-    first_submit = min(res[k][1] for k in cnt) if cnt else 0.0
+    sel = lambda f: [(res[k][3] - arr_us(k)) * 1e-3 for k in cnt if f(kinds[k])]
+    first_arrival = min(arr_us(k) for k in cnt) if cnt else 0.0
     last_done = max(res[k][3] for k in ok) if ok else 0.0
-    window_s = (last_done - first_submit) * 1e-6
-    drain_s = (last_done - res[m - 1][1]) * 1e-6 if ok and res[m - 1] else None
+    window_s = (last_done - first_arrival) * 1e-6
+    drain_s = (last_done - arr_us(m - 1)) * 1e-6 if ok else None
     q = max(1, len(cnt) // 5)
     head, tail = lat[:q], lat[-q:]
-    keeps_pace = bool(len(ok) == m and drain_s is not None and drain_s < 1.0 and len(cnt) >= 10 and
+    keeps_pace = bool(len(ok) == m and drain_s is not None and drain_s < 0.5 and len(cnt) >= 10 and
                       _pct(tail, 90) <= 2 * _pct(head, 90) + 50.0)
     ent = sum(traffic.classes[kinds[k][0]][3] for k in cnt)
     overlap, busy_ms = _overlap(spans)
@@ -1113,6 +1133,7 @@ def serve_trace(ctx, traffic, arrivals, kinds, n_streams, max_batch, warm_s=0.0,
            "assembly_p50_ms": _pct(asm, 50), "assembly_p99_ms": _pct(asm, 99),
            "Gentries_per_s": round(ent / window_s / 1e9, 2) if window_s > 0 else None,
            "drain_s": round(drain_s, 3) if drain_s is not None else None, "keeps_pace": keeps_pace,
+           "player_max_lag_ms": round(lag * 1e3, 3),
            "launches": st["launches"] - st0["launches"],
            "requests_per_launch": round((st["batched_requests"] - st0["batched_requests"]) /
                                         max(1, st["launches"] - st0["launches"]), 2),
@@ -1144,7 +1165,7 @@ def served_block(ctx, fe, dev, quick=False):
     traffic = ServedTraffic(fe, dev)
     out = {"workload": "Poisson arrivals; 90% hex n~logU[8,48] (half Q1 Laplace d=1, half Q1 elasticity d=3), "
                        "10% 128^3 Q1 elasticity; 80% warm pattern; fresh K per request generated on the device; "
-                       "deterministic CSR; latency = submission to completion",
+                       "deterministic CSR; latency = scheduled arrival to completion",
            "continuous": {"streams": CONT[0], "max_batch": CONT[1]}, "fifo": "one request at a time"}
     arr, kinds = traffic.trace(2000.0, 0.5 if quick else 1.0, seed=11)
     c = serve_trace(ctx, traffic, arr, kinds, *CONT, verify=8)

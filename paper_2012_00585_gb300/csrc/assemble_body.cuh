@@ -172,14 +172,33 @@ __device__ __forceinline__ void atomic_element_generic(const double *__restrict_
     __syncwarp();
 }
 
-// One node row v (its BB DOF rows, contiguous in values), the warp
-// cooperating: incidences in ascending element order, U at a time loaded to
-// registers, added into acc (shared, >= BB * row length doubles), written
-// once.  Bit-identical to the sequential sum.
+// Start of node row v in values, its first DOF row's length and its
+// adjacency range: what gather_row needs before its first load.
+template <int BB, bool CRAC>
+__device__ __forceinline__ void gather_row_head(const Geo &g, int64_t v, int64_t &rb, int64_t &RL, int64_t &a,
+                                                int64_t &b)
+{
+    const int64_t i0 = (int64_t)BB * v;
+    if (!CRAC) {
+        rb = g.row_ptr[i0];
+        RL = g.row_ptr[i0 + 1] - rb;
+    } else {
+        rb = crac_row_base(g, i0);
+        RL = crac_row_base(g, i0 + 1) - rb;
+    }
+    a = g.adj_ptr[v];
+    b = g.adj_ptr[v + 1];
+}
+
+// One node row (its BB DOF rows, contiguous in values from rb, each RL long;
+// incidences adj[a, b)), the warp cooperating: incidences in ascending
+// element order, U at a time loaded to registers, added into acc (shared,
+// >= BB * row length doubles), written once.  Bit-identical to the
+// sequential sum.
 template <int NLN, int BB, typename MT, bool CRAC, int U>
-__device__ __forceinline__ void gather_row(const double *__restrict__ K, int64_t v, const Geo &g,
-                                           const MT *__restrict__ map, const MT *__restrict__ mapc, double *acc,
-                                           int accumulate, double *values, int lane)
+__device__ __forceinline__ void gather_row(const double *__restrict__ K, const Geo &g, const MT *__restrict__ map,
+                                           const MT *__restrict__ mapc, double *acc, int accumulate, double *values,
+                                           int lane, int64_t rb, int64_t RL, int64_t a, int64_t b)
 {
     constexpr int NLOC = NLN * BB;
     constexpr int NN = NLOC * NLOC;
@@ -196,20 +215,10 @@ __device__ __forceinline__ void gather_row(const double *__restrict__ K, int64_t
         offu[j] = 0;
         if (CRAC && g.uniform_R) run_of(g.run_mask[0], c_[j] / BB, ku[j], offu[j]);
     }
-    const int64_t i0 = (int64_t)BB * v;
-    int64_t rb, RL;
-    if (!CRAC) {
-        rb = g.row_ptr[i0];
-        RL = g.row_ptr[i0 + 1] - rb;
-    } else {
-        rb = crac_row_base(g, i0);
-        RL = crac_row_base(g, i0 + 1) - rb;
-    }
     const int total = (int)(BB * RL);
     if (total > 0 && !FE_IN_BOUNDS(rb + total - 1, g.nnz, g.status)) return;
     for (int k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
     __syncwarp();
-    const int64_t a = g.adj_ptr[v], b = g.adj_ptr[v + 1];
     for (int64_t s0 = a; s0 < b; s0 += U) {
         double kv[U][IT];
         int rel[U][IT];

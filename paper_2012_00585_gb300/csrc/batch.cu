@@ -209,7 +209,8 @@ __device__ __noinline__ void gather_tile_small(const BatchItemDev *__restrict__ 
 }
 
 // The node rows [u0, u1) of an item with a specialised shape, one call per
-// tile (the item's geometry is read once per tile, not once per row).
+// tile (the item's geometry is read once per tile, not once per row); each
+// row's start and adjacency range are loaded one row ahead.
 template <int NLN, int BB, typename MT, bool CRAC>
 __device__ __noinline__ void gather_tile_node(const BatchItemDev *__restrict__ it, int64_t u0, int64_t u1,
                                               double *acc, int accumulate, int lane)
@@ -218,8 +219,17 @@ __device__ __noinline__ void gather_tile_node(const BatchItemDev *__restrict__ i
     const double *K = it->K;
     double *values = it->values;
     const MT *map = (const MT *)it->map, *mapc = (const MT *)it->mapc;
-    for (int64_t v = u0; v < u1; ++v)
-        gather_row<NLN, BB, MT, CRAC, 4>(K, v, g, map, mapc, acc, accumulate, values, lane);
+    int64_t rb, RL, a, b;
+    gather_row_head<BB, CRAC>(g, u0, rb, RL, a, b);
+    for (int64_t v = u0; v < u1; ++v) {
+        int64_t nrb = 0, nRL = 0, na = 0, nb = 0;
+        if (v + 1 < u1) gather_row_head<BB, CRAC>(g, v + 1, nrb, nRL, na, nb);
+        gather_row<NLN, BB, MT, CRAC, 4>(K, g, map, mapc, acc, accumulate, values, lane, rb, RL, a, b);
+        rb = nrb;
+        RL = nRL;
+        a = na;
+        b = nb;
+    }
 }
 
 template <typename MT, bool CRAC>
@@ -289,7 +299,7 @@ __host__ __device__ constexpr size_t batch_tables_bytes(int warps)
 constexpr int sched_threads(int) { return SCHED_THREADS; }
 
 template <bool CRAC, int SCHED>
-__global__ void __launch_bounds__(SCHED_THREADS) k_batch(const BatchItemDev *__restrict__ items, int n_items,
+__global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW ? 4 : 1) k_batch(const BatchItemDev *__restrict__ items, int n_items,
                                                          int64_t total_tiles, int tile, int cap, int accumulate,
                                                          unsigned long long *counter, int stage, int *status)
 {
@@ -672,6 +682,7 @@ int fe_assemble_batch(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, 
         (accumulate != 0 && accumulate != 1))
         return FE_ERR_INVALID_ARG;
     if (n_items == 0) return FE_OK;
+    FeRange range("fe_assemble_batch");
     DeviceScope ds(ctx->device);
     fe_schedule sc = default_schedule(mode);
     if (sched) {

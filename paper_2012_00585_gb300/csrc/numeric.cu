@@ -741,12 +741,14 @@ extern "C" {
 int fe_assemble_csr(fe_ctx *ctx, const fe_pattern *p, const double *elem_mats, double *values, int mode,
                     int accumulate, void *stream)
 {
+    FeRange range("fe_assemble_csr");
     return assemble(ctx, p, elem_mats, values, mode, accumulate, stream, false);
 }
 
 int fe_assemble_crac(fe_ctx *ctx, const fe_pattern *p, const double *elem_mats, double *values, int mode,
                      int accumulate, void *stream)
 {
+    FeRange range("fe_assemble_crac");
     return assemble(ctx, p, elem_mats, values, mode, accumulate, stream, true);
 }
 

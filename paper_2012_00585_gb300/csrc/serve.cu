@@ -390,6 +390,7 @@ void scheduler_loop(fe_server *sv)
                 if (g.t0) cudaEventDestroy(g.t0);
                 continue;
             }
+            FeRange range("serve: batched launch");
             int rc = fe_assemble_batch(sv->ctx, items.data(), (int32_t)items.size(), fmt, mode, 0, nullptr, s);
             if (rc == FE_OK && cudaEventCreate(&g.done) != cudaSuccess) rc = FE_ERR_DEVICE;
             if (rc == FE_OK && cudaEventRecord(g.done, s) != cudaSuccess) rc = FE_ERR_DEVICE;
@@ -446,6 +447,7 @@ void builder_loop(fe_server *sv, int idx)
         const fe_request req = sv->tickets[id].req;
         lk.unlock();
         fe_pattern *p = nullptr;
+        FeRange range("serve: pattern build");
         cudaEvent_t b0 = nullptr, b1 = nullptr;
         if (cudaEventCreate(&b0) != cudaSuccess || cudaEventCreate(&b1) != cudaSuccess) cudaGetLastError();
         if (b0) cudaEventRecord(b0, bs);

@@ -686,6 +686,7 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
     FE_CUDA(cudaMemsetAsync(sc + S_BLOCKS, 0xff, sizeof(int64_t), s));
 
     // A1: validation and block size
+    FePhase ph("A1 validate");
     if (n_e > 0) {
         uint32_t cand = 0;  // block sizes that divide both n_loc and n_dofs
         for (int b = 2; b <= 32; ++b)
@@ -719,6 +720,7 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
     p->mask_words = (nln + 31) / 32;
 
     // A2: block connectivity, runs, degrees
+    ph.next("A2 adjacency");
     int32_t *deg = nullptr, *runs = nullptr;
     FE_TRY(fe_alloc(ctx, (void **)&deg, sizeof(int32_t) * (size_t)(n_nodes + 1), s));
     tmp.add(deg);
@@ -754,6 +756,7 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
     p->uniform_runs = (h2[S_NONUNIFORM] == 0) && n_e > 0;
     p->runs_per_elem = n_e > 0 ? (int32_t)(p->n_runs / n_e) : 0;
 
+    ph.next("A3-A4 rows, CSR and CRAC");
     // A3: sorted distinct blocks of every node row (kept in `keys` at the
     // row's candidate offset adj_ptr[v]*nln), lengths and runs
     int32_t *node_len = nullptr, *node_runs2 = nullptr, *keys = nullptr;
@@ -839,6 +842,7 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
     FE_CUDA(cudaGetLastError());
 
     // A5: slot maps
+    ph.next("A5 slot maps");
     const int WM = 8;
     if (p->flags & FE_PATTERN_MAP_CSR) {
         FE_TRY(alloc_into(p, &p->map_csr, (size_t)(n_ninc * nln + 1) * p->map_bytes, s));
@@ -921,6 +925,7 @@ int fe_pattern_build(fe_ctx *ctx, int64_t n_elem, int32_t dofs_per_elem, int64_t
     if (dofs_per_elem > FE_MAX_NLOC) return FE_ERR_UNSUPPORTED;
     if (n_dofs >= INT32_MAX) return FE_ERR_OVERFLOW;
     if (n_elem * (int64_t)dofs_per_elem >= (int64_t)UINT32_MAX) return FE_ERR_OVERFLOW;
+    FeRange range("fe_pattern_build");
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != ctx->device) cudaSetDevice(ctx->device);
