@@ -99,7 +99,8 @@ typedef struct fe_pattern_info {
                               every element lists whole blocks
                               B*node .. B*node+B-1 (1 = no blocking)       */
     int32_t uniform_runs;  /* 1 when all elements share one run layout     */
-    int32_t reserved;
+    int32_t atomic_order;  /* 1 when FE_ATOMIC takes the elements in a
+                              locality order (FE_KNOB_ATOMIC_ORDER)        */
     int64_t device_bytes;  /* device memory held by the pattern            */
 } fe_pattern_info;
 
@@ -161,7 +162,12 @@ int fe_debug_checks(void);
 #define FE_KNOB_ATOMIC_KERNEL 3  /* FE_ATOMIC: 1 register warp-per-element,
                                     2 bulk-copy (TMA) staged warp-per-element */
 #define FE_KNOB_ATOMIC_WARPS 4   /* warps per block of the staged kernel     */
-/* knob 5 is reserved */
+#define FE_KNOB_ATOMIC_ORDER 5   /* read by fe_pattern_build: the element
+                                    order of the FE_ATOMIC scatter.  0 auto
+                                    (a locality order when the values exceed
+                                    256 MB and the numbering is scattered),
+                                    1 always ascending, 2 always the locality
+                                    order (clusters of the block graph)      */
 #define FE_KNOB_SPMV_LANES 7     /* lanes per row of fe_spmv_*: 2, 4, 8 or 16
                                     (0: 4)                                   */
 #define FE_KNOB_LOCK_SPIN 6      /* FE_ROWLOCK: a lock is given up after
@@ -387,6 +393,16 @@ int fe_assemble_batch(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, 
 int fe_batch_autotune(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
                       void *stream, fe_schedule *best, float *best_ms);
 
+/* The schedule fe_assemble_batch would take for this batch (sched = NULL):
+ * the one fe_batch_autotune found for a batch of the same signature, in this
+ * context or, with the environment variable FEASM_TUNE_CACHE naming a file,
+ * in any earlier process on the same GPU model (the autotuner appends every
+ * result to that file, one text line per entry keyed by GPU model and SM
+ * count, batch signature and format/mode; a context reads its device's
+ * entries when it first batches).  FE_ERR_NOT_FOUND when none is known. */
+int fe_batch_tuned(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
+                   fe_schedule *out);
+
 /* Capture one batched assembly into a CUDA graph (item table copied to the
  * device once); fe_batch_graph_launch replays it on any stream, e.g. after
  * new element values were written into the same K buffers.  The patterns and
@@ -467,9 +483,11 @@ typedef struct fe_server fe_server;
 
 /* Start a server on ctx: n_streams launch streams (1..64), at most max_batch
  * requests per launch, hbm_budget_bytes of device memory for admitted
- * requests and cached patterns (0 = the context's budget).  n_streams = 1
+ * requests and cached patterns (0 = the context's budget).  Requests of at
+ * least 2^26 element-matrix entries are launched alone on one of two extra
+ * high-priority streams (never grouped with small ones).  n_streams = 1
  * with max_batch = 1 is a strict FIFO: one request at a time from admission
- * to completion (the one-launch-per-request baseline). */
+ * to completion on one stream (the one-launch-per-request baseline). */
 int fe_server_start(fe_ctx *ctx, int32_t n_streams, int32_t max_batch, size_t hbm_budget_bytes,
                     fe_server **out);
 /* Stop the threads, wait for the device, free everything the server owns. */

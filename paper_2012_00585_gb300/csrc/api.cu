@@ -268,8 +268,8 @@ int fe_destroy(fe_ctx *ctx)
 {
     if (!ctx) return FE_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
-    fe_batch_state_destroy(ctx);
     cudaDeviceSynchronize();
+    fe_batch_state_destroy(ctx);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->d_status) cudaFree(ctx->d_status);
     delete ctx;
@@ -286,13 +286,13 @@ int fe_tune_set(fe_ctx *ctx, int knob, int value)
     case FE_KNOB_GATHER_WARPS: hi = 8; break;
     case FE_KNOB_ATOMIC_KERNEL: hi = 2; break;
     case FE_KNOB_ATOMIC_WARPS: hi = 8; break;
+    case FE_KNOB_ATOMIC_ORDER: hi = 2; break;
     case FE_KNOB_LOCK_SPIN: hi = 24; break;
     case FE_KNOB_SPMV_LANES: hi = 16; break;
     default: return FE_ERR_INVALID_ARG;
     }
     if (value < lo || value > hi) return FE_ERR_INVALID_ARG;
     if (knob == FE_KNOB_GATHER_BATCH && value != 0 && value != 4 && value != 8) return FE_ERR_INVALID_ARG;
-    if (knob == 5) return FE_ERR_INVALID_ARG;  // reserved
     if (knob == FE_KNOB_LOCK_SPIN && value != 0 && value < 4) return FE_ERR_INVALID_ARG;
     if (knob == FE_KNOB_SPMV_LANES && value != 0 && value != 2 && value != 4 && value != 8 && value != 16)
         return FE_ERR_INVALID_ARG;

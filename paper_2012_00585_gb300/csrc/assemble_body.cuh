@@ -23,7 +23,12 @@ struct Geo {
     // row starts of the block-map kernels: 0 from row_ptr (CSR), 1 from the
     // value position of each row's first CRAC pair (the CRAC gather)
     int crac_rows = 0;
+    // FE_ATOMIC: elements in this order (a locality order), or ascending
+    const int32_t *order = nullptr;
 };
+
+// Element at position i of the atomic scatter's order.
+__device__ __forceinline__ int64_t elem_at(const Geo &g, int64_t i) { return g.order ? (int64_t)g.order[i] : i; }
 
 __device__ __forceinline__ int64_t crac_row_base(const Geo &g, int64_t i) { return g.col_align[g.crac_ptr[i] + 1]; }
 
@@ -62,7 +67,7 @@ inline Geo geo_of(const fe_pattern *p)
 {
     return Geo{p->node_dofs, p->row_ptr,  p->crac_ptr, p->col_align, p->run_mask,
                p->run_ptr,   p->adj_ptr, p->adj,      p->uniform_runs ? p->runs_per_elem : 0, p->mask_words,
-               p->nnz,       p->ctx->d_status, p->crac_rows ? 1 : 0};
+               p->nnz,       p->ctx->d_status, p->crac_rows ? 1 : 0, p->elem_order};
 }
 
 // One element of NLN blocks of BB DOFs (NLN*BB <= 32), the warp cooperating:
@@ -172,107 +177,109 @@ __device__ __forceinline__ void atomic_element_generic(const double *__restrict_
     __syncwarp();
 }
 
-// Start of node row v in values, its first DOF row's length and its
-// adjacency range: what gather_row needs before its first load.
-template <int BB, bool CRAC>
-__device__ __forceinline__ void gather_row_head(const Geo &g, int64_t v, int64_t &rb, int64_t &RL, int64_t &a,
-                                                int64_t &b)
-{
-    const int64_t i0 = (int64_t)BB * v;
-    if (!CRAC) {
-        rb = g.row_ptr[i0];
-        RL = g.row_ptr[i0 + 1] - rb;
-    } else {
-        rb = crac_row_base(g, i0);
-        RL = crac_row_base(g, i0 + 1) - rb;
-    }
-    a = g.adj_ptr[v];
-    b = g.adj_ptr[v + 1];
-}
-
-// One node row (its BB DOF rows, contiguous in values from rb, each RL long;
-// incidences adj[a, b)), the warp cooperating: incidences in ascending
-// element order, U at a time loaded to registers, added into acc (shared,
-// >= BB * row length doubles), written once.  Bit-identical to the
-// sequential sum.
-template <int NLN, int BB, typename MT, bool CRAC, int U>
-__device__ __forceinline__ void gather_row(const double *__restrict__ K, const Geo &g, const MT *__restrict__ map,
-                                           const MT *__restrict__ mapc, double *acc, int accumulate, double *values,
-                                           int lane, int64_t rb, int64_t RL, int64_t a, int64_t b)
+// Node rows v0, v0 + dv, ... < v_end of one mesh (the warp cooperating;
+// acc: the warp's accumulator, cap doubles).  One warp per block row; the B
+// rows of the node are contiguous in values.  Incidences are taken U at a
+// time: their K slices and slots are loaded first, then added strictly in
+// ascending element order (bit-identical to the sequential sum).  The slot
+// of an entry is row start + B * pos + column % B, pos read from the block
+// map (the CSR map, or for the CRAC gather the CRAC run map expanded per
+// column block); row starts come from row_ptr or from the CRAC pairs
+// (row_start).  Rows of 3+ DOF blocks load the next row's start and
+// adjacency range one row ahead (no dependent load at the head of a row:
+// this also hides the CRAC pair read behind the pointer read).  Used by the
+// single-mesh gather (rows strided over all warps) and by the batched kernel
+// (a tile of consecutive rows).
+template <int NLN, int BB, typename MT, int U>
+__device__ __forceinline__ void gather_node_rows(const double *__restrict__ K, const Geo &g,
+                                                 const MT *__restrict__ map, double *acc, int cap, int accumulate,
+                                                 double *values, int64_t v0, int64_t v_end, int64_t dv, int lane)
 {
     constexpr int NLOC = NLN * BB;
     constexpr int NN = NLOC * NLOC;
-    constexpr int CHK = BB * NLOC;
+    constexpr int CHK = BB * NLOC;  // doubles of one incidence (B contiguous K rows)
     constexpr int IT = (CHK + 31) / 32;
-    int jr_[IT], c_[IT], ku[IT], offu[IT];
+    static_assert(NLN >= 1, "specialised shapes only");
+    // per-entry constants: block row jr, column c
+    int jr_[IT], c_[IT];
 #pragma unroll
     for (int j = 0; j < IT; ++j) {
         const int q = lane + 32 * j;
         const int qq = q < CHK ? q : 0;
         jr_[j] = qq / NLOC;
         c_[j] = qq % NLOC;
-        ku[j] = 0;
-        offu[j] = 0;
-        if (CRAC && g.uniform_R) run_of(g.run_mask[0], c_[j] / BB, ku[j], offu[j]);
     }
-    const int total = (int)(BB * RL);
-    if (total > 0 && !FE_IN_BOUNDS(rb + total - 1, g.nnz, g.status)) return;
-    for (int k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
-    __syncwarp();
-    for (int64_t s0 = a; s0 < b; s0 += U) {
-        double kv[U][IT];
-        int rel[U][IT];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const bool have = s0 + u < b;
-            const uint32_t t = have ? g.adj[s0 + u] : 0u;
-            const uint32_t e = t / NLN;
-            const int kr = (int)(t - e * NLN);
-            const double *chunk = K + (int64_t)e * NN + (int64_t)kr * CHK;
-            int64_t rp = 0;
-            int nr = 0;
-            uint32_t m = 0;
-            if (CRAC && have) {
-                if (g.uniform_R) {
-                    nr = g.uniform_R;
-                    rp = (int64_t)e * nr;
-                } else {
-                    rp = g.run_ptr[e];
-                    nr = (int)(g.run_ptr[e + 1] - rp);
-                    m = g.run_mask[e];
-                }
+    constexpr bool PF = BB >= 3;
+    const int64_t W = dv;
+    int64_t p0 = 0, p1 = 0, q0 = 0, q1 = 0;
+    if (PF) {
+        const int64_t v = v0;
+        if (v < v_end) {
+            p0 = row_start(g, (int64_t)BB * v);
+            p1 = row_start(g, (int64_t)BB * v + 1);
+            q0 = g.adj_ptr[v];
+            q1 = g.adj_ptr[v + 1];
+        }
+    }
+    for (int64_t v = v0; v < v_end; v += W) {
+        int64_t rb, RL, a, b;
+        if constexpr (PF) {
+            rb = p0;
+            RL = p1 - p0;
+            a = q0;
+            b = q1;
+            if (v + W < v_end) {
+                p0 = row_start(g, (int64_t)BB * (v + W));
+                p1 = row_start(g, (int64_t)BB * (v + W) + 1);
+                q0 = g.adj_ptr[v + W];
+                q1 = g.adj_ptr[v + W + 1];
             }
+        } else {
+            const int64_t i0 = (int64_t)BB * v;
+            rb = row_start(g, i0);
+            RL = row_start(g, i0 + 1) - rb;
+            a = g.adj_ptr[v];
+            b = g.adj_ptr[v + 1];
+        }
+        const int total = (int)(BB * RL);
+        if (total > 0 && (!FE_IN_BOUNDS(rb + total - 1, g.nnz, g.status) || !FE_IN_BOUNDS(total - 1, cap, g.status)))
+            continue;
+        for (int k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
+        __syncwarp();
+        for (int64_t s0 = a; s0 < b; s0 += U) {
+            double kv[U][IT];
+            int rel[U][IT];
 #pragma unroll
-            for (int j = 0; j < IT; ++j) {
-                const int q = lane + 32 * j;
-                kv[u][j] = 0.0;
-                rel[u][j] = 0;
-                if (have && q < CHK) {
-                    kv[u][j] = __ldcs(chunk + q);
-                    const int kc = c_[j] / BB;
-                    int pos;
-                    if (!CRAC) {
-                        pos = (int)map[(int64_t)t * NLN + kc];
-                    } else {
-                        int k = ku[j], off = offu[j];
-                        if (!g.uniform_R) run_of(m, kc, k, off);
-                        pos = (int)mapc[rp * NLN + (int64_t)kr * nr + k] + off;
+            for (int u = 0; u < U; ++u) {
+                const bool have = s0 + u < b;
+                const uint32_t t = have ? g.adj[s0 + u] : 0u;
+                const uint32_t e = t / NLN;
+                const int kr = (int)(t - e * NLN);
+                const double *chunk = K + (int64_t)e * NN + (int64_t)kr * CHK;
+#pragma unroll
+                for (int j = 0; j < IT; ++j) {
+                    const int q = lane + 32 * j;
+                    kv[u][j] = 0.0;
+                    rel[u][j] = 0;
+                    if (have && q < CHK) {
+                        kv[u][j] = __ldcs(chunk + q);
+                        const int pos = (int)map[(int64_t)t * NLN + c_[j] / BB];
+                        rel[u][j] = jr_[j] * (int)RL + BB * pos + c_[j] % BB;
                     }
-                    rel[u][j] = jr_[j] * (int)RL + BB * pos + c_[j] % BB;
                 }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
+            for (int u = 0; u < U; ++u) {
 #pragma unroll
-            for (int j = 0; j < IT; ++j)
-                if (s0 + u < b && lane + 32 * j < CHK && FE_IN_BOUNDS(rel[u][j], total, g.status))
-                    acc[rel[u][j]] += kv[u][j];
-            __syncwarp();
+                for (int j = 0; j < IT; ++j)
+                    if (s0 + u < b && lane + 32 * j < CHK && FE_IN_BOUNDS(rel[u][j], total, g.status))
+                        acc[rel[u][j]] += kv[u][j];
+                __syncwarp();
+            }
         }
+        for (int k = lane; k < total; k += 32) values[rb + k] = acc[k];
+        __syncwarp();
     }
-    for (int k = lane; k < total; k += 32) values[rb + k] = acc[k];
-    __syncwarp();
 }
 
 template <typename MT, bool CRAC>

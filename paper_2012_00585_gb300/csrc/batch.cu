@@ -17,6 +17,10 @@
 // fastest per batch signature in the context; a batch can also be captured
 // once into a CUDA graph and replayed.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -209,27 +213,26 @@ __device__ __noinline__ void gather_tile_small(const BatchItemDev *__restrict__ 
 }
 
 // The node rows [u0, u1) of an item with a specialised shape, one call per
-// tile (the item's geometry is read once per tile, not once per row); each
-// row's start and adjacency range are loaded one row ahead.
-template <int NLN, int BB, typename MT, bool CRAC>
+// tile: the single-mesh row loop (gather_node_rows, next row's head loaded
+// one row ahead) over the tile's consecutive rows, through the item's block
+// map (CSR, or the CRAC run map expanded per column block with row starts
+// from the CRAC pairs).  Only the fields the loop reads are taken from the
+// item, so that they stay in registers.
+template <int NLN, int BB, typename MT>
 __device__ __noinline__ void gather_tile_node(const BatchItemDev *__restrict__ it, int64_t u0, int64_t u1,
-                                              double *acc, int accumulate, int lane)
+                                              double *acc, int cap, int accumulate, int lane)
 {
-    const Geo g = it->g;
-    const double *K = it->K;
-    double *values = it->values;
-    const MT *map = (const MT *)it->map, *mapc = (const MT *)it->mapc;
-    int64_t rb, RL, a, b;
-    gather_row_head<BB, CRAC>(g, u0, rb, RL, a, b);
-    for (int64_t v = u0; v < u1; ++v) {
-        int64_t nrb = 0, nRL = 0, na = 0, nb = 0;
-        if (v + 1 < u1) gather_row_head<BB, CRAC>(g, v + 1, nrb, nRL, na, nb);
-        gather_row<NLN, BB, MT, CRAC, 4>(K, g, map, mapc, acc, accumulate, values, lane, rb, RL, a, b);
-        rb = nrb;
-        RL = nRL;
-        a = na;
-        b = nb;
-    }
+    Geo g;
+    g.row_ptr = it->g.row_ptr;
+    g.crac_ptr = it->g.crac_ptr;
+    g.col_align = it->g.col_align;
+    g.adj_ptr = it->g.adj_ptr;
+    g.adj = it->g.adj;
+    g.crac_rows = it->g.crac_rows;
+    g.nnz = it->g.nnz;
+    g.status = it->g.status;
+    gather_node_rows<NLN, BB, MT, 4>(it->K, g, (const MT *)it->map, acc, cap, accumulate, it->values, u0, u1, 1,
+                                     lane);
 }
 
 template <typename MT, bool CRAC>
@@ -420,11 +423,11 @@ __global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW 
                     }
                 } else if (it.shape == SH_8_3 || it.shape == SH_10_3) {
                     if (it.shape == SH_8_3) {
-                        if (it.map_bytes == 1) gather_tile_node<8, 3, uint8_t, CRAC>(&it, u0, u1, acc, accumulate, lane);
-                        else gather_tile_node<8, 3, uint16_t, CRAC>(&it, u0, u1, acc, accumulate, lane);
+                        if (it.map_bytes == 1) gather_tile_node<8, 3, uint8_t>(&it, u0, u1, acc, cap, accumulate, lane);
+                        else gather_tile_node<8, 3, uint16_t>(&it, u0, u1, acc, cap, accumulate, lane);
                     } else {
-                        if (it.map_bytes == 1) gather_tile_node<10, 3, uint8_t, CRAC>(&it, u0, u1, acc, accumulate, lane);
-                        else gather_tile_node<10, 3, uint16_t, CRAC>(&it, u0, u1, acc, accumulate, lane);
+                        if (it.map_bytes == 1) gather_tile_node<10, 3, uint8_t>(&it, u0, u1, acc, cap, accumulate, lane);
+                        else gather_tile_node<10, 3, uint16_t>(&it, u0, u1, acc, cap, accumulate, lane);
                     }
                 } else {
                     for (int64_t v = u0; v < u1; ++v) {
@@ -484,7 +487,7 @@ int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
         if ((p->n_e > 0 && !items[i].elem_mats) || (p->nnz > 0 && !items[i].values)) return FE_ERR_INVALID_ARG;
         if (((uintptr_t)items[i].elem_mats & 7u) || ((uintptr_t)items[i].values & 7u)) return FE_ERR_INVALID_ARG;
         if (format == FE_FORMAT_CSR && !p->map_csr) return FE_ERR_NOT_BUILT;
-        if (format == FE_FORMAT_CRAC && (!p->map_crac || !p->col_align)) return FE_ERR_NOT_BUILT;
+        if (format == FE_FORMAT_CRAC && (!p->map_crac || !p->col_align || !p->map_crac_blk)) return FE_ERR_NOT_BUILT;
         if (mode == FE_DETERMINISTIC && !p->adj) return FE_ERR_NOT_BUILT;
         BatchItemDev &d = plan.host[i];
         d.g = geo_of(p);
@@ -492,12 +495,17 @@ int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
         d.values = items[i].values;
         d.map = p->map_csr;
         d.mapc = p->map_crac;
+        d.shape = shape_of(p);
+        if (format == FE_FORMAT_CRAC && mode == FE_DETERMINISTIC && (d.shape == SH_8_3 || d.shape == SH_10_3)) {
+            // the CRAC gather of these shapes: expanded CRAC block map, CRAC row starts
+            d.map = p->map_crac_blk;
+            d.g.crac_rows = 1;
+        }
         d.units = mode == FE_ATOMIC ? p->n_e : p->n_nodes;
         d.nnz = p->nnz;
         d.tile_begin = plan.total_tiles;
         d.nln = p->nln;
         d.B = p->B;
-        d.shape = shape_of(p);
         d.map_bytes = p->map_bytes;
         const int nn = p->n_loc * p->n_loc;
         d.staged = d.shape != SH_GENERIC && nn <= STAGE_MAX && (nn * 8) % 16 == 0 &&
@@ -579,24 +587,100 @@ bool sched_valid(int mode, const fe_schedule &sc)
 
 // ---- per-context state: tuned schedules ----------------------------------
 
+// Item tables reach the device through a ring of pinned host slots: a copy
+// from pageable memory may wait for the stream's earlier work (the driver
+// stages it), which would stall a caller that launches on several streams,
+// such as the server's scheduler.  A slot is reused once the event recorded
+// after its copy has completed.
+constexpr int UPLOAD_SLOTS = 64;
+constexpr size_t UPLOAD_SLOT_BYTES = 64 << 10;
+
 struct fe_batch_state {
     std::mutex mu;
     std::map<std::tuple<int, int, uint64_t, int>, fe_schedule> tuned;  // (format, mode, shapes, size bucket)
+    std::mutex up_mu;
+    unsigned char *up_host = nullptr;  // UPLOAD_SLOTS x UPLOAD_SLOT_BYTES, pinned
+    cudaEvent_t up_done[UPLOAD_SLOTS] = {};
+    int up_next = 0;
+    bool up_failed = false;
 };
 
 void fe_batch_state_destroy(fe_ctx *ctx)
 {
+    fe_batch_state *st = ctx->batch;
+    if (st) {
+        for (cudaEvent_t e : st->up_done)
+            if (e) {
+                cudaEventSynchronize(e);
+                cudaEventDestroy(e);
+            }
+        if (st->up_host) cudaFreeHost(st->up_host);
+    }
     delete ctx->batch;
     ctx->batch = nullptr;
 }
 
 namespace {
 
+// ---- the autotuner's cache file --------------------------------------------
+// With FEASM_TUNE_CACHE set to a path, tuned schedules persist across
+// processes: one text line per entry, "<device> <format> <mode> <shapes>
+// <size bucket> <kind> <tile>", where <device> names the GPU model and its SM
+// count (schedules tuned on one GPU model are not taken on another) and
+// <shapes> is the set of element shapes and map widths of the batch.  A
+// context reads the entries of its device when it first batches; every
+// autotune appends its result (later lines win).
+std::string device_key(int device)
+{
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    std::string k = prop.name;
+    for (char &c : k)
+        if (c == ' ' || c == '\t') c = '_';
+    return k + "_sm" + std::to_string(prop.multiProcessorCount);
+}
+
+void load_tune_cache(fe_ctx *ctx, fe_batch_state *st)
+{
+    const char *path = getenv("FEASM_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    const std::string key = device_key(ctx->device);
+    char dev[256];
+    int fmt, mode, bucket, kind, tile;
+    unsigned long long shapes;
+    while (fscanf(f, "%255s %d %d %llx %d %d %d", dev, &fmt, &mode, &shapes, &bucket, &kind, &tile) == 7) {
+        if (key == dev && sched_valid(mode, fe_schedule{kind, tile}))
+            st->tuned[std::make_tuple(fmt, mode, (uint64_t)shapes, bucket)] = fe_schedule{kind, tile};
+    }
+    fclose(f);
+}
+
+void store_tune_cache(fe_ctx *ctx, const std::tuple<int, int, uint64_t, int> &sig, const fe_schedule &sc)
+{
+    const char *path = getenv("FEASM_TUNE_CACHE");
+    if (!path || !*path) return;
+    static std::mutex file_mu;  // appends from several contexts of this process
+    std::lock_guard<std::mutex> lk(file_mu);
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %llx %d %d %d\n", device_key(ctx->device).c_str(), std::get<0>(sig), std::get<1>(sig),
+            (unsigned long long)std::get<2>(sig), std::get<3>(sig), sc.kind, sc.tile);
+    fclose(f);
+}
+
 fe_batch_state *state_of(fe_ctx *ctx)
 {
     static std::mutex create_mu;
     std::lock_guard<std::mutex> lk(create_mu);
-    if (!ctx->batch) ctx->batch = new fe_batch_state();
+    if (!ctx->batch) {
+        ctx->batch = new fe_batch_state();
+        load_tune_cache(ctx, ctx->batch);
+    }
     return ctx->batch;
 }
 
@@ -635,6 +719,39 @@ struct DeviceScope {
     }
 };
 
+// Copy n bytes of host data to dst on stream s through a pinned slot (the
+// pageable copy when the table is larger than a slot or pinned memory could
+// not be had).
+int upload(fe_ctx *ctx, void *dst, const void *src, size_t n, cudaStream_t s)
+{
+    fe_batch_state *st = state_of(ctx);
+    if (n <= UPLOAD_SLOT_BYTES) {
+        std::lock_guard<std::mutex> lk(st->up_mu);
+        if (!st->up_host && !st->up_failed) {
+            bool ok = cudaHostAlloc((void **)&st->up_host, UPLOAD_SLOTS * UPLOAD_SLOT_BYTES, cudaHostAllocPortable) ==
+                      cudaSuccess;
+            for (int k = 0; ok && k < UPLOAD_SLOTS; ++k)
+                ok = cudaEventCreateWithFlags(&st->up_done[k], cudaEventDisableTiming) == cudaSuccess;
+            if (!ok) {
+                cudaGetLastError();
+                st->up_failed = true;
+            }
+        }
+        if (st->up_host && !st->up_failed) {
+            const int k = st->up_next;
+            st->up_next = (k + 1) % UPLOAD_SLOTS;
+            FE_CUDA(cudaEventSynchronize(st->up_done[k]));  // the slot's previous copy (long done, normally)
+            unsigned char *slot = st->up_host + (size_t)k * UPLOAD_SLOT_BYTES;
+            memcpy(slot, src, n);
+            FE_CUDA(cudaMemcpyAsync(dst, slot, n, cudaMemcpyHostToDevice, s));
+            FE_CUDA(cudaEventRecord(st->up_done[k], s));
+            return FE_OK;
+        }
+    }
+    FE_CUDA(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s));
+    return FE_OK;
+}
+
 // Plan upload + launch on stream s.  The item table and the tile counter are
 // stream-ordered allocations freed after the launch.
 int run_batch(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mode, int acc, fe_schedule sc,
@@ -646,9 +763,7 @@ int run_batch(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
     unsigned long long *counter = nullptr;
     FE_TRY(fe_alloc(ctx, (void **)&d_items, sizeof(BatchItemDev) * n, s));
     int rc = fe_alloc(ctx, (void **)&counter, sizeof(unsigned long long), s);
-    if (rc == FE_OK && cudaMemcpyAsync(d_items, plan.host.data(), sizeof(BatchItemDev) * n, cudaMemcpyHostToDevice,
-                                       s) != cudaSuccess)
-        rc = FE_ERR_DEVICE;
+    if (rc == FE_OK) rc = upload(ctx, d_items, plan.host.data(), sizeof(BatchItemDev) * n, s);
     if (rc == FE_OK && cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s) != cudaSuccess) rc = FE_ERR_DEVICE;
     if (rc == FE_OK && mode == FE_ATOMIC && !acc) {
         k_batch_zero<<<ctx->num_sms * 4, 256, 0, s>>>(d_items, n);
@@ -695,6 +810,23 @@ int fe_assemble_batch(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, 
         if (it != st->tuned.end()) sc = it->second;
     }
     return run_batch(ctx, items, n_items, format, mode, accumulate, sc, (cudaStream_t)stream);
+}
+
+int fe_batch_tuned(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
+                   fe_schedule *out)
+{
+    if (!ctx || n_items <= 0 || !items || !out) return FE_ERR_INVALID_ARG;
+    if ((format != FE_FORMAT_CSR && format != FE_FORMAT_CRAC) || (mode != FE_ATOMIC && mode != FE_DETERMINISTIC))
+        return FE_ERR_INVALID_ARG;
+    for (int i = 0; i < n_items; ++i)
+        if (!items[i].pattern) return FE_ERR_INVALID_ARG;
+    DeviceScope ds(ctx->device);
+    fe_batch_state *st = state_of(ctx);
+    std::lock_guard<std::mutex> lk(st->mu);
+    auto it = st->tuned.find(signature(items, n_items, format, mode));
+    if (it == st->tuned.end()) return FE_ERR_NOT_FOUND;
+    *out = it->second;
+    return FE_OK;
 }
 
 int fe_batch_autotune(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
@@ -747,8 +879,12 @@ int fe_batch_autotune(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, 
     if (rc != FE_OK) return rc;
     {
         fe_batch_state *st = state_of(ctx);
-        std::lock_guard<std::mutex> lk(st->mu);
-        st->tuned[signature(items, n_items, format, mode)] = win;
+        const auto sig = signature(items, n_items, format, mode);
+        {
+            std::lock_guard<std::mutex> lk(st->mu);
+            st->tuned[sig] = win;
+        }
+        store_tune_cache(ctx, sig, win);
     }
     if (best) *best = win;
     if (best_ms) *best_ms = win_ms;

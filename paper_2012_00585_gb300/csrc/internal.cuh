@@ -108,6 +108,9 @@ struct fe_pattern {
     // [n_e * nln * nln] uint8/uint16: the CRAC run map expanded to one entry
     // per column block (run start + offset in the run), for the CRAC gather
     void *map_crac_blk = nullptr;
+    // [n_e] elements grouped by compact clusters of the block graph, the
+    // order of the atomic scatter on scattered numberings (null: ascending)
+    int32_t *elem_order = nullptr;
     // set only on a numeric-phase view of the pattern: row starts are read
     // from the CRAC pairs (the CRAC gather through map_crac_blk)
     bool crac_rows = false;

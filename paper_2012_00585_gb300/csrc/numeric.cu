@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(256) k_atomic_elem(const double *__restrict__ 
     const int lane = threadIdx.x & 31;
     int kk = 0, koff = 0;
     if (CRAC && g.uniform_R && lane < NLN) run_of(g.run_mask[0], lane, kk, koff);
-    for (int64_t e = fe_warp_id(); e < n_e; e += fe_warps()) {
+    for (int64_t i = fe_warp_id(); i < n_e; i += fe_warps()) {
+        const int64_t e = elem_at(g, i);
         const int32_t nd = lane < NLN ? g.N[e * NLN + lane] : 0;
         const int32_t rnode = __shfl_sync(0xffffffffu, nd, lane < NLOC ? lane / BB : 0);
         int64_t base = 0;
@@ -114,7 +115,8 @@ __global__ void __launch_bounds__(256) k_atomic_generic(const double *__restrict
     const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) & 7;
     const int n_loc = nln * B;
     const int64_t NN = (int64_t)n_loc * n_loc;
-    for (int64_t e = fe_warp_id(); e < n_e; e += fe_warps()) {
+    for (int64_t i = fe_warp_id(); i < n_e; i += fe_warps()) {
+        const int64_t e = elem_at(g, i);
         int64_t rp = 0;
         int nr = 0;
         if (CRAC) {
@@ -143,108 +145,17 @@ __global__ void __launch_bounds__(256) k_atomic_generic(const double *__restrict
 }
 
 // ------------------------------------------------------ deterministic ---
-// One warp per block row; the B rows of the node are contiguous in values.
-// Incidences are taken U at a time: their K slices and slots are loaded
-// first, then added strictly in ascending element order.  The slot of an
-// entry is row start + B * pos + column % B, pos read from the block map
-// (the CSR map, or for the CRAC gather the CRAC run map expanded per column
-// block); row starts come from row_ptr or from the CRAC pairs (row_start).
-// Rows of 3+ DOF blocks load the next row's start and adjacency range one
-// row ahead (no dependent load at the head of a row: this also hides the
-// CRAC pair read behind the pointer read).
+// One warp per node row, rows strided over all warps (gather_node_rows in
+// assemble_body.cuh: ascending-element sums, bit-identical to Listing 2).
 template <int NLN, int BB, typename MT, int U>
 __global__ void __launch_bounds__(256) k_gather_node(const double *__restrict__ K, int64_t n_nodes, Geo g,
                                                      const MT *__restrict__ map, int cap, int accumulate,
                                                      double *values)
 {
-    constexpr int NLOC = NLN * BB;
-    constexpr int NN = NLOC * NLOC;
-    constexpr int CHK = BB * NLOC;  // doubles of one incidence (B contiguous K rows)
-    constexpr int IT = (CHK + 31) / 32;
-    static_assert(NLN >= 1, "specialised shapes only");
     extern __shared__ double acc_all[];
-    const int lane = threadIdx.x & 31;
     double *acc = acc_all + (size_t)(threadIdx.x >> 5) * cap;
-    // per-entry constants: block row jr, column c
-    int jr_[IT], c_[IT];
-#pragma unroll
-    for (int j = 0; j < IT; ++j) {
-        const int q = lane + 32 * j;
-        const int qq = q < CHK ? q : 0;
-        jr_[j] = qq / NLOC;
-        c_[j] = qq % NLOC;
-    }
-    constexpr bool PF = BB >= 3;
-    const int64_t W = fe_warps();
-    int64_t p0 = 0, p1 = 0, q0 = 0, q1 = 0;
-    if (PF) {
-        const int64_t v = fe_warp_id();
-        if (v < n_nodes) {
-            p0 = row_start(g, (int64_t)BB * v);
-            p1 = row_start(g, (int64_t)BB * v + 1);
-            q0 = g.adj_ptr[v];
-            q1 = g.adj_ptr[v + 1];
-        }
-    }
-    for (int64_t v = fe_warp_id(); v < n_nodes; v += W) {
-        int64_t rb, RL, a, b;
-        if constexpr (PF) {
-            rb = p0;
-            RL = p1 - p0;
-            a = q0;
-            b = q1;
-            if (v + W < n_nodes) {
-                p0 = row_start(g, (int64_t)BB * (v + W));
-                p1 = row_start(g, (int64_t)BB * (v + W) + 1);
-                q0 = g.adj_ptr[v + W];
-                q1 = g.adj_ptr[v + W + 1];
-            }
-        } else {
-            const int64_t i0 = (int64_t)BB * v;
-            rb = row_start(g, i0);
-            RL = row_start(g, i0 + 1) - rb;
-            a = g.adj_ptr[v];
-            b = g.adj_ptr[v + 1];
-        }
-        const int total = (int)(BB * RL);
-        if (total > 0 && (!FE_IN_BOUNDS(rb + total - 1, g.nnz, g.status) || !FE_IN_BOUNDS(total - 1, cap, g.status)))
-            continue;
-        for (int k = lane; k < total; k += 32) acc[k] = accumulate ? values[rb + k] : 0.0;
-        __syncwarp();
-        for (int64_t s0 = a; s0 < b; s0 += U) {
-            double kv[U][IT];
-            int rel[U][IT];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool have = s0 + u < b;
-                const uint32_t t = have ? g.adj[s0 + u] : 0u;
-                const uint32_t e = t / NLN;
-                const int kr = (int)(t - e * NLN);
-                const double *chunk = K + (int64_t)e * NN + (int64_t)kr * CHK;
-#pragma unroll
-                for (int j = 0; j < IT; ++j) {
-                    const int q = lane + 32 * j;
-                    kv[u][j] = 0.0;
-                    rel[u][j] = 0;
-                    if (have && q < CHK) {
-                        kv[u][j] = __ldcs(chunk + q);
-                        const int pos = (int)map[(int64_t)t * NLN + c_[j] / BB];
-                        rel[u][j] = jr_[j] * (int)RL + BB * pos + c_[j] % BB;
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-#pragma unroll
-                for (int j = 0; j < IT; ++j)
-                    if (s0 + u < b && lane + 32 * j < CHK && FE_IN_BOUNDS(rel[u][j], total, g.status))
-                        acc[rel[u][j]] += kv[u][j];
-                __syncwarp();
-            }
-        }
-        for (int k = lane; k < total; k += 32) values[rb + k] = acc[k];
-        __syncwarp();
-    }
+    gather_node_rows<NLN, BB, MT, U>(K, g, map, acc, cap, accumulate, values, fe_warp_id(), n_nodes, fe_warps(),
+                                     threadIdx.x & 31);
 }
 
 // Node rows whose incidence slices hold at most 16 entries (one-DOF elements
@@ -416,14 +327,16 @@ __global__ void __launch_bounds__(128) k_atomic_tma(const double *__restrict__ K
             fe_bulk_g2s(stage0 + st * NN, K + e * NN, NNB, &bar[st], pol);
         }
     };
-    int64_t e = fe_warp_id();
+    int64_t i = fe_warp_id();
+    int64_t e = i < n_e ? elem_at(g, i) : 0;
     int st = 0;
     uint32_t phase = 0;
-    if (e < n_e) issue(e, 0);
+    if (i < n_e) issue(e, 0);
     bool ok = true, next_issued = false;
-    while (e < n_e) {
-        const int64_t en = e + fe_warps();
-        next_issued = en < n_e;
+    while (i < n_e) {
+        const int64_t in = i + fe_warps();
+        next_issued = in < n_e;
+        const int64_t en = next_issued ? elem_at(g, in) : 0;
         if (next_issued) issue(en, st ^ 1);
         // per-element tables
         if (lane < NLOC) {
@@ -478,6 +391,7 @@ __global__ void __launch_bounds__(128) k_atomic_tma(const double *__restrict__ K
             }
         }
         __syncwarp();
+        i = in;
         e = en;
         st ^= 1;
     }

@@ -93,6 +93,16 @@ struct Group {
     int stream = 0;
 };
 
+// Requests of at least this many element-matrix entries are launched alone
+// on a high-priority stream: they are not grouped with small requests (whose
+// completion would wait for theirs), and the GPU's block scheduler serves
+// their kernels first, so that their latency stays near their own device
+// time while small requests fill the SMs around them.
+constexpr int64_t BIG_ENTRIES = (int64_t)1 << 26;
+constexpr int N_BIG_STREAMS = 2;
+
+bool is_big(const fe_request &r) { return r.n_elem * (int64_t)r.dofs_per_elem * r.dofs_per_elem >= BIG_ENTRIES; }
+
 // Keys of evicted patterns remembered to count rebuilds (bounded).
 constexpr size_t EVICTED_KEYS_MAX = 1 << 20;
 // Device spans kept for fe_server_timeline (bounded).
@@ -110,7 +120,8 @@ struct fe_server {
     std::unordered_map<uint64_t, CacheEntry> cache;
     size_t budget = 0, in_use = 0;
     size_t cache_bytes = 0;  // bytes of the built patterns in the cache (part of in_use)
-    std::vector<cudaStream_t> streams;
+    std::vector<cudaStream_t> streams;          // n_small launch streams, then n_big high-priority ones
+    int n_small = 0, n_big = 0, next_big = 0;
     cudaStream_t build_stream = nullptr;       // = build_streams[0]; evicted patterns are freed on it
     std::vector<cudaStream_t> build_streams;   // one per builder thread
     int next_stream = 0, max_batch = 64;
@@ -337,9 +348,17 @@ void scheduler_loop(fe_server *sv)
         while (!sv->ready.empty()) {
             const uint64_t id0 = sv->ready.front();
             const int fmt = sv->tickets[id0].req.format, mode = sv->tickets[id0].req.mode;
+            // a big request goes alone on a high-priority stream; otherwise
+            // the group takes small requests only
+            const bool big = sv->n_big > 0 && is_big(sv->tickets[id0].req);
             Group g;
-            g.stream = sv->next_stream;
-            sv->next_stream = (sv->next_stream + 1) % (int)sv->streams.size();
+            if (big) {
+                g.stream = sv->n_small + sv->next_big;
+                sv->next_big = (sv->next_big + 1) % sv->n_big;
+            } else {
+                g.stream = sv->next_stream;
+                sv->next_stream = (sv->next_stream + 1) % sv->n_small;
+            }
             cudaStream_t s = sv->streams[g.stream];
             if (cudaEventCreate(&g.t0) != cudaSuccess || cudaEventRecord(g.t0, s) != cudaSuccess) {
                 cudaGetLastError();
@@ -347,9 +366,10 @@ void scheduler_loop(fe_server *sv)
                 g.t0 = nullptr;
             }
             std::vector<fe_batch_item> items;
-            for (auto it = sv->ready.begin(); it != sv->ready.end() && (int)items.size() < sv->max_batch;) {
+            const int cap = big ? 1 : sv->max_batch;
+            for (auto it = sv->ready.begin(); it != sv->ready.end() && (int)items.size() < cap;) {
                 Ticket &t = sv->tickets[*it];
-                if (t.req.format != fmt || t.req.mode != mode) {
+                if (t.req.format != fmt || t.req.mode != mode || (sv->n_big > 0 && is_big(t.req) != big)) {
                     ++it;
                     continue;
                 }
@@ -551,6 +571,17 @@ int fe_server_start(fe_ctx *ctx, int32_t n_streams, int32_t max_batch, size_t hb
         cudaStream_t s;
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) rc = FE_ERR_DEVICE;
         else sv->streams.push_back(s);
+    }
+    sv->n_small = n_streams;
+    if (!sv->strict_fifo) {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) rc = FE_ERR_DEVICE;
+        for (int k = 0; k < N_BIG_STREAMS && rc == FE_OK; ++k) {
+            cudaStream_t s;
+            if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest) != cudaSuccess) rc = FE_ERR_DEVICE;
+            else sv->streams.push_back(s);
+        }
+        if (rc == FE_OK) sv->n_big = N_BIG_STREAMS;
     }
     for (int k = 0; k < N_BUILDERS && rc == FE_OK; ++k) {
         cudaStream_t s;

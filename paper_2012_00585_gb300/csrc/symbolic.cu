@@ -25,7 +25,7 @@
 
 namespace {
 
-enum { S_ERR = 0, S_MAX_DEG = 1, S_MAX_NODE = 2, S_NONUNIFORM = 3, S_BLOCKS = 4, S_COUNT = 6 };
+enum { S_ERR = 0, S_MAX_DEG = 1, S_MAX_NODE = 2, S_NONUNIFORM = 3, S_BLOCKS = 4, S_SPREAD = 5, S_COUNT = 6 };
 
 constexpr int32_t PAD = INT32_MAX;
 constexpr int REG_SORT_MAX = 256;  // candidates sorted in registers (8 per lane)
@@ -158,15 +158,19 @@ __global__ void __launch_bounds__(256) k_validate(const int32_t *__restrict__ D,
 // ---------------------------------------------------------------- A2 ---
 // One warp per element: block ids, run-start bits over the element's blocks
 // (bit k set when block k does not continue block k-1), runs per element,
-// whether all elements share element 0's bits, and block degrees.
+// whether all elements share element 0's bits, block degrees, and the sum
+// over elements of (largest - smallest block id), a measure of how local the
+// numbering is.
 __global__ void k_node_conn(const int32_t *__restrict__ D, int64_t n_e, int32_t n_loc, int32_t B, int32_t nln,
                             int mask_words, int32_t *__restrict__ N, uint32_t *__restrict__ run_mask,
                             int32_t *__restrict__ runs, int32_t *deg, int64_t *sc)
 {
     const int lane = threadIdx.x & 31;
+    int64_t spread = 0;
     for (int64_t e = fe_warp_id(); e < n_e; e += fe_warps()) {
         int nr = 0;
         bool differs = false;
+        int32_t lo = INT32_MAX, hi = 0;
         for (int k0 = 0; k0 < nln; k0 += 32) {
             const int k = k0 + lane;
             const bool valid = k < nln;
@@ -182,15 +186,23 @@ __global__ void k_node_conn(const int32_t *__restrict__ D, int64_t n_e, int32_t 
             if (valid) {
                 N[e * nln + k] = nd;
                 atomicAdd(&deg[nd], 1);
+                lo = min(lo, nd);
+                hi = max(hi, nd);
             }
             if (lane == 0) run_mask[e * mask_words + (k0 >> 5)] = m;
             nr += __popc(m);
         }
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        spread += hi - lo;
         if (lane == 0) {
             runs[e] = nr;
             if (differs) sc[S_NONUNIFORM] = 1;
         }
     }
+    if (lane == 0 && spread) atomicAdd((unsigned long long *)&sc[S_SPREAD], (unsigned long long)spread);
 }
 
 __global__ void k_max_i32(const int32_t *__restrict__ x, int64_t n, int64_t *out)
@@ -630,6 +642,85 @@ __global__ void k_expand_run_map(int64_t n_e, int32_t nln, int32_t mask_words, c
     }
 }
 
+// ---------------------------------------------------- element order ---
+// A locality order of the elements for the atomic scatter, built when the
+// numbering is scattered (e.g. node ids permuted): the atomic adds of
+// consecutive elements then land in rows far apart, and a row's values are
+// evicted from L2 between the elements that touch it.  The block graph
+// (blocks adjacent when they share an element) is split into compact
+// clusters by a breadth-first search from seeds (every stride-th block), all
+// grown at once level by level; a block reached from several clusters in the
+// same level joins the smallest cluster id, so the clusters do not depend on
+// thread timing.  Elements are then grouped by the cluster of their first
+// block (counting sort): each group touches one compact region of rows, which
+// stays in L2 while the group is added.  The order within a group is
+// unspecified (it only changes the order of atomic adds).
+constexpr int32_t ORDER_UNSET = INT32_MAX;
+
+__global__ void k_order_seed(int64_t n_nodes, int64_t stride, int32_t *__restrict__ owner,
+                             int32_t *__restrict__ level, int32_t *__restrict__ front, int32_t *n_front)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_nodes; v += (int64_t)gridDim.x * blockDim.x) {
+        if (v % stride == 0) {
+            owner[v] = (int32_t)(v / stride);
+            level[v] = 0;
+            front[atomicAdd(n_front, 1)] = (int32_t)v;
+        } else {
+            owner[v] = ORDER_UNSET;
+            level[v] = ORDER_UNSET;
+        }
+    }
+}
+
+// Level L: every block adjacent to a frontier block (whose cluster is final)
+// and not reached before joins the smallest adjacent frontier cluster; blocks
+// reached for the first time form the next frontier.  A warp per frontier
+// block, its lanes over (incidence, local block) pairs.
+__global__ void k_order_expand(const int32_t *__restrict__ front, int32_t n_front, int32_t L,
+                               const int64_t *__restrict__ adj_ptr, const uint32_t *__restrict__ adj,
+                               const int32_t *__restrict__ N, int32_t nln, int32_t *__restrict__ owner,
+                               int32_t *__restrict__ level, int32_t *__restrict__ next, int32_t *n_next)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t f = fe_warp_id(); f < n_front; f += fe_warps()) {
+        const int32_t v = front[f];
+        const int32_t ov = owner[v];
+        const int64_t a = adj_ptr[v];
+        const int64_t cnt = (adj_ptr[v + 1] - a) * nln;
+        for (int64_t x = lane; x < cnt; x += 32) {
+            const uint32_t t = adj[a + x / nln];
+            const uint32_t e = t / (uint32_t)nln;
+            const int32_t w = N[(int64_t)e * nln + x % nln];
+            const int32_t lw = level[w];
+            if (lw != ORDER_UNSET && lw != L) continue;  // settled in an earlier level
+            if (lw == ORDER_UNSET && atomicCAS(&level[w], ORDER_UNSET, L) == ORDER_UNSET)
+                next[atomicAdd(n_next, 1)] = w;
+            atomicMin(&owner[w], ov);
+        }
+    }
+}
+
+// Cluster of each element (its first block's; unreached blocks: the last
+// group), histogrammed.
+__global__ void k_order_count(const int32_t *__restrict__ N, int64_t n_e, int32_t nln,
+                              const int32_t *__restrict__ owner, int32_t n_groups, int32_t *__restrict__ grp,
+                              int32_t *__restrict__ hist)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_e; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = owner[N[e * nln]];
+        const int32_t c = o == ORDER_UNSET ? n_groups - 1 : o;
+        grp[e] = c;
+        atomicAdd(&hist[c], 1);
+    }
+}
+
+__global__ void k_order_place(int64_t n_e, const int32_t *__restrict__ grp, int64_t *__restrict__ cursor,
+                              int32_t *__restrict__ order)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_e; e += (int64_t)gridDim.x * blockDim.x)
+        order[atomicAdd((unsigned long long *)&cursor[grp[e]], 1ull)] = (int32_t)e;
+}
+
 struct Scratch {
     cudaStream_t s;
     void *p[12] = {};
@@ -645,7 +736,7 @@ void pattern_release(fe_pattern *p, cudaStream_t s)
 {
     fe_colouring_free(p, s);
     void *ptrs[] = {p->node_dofs, p->row_ptr, p->col_idx, p->crac_ptr, p->col_align, p->adj_ptr, p->adj,
-                    p->map_csr,   p->run_mask, p->run_ptr, p->map_crac, p->map_crac_blk};
+                    p->map_csr,   p->run_mask, p->run_ptr, p->map_crac, p->map_crac_blk, p->elem_order};
     for (void *x : ptrs) fe_free_async(x, s);
     delete p;
 }
@@ -669,6 +760,66 @@ int configure_smem(KernelT kernel, size_t bytes)
         __VA_ARGS__;   \
         fe_note_launch(); \
     } while (0)
+
+// A6 (see k_order_seed): clusters of about ORDER_STRIDE blocks (for 3-DOF
+// blocks of about 85 columns, some 33 MB of rows: a few clusters fit in L2).
+constexpr int64_t ORDER_STRIDE = 16384;
+
+int build_elem_order(fe_pattern *p, cudaStream_t s)
+{
+    fe_ctx *ctx = p->ctx;
+    const int sms = ctx->num_sms;
+    const int64_t n_nodes = p->n_nodes, n_e = p->n_e;
+    const int32_t nln = p->nln;
+    if (n_nodes >= INT32_MAX || n_e >= INT32_MAX) return FE_OK;  // no order: ascending elements
+    Scratch tmp;
+    tmp.s = s;
+    int32_t *owner = nullptr, *level = nullptr, *front = nullptr, *next = nullptr, *counts = nullptr;
+    FE_TRY(fe_alloc(ctx, (void **)&owner, sizeof(int32_t) * (size_t)n_nodes, s));
+    tmp.add(owner);
+    FE_TRY(fe_alloc(ctx, (void **)&level, sizeof(int32_t) * (size_t)n_nodes, s));
+    tmp.add(level);
+    FE_TRY(fe_alloc(ctx, (void **)&front, sizeof(int32_t) * (size_t)n_nodes, s));
+    tmp.add(front);
+    FE_TRY(fe_alloc(ctx, (void **)&next, sizeof(int32_t) * (size_t)n_nodes, s));
+    tmp.add(next);
+    FE_TRY(fe_alloc(ctx, (void **)&counts, sizeof(int32_t) * 2, s));
+    tmp.add(counts);
+    FE_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * 2, s));
+    FE_LAUNCH((k_order_seed<<<fe_grid_for(n_nodes, 256, sms, 16), 256, 0, s>>>(n_nodes, ORDER_STRIDE, owner, level,
+                                                                                front, counts)));
+    int32_t n_front = 0;
+    FE_CUDA(cudaMemcpyAsync(&n_front, counts, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    // every level settles at least one more block, so the loop ends; the
+    // bound only guards against a corrupted count
+    for (int32_t L = 1; n_front > 0 && L <= (int32_t)std::min<int64_t>(n_nodes, INT32_MAX - 1); ++L) {
+        FE_CUDA(cudaMemsetAsync(counts + 1, 0, sizeof(int32_t), s));
+        FE_LAUNCH((k_order_expand<<<fe_grid_for((int64_t)n_front * 32, 256, sms, 8), 256, 0, s>>>(
+            front, n_front, L, p->adj_ptr, p->adj, p->node_dofs, nln, owner, level, next, counts + 1)));
+        FE_CUDA(cudaMemcpyAsync(&n_front, counts + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        FE_CUDA(cudaStreamSynchronize(s));
+        std::swap(front, next);
+    }
+    // groups: one per seed, plus the last for blocks no seed reached
+    const int32_t n_groups = (int32_t)((n_nodes + ORDER_STRIDE - 1) / ORDER_STRIDE) + 1;
+    int32_t *grp = nullptr, *hist = nullptr;
+    int64_t *cursor = nullptr;
+    FE_TRY(fe_alloc(ctx, (void **)&grp, sizeof(int32_t) * (size_t)n_e, s));
+    tmp.add(grp);
+    FE_TRY(fe_alloc(ctx, (void **)&hist, sizeof(int32_t) * (size_t)n_groups, s));
+    tmp.add(hist);
+    FE_TRY(fe_alloc(ctx, (void **)&cursor, sizeof(int64_t) * (size_t)(n_groups + 1), s));
+    tmp.add(cursor);
+    FE_CUDA(cudaMemsetAsync(hist, 0, sizeof(int32_t) * (size_t)n_groups, s));
+    FE_LAUNCH((k_order_count<<<fe_grid_for(n_e, 256, sms, 16), 256, 0, s>>>(p->node_dofs, n_e, nln, owner, n_groups,
+                                                                           grp, hist)));
+    FE_TRY(fe_scan_i32_to_i64(ctx, hist, cursor, n_groups, s));
+    FE_TRY(alloc_into(p, (void **)&p->elem_order, sizeof(int32_t) * (size_t)n_e, s));
+    FE_LAUNCH((k_order_place<<<fe_grid_for(n_e, 256, sms, 16), 256, 0, s>>>(n_e, grp, cursor, p->elem_order)));
+    FE_CUDA(cudaGetLastError());
+    return FE_OK;
+}
 
 int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
 {
@@ -754,6 +905,7 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
     p->max_deg = (int32_t)h2[S_MAX_DEG];
     p->n_runs = h2[S_COUNT];
     p->uniform_runs = (h2[S_NONUNIFORM] == 0) && n_e > 0;
+    const int64_t spread_sum = h2[S_SPREAD];
     p->runs_per_elem = n_e > 0 ? (int32_t)(p->n_runs / n_e) : 0;
 
     ph.next("A3-A4 rows, CSR and CRAC");
@@ -901,6 +1053,19 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
             FE_CUDA(cudaGetLastError());
         }
     }
+    // A6: locality order of the elements for the atomic scatter
+    {
+        const int want = ctx->knob[FE_KNOB_ATOMIC_ORDER];
+        const bool maps = (p->flags & (FE_PATTERN_MAP_CSR | FE_PATTERN_MAP_CRAC)) != 0;
+        // auto: values too large to stay in L2, and a scattered numbering (an
+        // element's blocks lie on average more than n_nodes / 16 apart)
+        const bool scattered = n_e > 0 && spread_sum / n_e > n_nodes / 16;
+        const bool large = p->nnz * 8 > ((int64_t)256 << 20);
+        if (maps && n_e > 0 && n_nodes > 0 && (want == 2 || (want == 0 && large && scattered))) {
+            ph.next("A6 element order");
+            FE_TRY(build_elem_order(p, s));
+        }
+    }
     if (!(p->flags & FE_PATTERN_CRAC) && !(p->flags & FE_PATTERN_MAP_CRAC)) {
         // CRAC was only scaffolding for this pattern
         fe_free_async(p->col_align, s);
@@ -1023,6 +1188,7 @@ int fe_pattern_info_get(const fe_pattern *p, fe_pattern_info *out)
     out->flags = p->flags;
     out->block = p->B;
     out->uniform_runs = p->uniform_runs ? 1 : 0;
+    out->atomic_order = p->elem_order ? 1 : 0;
     out->device_bytes = p->device_bytes;
     return FE_OK;
 }

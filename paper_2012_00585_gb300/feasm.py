@@ -45,6 +45,7 @@ FE_KNOB_GATHER_BATCH = 1
 FE_KNOB_GATHER_WARPS = 2
 FE_KNOB_ATOMIC_KERNEL = 3
 FE_KNOB_ATOMIC_WARPS = 4
+FE_KNOB_ATOMIC_ORDER = 5
 FE_KNOB_LOCK_SPIN = 6
 FE_KNOB_SPMV_LANES = 7
 FE_KNOB_COUNT = 8
@@ -85,7 +86,7 @@ class fe_pattern_info(ctypes.Structure):
         ("flags", ctypes.c_uint32),
         ("block", ctypes.c_int32),
         ("uniform_runs", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("atomic_order", ctypes.c_int32),
         ("device_bytes", ctypes.c_int64),
     ]
 
@@ -181,6 +182,7 @@ def load():
                                       ctypes.POINTER(fe_schedule), ctypes.POINTER(ctypes.c_float)]),
             "fe_batch_graph_create": (i, [vp, ctypes.POINTER(fe_batch_item), i32, i32, i32, i32,
                                           ctypes.POINTER(fe_schedule), vp, pp]),
+            "fe_batch_tuned": (i, [vp, ctypes.POINTER(fe_batch_item), i32, i32, i32, ctypes.POINTER(fe_schedule)]),
             "fe_batch_graph_launch": (i, [vp, vp]),
             "fe_batch_graph_destroy": (i, [vp]),
             "fe_server_start": (i, [vp, i32, i32, ctypes.c_size_t, pp]),
@@ -400,6 +402,19 @@ def fe_batch_autotune(ctx, items, fmt=FE_FORMAT_CSR, mode=FE_ATOMIC, stream=None
     _check(load().fe_batch_autotune(ctx, arr, len(items), int(fmt), int(mode), _stream(stream), ctypes.byref(best),
                                     ctypes.byref(ms)), "fe_batch_autotune")
     return best.kind, best.tile, ms.value
+
+
+def fe_batch_tuned(ctx, items, fmt=FE_FORMAT_CSR, mode=FE_ATOMIC):
+    """-> (kind, tile) that fe_assemble_batch takes for this batch signature,
+    or None when no tuned schedule is known (in this context or the
+    FEASM_TUNE_CACHE file)."""
+    arr = _items(items)
+    out = fe_schedule()
+    rc = load().fe_batch_tuned(ctx, arr, len(items), int(fmt), int(mode), ctypes.byref(out))
+    if rc == FE_ERR_NOT_FOUND:
+        return None
+    _check(rc, "fe_batch_tuned")
+    return out.kind, out.tile
 
 
 def fe_batch_graph_create(ctx, items, fmt=FE_FORMAT_CSR, mode=FE_ATOMIC, accumulate=0, sched=None, stream=None):

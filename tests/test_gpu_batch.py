@@ -215,3 +215,47 @@ def test_batch_full_size_sampled(ctx, mode):
     feasm.fe_batch_graph_destroy(g)
     for r in rows:
         r[6].free()
+
+
+def test_tune_cache_file(tmp_path, monkeypatch):
+    """With FEASM_TUNE_CACHE naming a file, the autotuner's result reaches a
+    context created later (as in another process): the file holds one line
+    per result keyed by GPU model, SM count and batch signature; a line edited
+    by hand is what a new context then takes; without the variable nothing is
+    known."""
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("FEASM_TUNE_CACHE", str(path))
+    c1 = feasm.fe_create(0)
+    pats, items = [], []
+    try:
+        for n, d in ((4, 3), (6, 1)):
+            D, n_dofs = wl.hex_q1_grid(n, d)
+            Kr = wl.laplace_q1_hex(1.0 / n) if d == 1 else wl.elasticity_q1_hex(1.0 / n)
+            p = feasm.Pattern(c1, torch.from_numpy(D).cuda(), n_dofs)
+            pats.append(p)
+            items.append((p, torch.from_numpy(wl.scaled_matrices(Kr, D.shape[0], seed=n)).cuda(),
+                          torch.empty(p.info["nnz"], dtype=torch.float64, device="cuda")))
+        assert feasm.fe_batch_tuned(c1, items, 0, feasm.FE_ATOMIC) is None
+        kind, tile, _ = feasm.fe_batch_autotune(c1, items, 0, feasm.FE_ATOMIC)
+        assert feasm.fe_batch_tuned(c1, items, 0, feasm.FE_ATOMIC) == (kind, tile)
+        lines = path.read_text().splitlines()
+        assert len(lines) == 1 and lines[0].split()[-2:] == [str(kind), str(tile)]
+        c2 = feasm.fe_create(0)
+        assert feasm.fe_batch_tuned(c2, items, 0, feasm.FE_ATOMIC) == (kind, tile)
+        assert feasm.fe_batch_tuned(c2, items, 0, feasm.FE_DETERMINISTIC) is None
+        feasm.fe_destroy(c2)
+        f = lines[0].split()
+        path.write_text(" ".join(f[:-2] + [str(feasm.FE_SCHED_WARP_PER_ELEMENT), "3"]) + "\n")
+        c3 = feasm.fe_create(0)
+        assert feasm.fe_batch_tuned(c3, items, 0, feasm.FE_ATOMIC) == (feasm.FE_SCHED_WARP_PER_ELEMENT, 3)
+        feasm.fe_destroy(c3)
+        monkeypatch.delenv("FEASM_TUNE_CACHE")
+        c4 = feasm.fe_create(0)
+        assert feasm.fe_batch_tuned(c4, items, 0, feasm.FE_ATOMIC) is None
+        feasm.fe_destroy(c4)
+    finally:
+        for p in pats:
+            p.free()
+        feasm.fe_destroy(c1)

@@ -123,6 +123,51 @@ def test_c3_p2_tets_permuted_spd(ctx, n):
     g.free()
 
 
+@pytest.mark.parametrize("case", ["tets_permuted", "hex_d3", "quads_q3", "scattered"])
+def test_atomic_locality_order(ctx, case):
+    """FE_ATOMIC through the locality order of the elements (forced on with
+    FE_KNOB_ATOMIC_ORDER = 2; the automatic choice takes it only for large
+    meshes with scattered numbering): within the row tolerance of the oracle
+    in both formats, and the deterministic modes unchanged.  Several seeds
+    (clusters) per mesh: the tet mesh has more than 16,384 blocks."""
+    from paper_2012_00585_gb300 import feasm
+    if case == "tets_permuted":
+        D, n_dofs = wl.tet_p2_kuhn(14, d=3, seed=21)  # 24,389 blocks: two clusters and a ragged one
+        K = wl.random_spd_matrices(D.shape[0], 30, seed=2)
+    elif case == "hex_d3":
+        D, n_dofs = wl.hex_q1_grid(7, 3)
+        K = wl.random_matrices(D.shape[0], 24, seed=3)
+    elif case == "quads_q3":
+        D, n_dofs = wl.quad_qp_grid(6, 3, 1)
+        K = wl.random_matrices(D.shape[0], 16, seed=4)
+    else:
+        rng = np.random.default_rng(9)
+        n_dofs = 700
+        D = np.stack([rng.choice(n_dofs - 50, 7, replace=False) for _ in range(300)]).astype(np.int32)
+        K = wl.random_matrices(D.shape[0], 7, seed=5)
+    feasm.fe_tune_set(ctx, feasm.FE_KNOB_ATOMIC_ORDER, 2)
+    try:
+        g = gu.GpuAssembly(ctx, D, n_dofs)
+    finally:
+        feasm.fe_tune_set(ctx, feasm.FE_KNOB_ATOMIC_ORDER, 0)
+    assert g.pattern.info["atomic_order"] == 1
+    pat = _check_pattern(g, D, n_dofs)
+    _run_all_modes(g, D, K, n_dofs, *pat)
+    # all-ones K: integer sums, exact whatever the order of the adds
+    ones = np.ones_like(K)
+    v_o = oracle.assemble_csr(D, ones, pat[0], pat[1])
+    for fmt in ("csr", "crac"):
+        assert np.array_equal(g.assemble(ones, fmt, feasm.FE_ATOMIC).cpu().numpy(), v_o)
+    g.free()
+    feasm.fe_tune_set(ctx, feasm.FE_KNOB_ATOMIC_ORDER, 1)
+    try:
+        g = gu.GpuAssembly(ctx, D, n_dofs)
+        assert g.pattern.info["atomic_order"] == 0
+        g.free()
+    finally:
+        feasm.fe_tune_set(ctx, feasm.FE_KNOB_ATOMIC_ORDER, 0)
+
+
 def test_c4_mixed_sizes_one_by_one(ctx):
     """Config 4's two element kinds: Q1 Laplace (8x8, d=1) and elasticity (24x24)."""
     for n, d in [(5, 1), (7, 1), (5, 3), (6, 3)]:
@@ -147,6 +192,7 @@ def test_c2_full_size_64cubed(ctx):
     g = gu.GpuAssembly(ctx, D, n_dofs)
     info = g.pattern.info
     assert info["nnz"] == 64_701_513 and info["n_ca"] == 14_527_112
+    assert info["atomic_order"] == 0  # natural numbering: elements stay in ascending order
     rp_o, ci_o = oracle.csr_pattern(D, n_dofs)
     rp, ci = g.csr_host()
     assert np.array_equal(rp, rp_o) and np.array_equal(ci, ci_o)
@@ -380,6 +426,7 @@ def test_c3_full_size_sampled_rows(ctx):
     g = gu.GpuAssembly(ctx, D, n_dofs)
     info = g.pattern.info
     assert info["nnz"] == 1_842_870_537 and info["block"] == 3
+    assert info["atomic_order"] == 1  # scattered numbering, 14.7 GB of values: the locality order is built
     rp_d, ci_d = g.pattern.csr()
     crp_d, ca_d = g.pattern.crac()
     Kd = wl.random_spd_matrices(D.shape[0], 30, seed=7, device="cuda", chunk=1 << 18)
