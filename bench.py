@@ -59,6 +59,8 @@ def parse(argv=None):
                          "Kuhn-split P2 tet mesh with permuted node ids (30x30 SPD K)")
     ap.add_argument("--meshes", type=int, default=256, help="batched workload: number of meshes")
     ap.add_argument("--tet-n", type=int, default=96, help="tet96 workload: hex grid side (96 = the 96^3 workload)")
+    ap.add_argument("--tet-natural", action="store_true",
+                    help="tet96 workload: keep the natural node numbering (no seeded permutation)")
     ap.add_argument("--rate", type=float, default=2000.0, help="served workload: mean arrivals per second")
     ap.add_argument("--duration", type=float, default=2.0, help="served workload: seconds of arrivals")
     return ap.parse_args(argv)
@@ -412,7 +414,8 @@ def c1_latency(ctx, feasm, dev, stream):
 def hbm_probe(dev, stream):
     """Live bandwidth of this GPU (2 GiB streamed, best of 6), from the
     benchmark's probe library (not the assembly library): read-only by the
-    SMs' loads, copy, and read-only by bulk copies (TMA).  The copy rate
+    SMs' 16-byte loads, copy, read-only by bulk copies (TMA), and read-only by
+    32-byte loads.  The copy rate
     matches the measured peak; loads alone stream about half of what bulk
     copies do."""
     import ctypes
@@ -423,19 +426,22 @@ def hbm_probe(dev, stream):
     vp = ctypes.c_void_p
     lib.feprobe_stream.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
     lib.feprobe_stream_bulk.argtypes = [vp, ctypes.c_int64, vp, vp, vp]
+    lib.feprobe_stream_v4.argtypes = [vp, ctypes.c_int64, vp, vp]
     n = 1 << 28
     a = torch.ones(n, dtype=torch.float64, device=dev)
     b = torch.empty(n, dtype=torch.float64, device=dev)
     sink = torch.zeros(1, dtype=torch.float64, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     out = {}
-    for name, dst, mult in (("read", None, 1), ("copy", b, 2), ("read_bulk", None, 1)):
+    for name, dst, mult in (("read", None, 1), ("copy", b, 2), ("read_bulk", None, 1), ("read_32B", None, 1)):
         best = 1e30
         for _ in range(6):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             if name == "read_bulk":
                 rc = lib.feprobe_stream_bulk(a.data_ptr(), n, sink.data_ptr(), status.data_ptr(), stream.cuda_stream)
+            elif name == "read_32B":
+                rc = lib.feprobe_stream_v4(a.data_ptr(), n, sink.data_ptr(), stream.cuda_stream)
             else:
                 rc = lib.feprobe_stream(a.data_ptr(), None if dst is None else dst.data_ptr(), n, sink.data_ptr(),
                                         stream.cuda_stream)
@@ -731,6 +737,34 @@ def run_batched(args, local_rank):
         res["schedule"] = {"kind": kind, "tile": tile}
         res["speedup_graph_vs_per_mesh"] = round(res["per_mesh"]["ms_median"] / res["graph"]["ms_median"], 3)
         fe.fe_batch_graph_destroy(g)
+        # per-mesh completion latency: when each mesh's result is complete,
+        # from the start of the step; one launch per mesh (an event after each
+        # launch) against one graph launch (the kernel's per-item timestamps)
+        reps = 5
+        lat_pm, lat_g = [], []
+        times = torch.zeros((len(meshes), 2), dtype=torch.int64, device=dev)
+        gt = fe.fe_batch_graph_create(ctx, [(p, K, v, times[k]) for k, (p, K, v, _, _) in enumerate(meshes)],
+                                      fe.FE_FORMAT_CSR, mode, 0, None, stream)
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in meshes]
+            e0.record(stream)
+            for (p, K, v, _, _), e in zip(meshes, ev):
+                fe.fe_assemble_csr(ctx, p, K, v, mode, 0, stream)
+                e.record(stream)
+            torch.cuda.synchronize()
+            lat_pm += [e0.elapsed_time(e) for e in ev]
+            fe.fe_batch_graph_launch(gt, stream)
+            torch.cuda.synchronize()
+            t = times.cpu()
+            lat_g += ((t[:, 1] - t[:, 0].min()).double() * 1e-6).tolist()
+        fe.fe_batch_graph_destroy(gt)
+        pct = lambda xs, q: round(float(statistics.quantiles(xs, n=100)[q - 1]), 3)
+        res["per_mesh_latency_ms"] = {
+            "per_mesh": {"p50": pct(lat_pm, 50), "p99": pct(lat_pm, 99), "max": round(max(lat_pm), 3)},
+            "graph": {"p50": pct(lat_g, 50), "p99": pct(lat_g, 99), "max": round(max(lat_g), 3)},
+            "meshes": len(meshes), "repeats": reps,
+            "definition": "time from the start of the step until a mesh's values are complete, over every mesh"}
         out[mode_name] = res
     hbm, _ = measured_peaks()
     best = min(out["det"]["graph"]["ms_median"], out["det"]["batched"]["ms_median"])
@@ -865,8 +899,11 @@ def run_tet(args, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
     ctx = fe.fe_create(local_rank)
+    for kv in args.knob:
+        name, value = kv.split("=")
+        fe.fe_tune_set(ctx, getattr(fe, "FE_KNOB_" + name.upper()), int(value))
     n = args.tet_n
-    D, n_dofs = wl.tet_p2_kuhn(n, d=3, seed=0)
+    D, n_dofs = wl.tet_p2_kuhn(n, d=3, seed=0, permute=not args.tet_natural)
     n_e, n_loc = D.shape
     N_ent = n_e * n_loc * n_loc
     with torch.cuda.stream(stream):
@@ -908,10 +945,12 @@ def run_tet(args, local_rank):
             "ms_per_step": det, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"{n}^3 hex grid, 6 Kuhn tets per cube, P2 (10 nodes), 3 DOF/node, node ids "
-                                   f"permuted ({n_dofs} DOFs, {n_e} elements, 30x30 SPD FP64 K on the device); "
+                                   f"{'natural' if args.tet_natural else 'permuted'} ({n_dofs} DOFs, {n_e} elements, "
+                                   "30x30 SPD FP64 K on the device); "
                                    "step = one deterministic CSR assembly",
                        "entries_per_assembly": N_ent, "nnz": nnz, "n_ca": info["n_ca"],
                        "gamma": round(info["n_ca"] / nnz, 4), "pattern_build_ms": round(build_ms, 2),
+                       "atomic_order": info["atomic_order"],
                        "l2": "inputs larger than L2 (K = %.1f GB)" % (8 * N_ent / 1e9)},
             "roofline": {"bound": "hbm", "achieved": round(B / (det * 1e-3) / 1e9, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(B / (det * 1e-3) / 1e9 / hbm, 4), "traffic": None, "peak_source": src,

@@ -376,6 +376,10 @@ typedef struct fe_batch_item {
     const fe_pattern *pattern;  /* built on the same context                     */
     const double *elem_mats;    /* device, [n_elem * n_loc * n_loc], read only    */
     double *values;             /* device, [nnz], written (or added to)           */
+    uint64_t *times_ns;         /* device, 2 entries, or NULL: written with the
+                                   GPU's global timer (ns) when the first tile of
+                                   this item started and when its last tile
+                                   finished (per-item latency inside one launch) */
 } fe_batch_item;
 
 /* Assemble n_items meshes in one persistent launch on `stream` (plus one

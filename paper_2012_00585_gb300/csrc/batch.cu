@@ -48,7 +48,31 @@ struct BatchItemDev {
     int64_t tile_begin;  // first global tile of this item
     int32_t nln, B, shape, map_bytes;
     int32_t staged;      // FE_SCHED_WARP_PER_ELEMENT_TMA: K_e moved by a bulk copy
+    uint64_t *times;     // the caller's [first tile started, last tile finished] (ns) or null
 };
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Per-item timestamps (items with a times array): tc holds two counters per
+// item, tiles started and tiles finished; the first start and the last
+// finish write the global timer.  Called by one thread per tile.
+__device__ __forceinline__ void tile_started(const BatchItemDev &it, int i, unsigned int *tc)
+{
+    if (it.times && atomicAdd(&tc[2 * i], 1u) == 0) it.times[0] = global_ns();
+}
+
+__device__ __forceinline__ void tile_finished(const BatchItemDev &it, int i, unsigned int *tc, int tile)
+{
+    if (!it.times) return;
+    __threadfence();
+    const unsigned int n_tiles = (unsigned int)((it.units + tile - 1) / tile);
+    if (atomicAdd(&tc[2 * i + 1], 1u) + 1 == n_tiles) it.times[1] = global_ns();
+}
 
 int shape_of(const fe_pattern *p)
 {
@@ -301,10 +325,14 @@ __host__ __device__ constexpr size_t batch_tables_bytes(int warps)
 // bulk-copy schedule measured slower).
 constexpr int sched_threads(int) { return SCHED_THREADS; }
 
+// The row-gather schedule is capped at 80 registers (3 blocks of 8 warps per
+// SM): measured on the 256-mesh batch, 6.54 ms against 6.73 ms at 64
+// registers (which spilled in the per-tile call) and 7.65 ms at 128.
 template <bool CRAC, int SCHED>
-__global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW ? 4 : 1) k_batch(const BatchItemDev *__restrict__ items, int n_items,
+__global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW ? 3 : 1) k_batch(const BatchItemDev *__restrict__ items, int n_items,
                                                          int64_t total_tiles, int tile, int cap, int accumulate,
-                                                         unsigned long long *counter, int stage, int *status)
+                                                         unsigned long long *counter, int stage, int *status,
+                                                         unsigned int *tc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long block_tile;
@@ -319,8 +347,10 @@ __global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW 
             const unsigned long long t = block_tile;
             __syncthreads();
             if (t >= (unsigned long long)total_tiles) break;
-            const BatchItemDev &it = items[find_item(items, n_items, (int64_t)t)];
+            const int ii = find_item(items, n_items, (int64_t)t);
+            const BatchItemDev &it = items[ii];
             const int64_t u0 = ((int64_t)t - it.tile_begin) * tile, u1 = min(u0 + tile, it.units);
+            if (threadIdx.x == 0) tile_started(it, ii, tc);
             const int B = it.B, nln = it.nln, n_loc = nln * B;
             const int NN = n_loc * n_loc;
             for (int64_t e = u0; e < u1; ++e) {
@@ -355,6 +385,7 @@ __global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW 
                 }
                 __syncthreads();
             }
+            if (threadIdx.x == 0) tile_finished(it, ii, tc, tile);
         }
         return;
     }
@@ -384,8 +415,10 @@ __global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW 
             if (lane == 0) t = atomicAdd(counter, 1ull);
             t = __shfl_sync(0xffffffffu, t, 0);
             if (t >= (unsigned long long)total_tiles) break;
-            const BatchItemDev &it = items[find_item(items, n_items, (int64_t)t)];
+            const int ii = find_item(items, n_items, (int64_t)t);
+            const BatchItemDev &it = items[ii];
             const int64_t u0 = ((int64_t)t - it.tile_begin) * tile, u1 = min(u0 + tile, it.units);
+            if (lane == 0) tile_started(it, ii, tc);
             if (it.staged) {
                 const bool ok = it.map_bytes == 1
                                     ? staged_tile_any<uint8_t, CRAC>(&it, it.shape, u0, u1, lane, kst, stage, bar,
@@ -402,6 +435,8 @@ __global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW 
                     else atomic_elem_any<uint16_t, CRAC>(&it, it.shape, e, lane, base_s, k_s, off_s);
                 }
             }
+            __syncwarp();
+            if (lane == 0) tile_finished(it, ii, tc, tile);
         }
     } else {
         for (;;) {
@@ -409,8 +444,10 @@ __global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW 
             if (lane == 0) t = atomicAdd(counter, 1ull);
             t = __shfl_sync(0xffffffffu, t, 0);
             if (t >= (unsigned long long)total_tiles) break;
-            const BatchItemDev &it = items[find_item(items, n_items, (int64_t)t)];
+            const int ii = find_item(items, n_items, (int64_t)t);
+            const BatchItemDev &it = items[ii];
             const int64_t u0 = ((int64_t)t - it.tile_begin) * tile, u1 = min(u0 + tile, it.units);
+            if (lane == 0) tile_started(it, ii, tc);
             if (SCHED == FE_SCHED_WARP_PER_ROW) {
                 if (it.shape == SH_4_1 || it.shape == SH_8_1) {
                     // one-DOF rows: several per warp (gather_small.cuh)
@@ -451,6 +488,8 @@ __global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW 
                     if (FE_IN_BOUNDS(slot, it.g.nnz, it.g.status)) atomicAdd(it.values + slot, __ldcs(it.K + x));
                 }
             }
+            __syncwarp();
+            if (lane == 0) tile_finished(it, ii, tc, tile);
         }
     }
 }
@@ -485,7 +524,9 @@ int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
         const fe_pattern *p = items[i].pattern;
         if (!p || p->ctx != ctx) return FE_ERR_INVALID_ARG;
         if ((p->n_e > 0 && !items[i].elem_mats) || (p->nnz > 0 && !items[i].values)) return FE_ERR_INVALID_ARG;
-        if (((uintptr_t)items[i].elem_mats & 7u) || ((uintptr_t)items[i].values & 7u)) return FE_ERR_INVALID_ARG;
+        if (((uintptr_t)items[i].elem_mats & 7u) || ((uintptr_t)items[i].values & 7u) ||
+            ((uintptr_t)items[i].times_ns & 7u))
+            return FE_ERR_INVALID_ARG;
         if (format == FE_FORMAT_CSR && !p->map_csr) return FE_ERR_NOT_BUILT;
         if (format == FE_FORMAT_CRAC && (!p->map_crac || !p->col_align || !p->map_crac_blk)) return FE_ERR_NOT_BUILT;
         if (mode == FE_DETERMINISTIC && !p->adj) return FE_ERR_NOT_BUILT;
@@ -508,6 +549,7 @@ int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
         d.B = p->B;
         d.map_bytes = p->map_bytes;
         const int nn = p->n_loc * p->n_loc;
+        d.times = items[i].times_ns;
         d.staged = d.shape != SH_GENERIC && nn <= STAGE_MAX && (nn * 8) % 16 == 0 &&
                    ((uintptr_t)items[i].elem_mats & 15u) == 0;
         if (d.staged) plan.stage = std::max(plan.stage, (nn + 1) & ~1);
@@ -534,7 +576,7 @@ size_t batch_smem(int mode, int sched, int cap, int stage)
 
 template <bool CRAC, int SCHED>
 int launch_batch_t(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t total, int tile, int cap, int acc,
-                   unsigned long long *counter, size_t smem, int stage, cudaStream_t s)
+                   unsigned long long *counter, size_t smem, int stage, unsigned int *tc, cudaStream_t s)
 {
     auto kern = k_batch<CRAC, SCHED>;
     constexpr int threads = sched_threads(SCHED);
@@ -544,34 +586,35 @@ int launch_batch_t(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t tota
     if (per_sm < 1) return FE_ERR_UNSUPPORTED;
     const int64_t want = SCHED == FE_SCHED_BLOCK_PER_ELEMENT ? total : (total + threads / 32 - 1) / (threads / 32);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * per_sm, want));
-    kern<<<grid, threads, smem, s>>>(d_items, n, total, tile, cap, acc, counter, stage, ctx->d_status);
+    kern<<<grid, threads, smem, s>>>(d_items, n, total, tile, cap, acc, counter, stage, ctx->d_status, tc);
     fe_note_launch();
     FE_CUDA(cudaGetLastError());
     return FE_OK;
 }
 
 int launch_batch(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t total, int format, int mode, int acc,
-                 int sched, int tile, int cap, int stage, unsigned long long *counter, cudaStream_t s)
+                 int sched, int tile, int cap, int stage, unsigned long long *counter, unsigned int *tc,
+                 cudaStream_t s)
 {
     const size_t smem = batch_smem(mode, sched, cap, stage);
     if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
     const bool crac = format == FE_FORMAT_CRAC;
     if (mode == FE_DETERMINISTIC)
-        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s)
-                    : launch_batch_t<false, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s);
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s);
     switch (sched) {
     case FE_SCHED_THREAD_PER_ENTRY:
-        return crac ? launch_batch_t<true, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s)
-                    : launch_batch_t<false, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s);
+        return crac ? launch_batch_t<true, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s)
+                    : launch_batch_t<false, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s);
     case FE_SCHED_BLOCK_PER_ELEMENT:
-        return crac ? launch_batch_t<true, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s)
-                    : launch_batch_t<false, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s);
+        return crac ? launch_batch_t<true, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s)
+                    : launch_batch_t<false, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s);
     case FE_SCHED_WARP_PER_ELEMENT_TMA:
-        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s)
-                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s);
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s);
     default:
-        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s)
-                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, s);
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s);
     }
 }
 
@@ -762,16 +805,19 @@ int run_batch(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
     BatchItemDev *d_items = nullptr;
     unsigned long long *counter = nullptr;
     FE_TRY(fe_alloc(ctx, (void **)&d_items, sizeof(BatchItemDev) * n, s));
-    int rc = fe_alloc(ctx, (void **)&counter, sizeof(unsigned long long), s);
+    // the tile counter, then two tile counters per item (per-item timestamps)
+    const size_t cbytes = sizeof(unsigned long long) + sizeof(unsigned int) * 2 * (size_t)n;
+    int rc = fe_alloc(ctx, (void **)&counter, cbytes, s);
     if (rc == FE_OK) rc = upload(ctx, d_items, plan.host.data(), sizeof(BatchItemDev) * n, s);
-    if (rc == FE_OK && cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s) != cudaSuccess) rc = FE_ERR_DEVICE;
+    if (rc == FE_OK && cudaMemsetAsync(counter, 0, cbytes, s) != cudaSuccess) rc = FE_ERR_DEVICE;
     if (rc == FE_OK && mode == FE_ATOMIC && !acc) {
         k_batch_zero<<<ctx->num_sms * 4, 256, 0, s>>>(d_items, n);
         fe_note_launch();
         if (cudaGetLastError() != cudaSuccess) rc = FE_ERR_DEVICE;
     }
     if (rc == FE_OK && plan.total_tiles > 0)
-        rc = launch_batch(ctx, d_items, n, plan.total_tiles, format, mode, acc, sc.kind, sc.tile, plan.cap, plan.stage, counter, s);
+        rc = launch_batch(ctx, d_items, n, plan.total_tiles, format, mode, acc, sc.kind, sc.tile, plan.cap, plan.stage,
+                          counter, (unsigned int *)(counter + 1), s);
     fe_free_async(d_items, s);
     fe_free_async(counter, s);
     return rc;
@@ -917,8 +963,9 @@ int fe_batch_graph_create(fe_ctx *ctx, const fe_batch_item *items, int32_t n_ite
     g->ctx = ctx;
     int rc = FE_OK;
     // the graph's own item table and counter live as long as the graph
+    const size_t cbytes = sizeof(unsigned long long) + sizeof(unsigned int) * 2 * (size_t)n_items;
     if (cudaMalloc((void **)&g->d_items, sizeof(BatchItemDev) * n_items) != cudaSuccess ||
-        cudaMalloc((void **)&g->counter, sizeof(unsigned long long)) != cudaSuccess)
+        cudaMalloc((void **)&g->counter, cbytes) != cudaSuccess)
         rc = FE_ERR_OOM;
     // uploaded on the caller's stream (ordered after the work that built the patterns)
     if (rc == FE_OK && (cudaMemcpyAsync(g->d_items, plan.host.data(), sizeof(BatchItemDev) * n_items,
@@ -929,14 +976,14 @@ int fe_batch_graph_create(fe_ctx *ctx, const fe_batch_item *items, int32_t n_ite
     if (rc == FE_OK && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = FE_ERR_DEVICE;
     if (rc == FE_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = FE_ERR_DEVICE;
     if (rc == FE_OK) {
-        int lrc = cudaMemsetAsync(g->counter, 0, sizeof(unsigned long long), cs) == cudaSuccess ? FE_OK : FE_ERR_DEVICE;
+        int lrc = cudaMemsetAsync(g->counter, 0, cbytes, cs) == cudaSuccess ? FE_OK : FE_ERR_DEVICE;
         if (lrc == FE_OK && mode == FE_ATOMIC && !accumulate) {
             k_batch_zero<<<ctx->num_sms * 4, 256, 0, cs>>>(g->d_items, n_items);
             if (cudaGetLastError() != cudaSuccess) lrc = FE_ERR_DEVICE;
         }
         if (lrc == FE_OK && plan.total_tiles > 0)
             lrc = launch_batch(ctx, g->d_items, n_items, plan.total_tiles, format, mode, accumulate, sc.kind, sc.tile,
-                               plan.cap, plan.stage, g->counter, cs);
+                               plan.cap, plan.stage, g->counter, (unsigned int *)(g->counter + 1), cs);
         const cudaError_t ec = cudaStreamEndCapture(cs, &g->graph);
         rc = lrc != FE_OK ? lrc : (ec == cudaSuccess ? FE_OK : FE_ERR_DEVICE);
     }

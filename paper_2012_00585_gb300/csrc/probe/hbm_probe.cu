@@ -33,6 +33,30 @@ __global__ void k_hbm_probe(const double2 *__restrict__ src, double2 *__restrict
     if (s == 1.2345e300) *sink = s;  // keeps the loads alive
 }
 
+// Read-only stream by 32-byte (256-bit) loads, 4 independent loads in flight
+// per thread (src 32-byte aligned, n a multiple of 4).
+__global__ void k_hbm_probe_v4(const double *__restrict__ src, int64_t n4, double *sink)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += 4 * stride) {
+        double v[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t k = i + u * stride;
+            if (k < n4)
+                asm volatile("ld.global.nc.L1::no_allocate.v4.f64 {%0,%1,%2,%3}, [%4];"
+                             : "=d"(v[u][0]), "=d"(v[u][1]), "=d"(v[u][2]), "=d"(v[u][3])
+                             : "l"(src + 4 * k));
+            else
+                v[u][0] = v[u][1] = v[u][2] = v[u][3] = 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s += v[u][0] + v[u][1] + v[u][2] + v[u][3];
+    }
+    if (s == 1.2345e300) *sink = s;  // keeps the loads alive
+}
+
 // The same read-only stream moved by the bulk-copy (TMA) engine: chunks of
 // PROBE_CHUNK bytes into a ring of PROBE_STAGES shared-memory stages per
 // block (one mbarrier each).  Waits are bounded: a wait that runs out sets
@@ -102,6 +126,16 @@ int feprobe_stream(const double *src, double *dst, int64_t n, double *sink, void
     const int sms = sms_of_current();
     if (!src || !sink || n < 2 || ((uintptr_t)src & 15u) || ((uintptr_t)dst & 15u) || sms <= 0) return -1;
     k_hbm_probe<<<sms * 8, 256, 0, (cudaStream_t)stream>>>((const double2 *)src, (double2 *)dst, n / 2, sink);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// The read-only stream by 32-byte loads (src 32-byte aligned, n a multiple
+// of 4).  0 or -1.
+int feprobe_stream_v4(const double *src, int64_t n, double *sink, void *stream)
+{
+    const int sms = sms_of_current();
+    if (!src || !sink || n < 4 || (n & 3) || ((uintptr_t)src & 31u) || sms <= 0) return -1;
+    k_hbm_probe_v4<<<sms * 8, 256, 0, (cudaStream_t)stream>>>(src, n / 4, sink);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

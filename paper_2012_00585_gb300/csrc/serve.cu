@@ -344,7 +344,13 @@ void scheduler_loop(fe_server *sv)
                 sv->cv_build.notify_one();
             }
         }
-        // launches: ready requests grouped by (format, mode)
+        // launches: ready requests grouped by (format, mode).  The members
+        // are taken from the ready queue under the lock; their memory, the
+        // element generation and the batched assembly are issued with the
+        // lock released (an allocation that grows the memory pool can take
+        // milliseconds), and the outcome is booked under the lock again.
+        // Members are marked RUNNING meanwhile: no other thread touches a
+        // RUNNING ticket (release, cancel and the watchdog skip it).
         while (!sv->ready.empty()) {
             const uint64_t id0 = sv->ready.front();
             const int fmt = sv->tickets[id0].req.format, mode = sv->tickets[id0].req.mode;
@@ -360,14 +366,18 @@ void scheduler_loop(fe_server *sv)
                 sv->next_stream = (sv->next_stream + 1) % sv->n_small;
             }
             cudaStream_t s = sv->streams[g.stream];
-            if (cudaEventCreate(&g.t0) != cudaSuccess || cudaEventRecord(g.t0, s) != cudaSuccess) {
-                cudaGetLastError();
-                if (g.t0) cudaEventDestroy(g.t0);
-                g.t0 = nullptr;
-            }
-            std::vector<fe_batch_item> items;
+            struct Member {
+                uint64_t id;
+                Ticket *t;
+                fe_request req;
+                const fe_pattern *pattern;
+                size_t k_bytes, v_bytes;
+                double *values = nullptr, *K = nullptr;
+                int rc = FE_OK;
+            };
+            std::vector<Member> mem;
             const int cap = big ? 1 : sv->max_batch;
-            for (auto it = sv->ready.begin(); it != sv->ready.end() && (int)items.size() < cap;) {
+            for (auto it = sv->ready.begin(); it != sv->ready.end() && (int)mem.size() < cap;) {
                 Ticket &t = sv->tickets[*it];
                 if (t.req.format != fmt || t.req.mode != mode || (sv->n_big > 0 && is_big(t.req) != big)) {
                     ++it;
@@ -377,19 +387,47 @@ void scheduler_loop(fe_server *sv)
                     it = sv->ready.erase(it);
                     continue;
                 }
-                int rc = FE_OK;
-                t.v_bytes = (size_t)t.pattern->nnz * 8;
-                rc = fe_alloc(sv->ctx, (void **)&t.values, t.v_bytes, s);
-                if (rc == FE_OK && !t.req.elem_mats) {
-                    rc = fe_alloc(sv->ctx, (void **)&t.K, t.k_bytes, s);
-                    if (rc == FE_OK)
-                        rc = launch_generate(t.req.k_ref, t.req.dofs_per_elem, t.req.n_elem, t.req.seed, t.K,
-                                             sv->ctx->num_sms, s);
+                t.state = FE_STATE_RUNNING;
+                t.stream = g.stream;
+                mem.push_back(Member{*it, &t, t.req, t.pattern, t.k_bytes, (size_t)t.pattern->nnz * 8});
+                it = sv->ready.erase(it);
+            }
+            if (mem.empty()) continue;
+            progress = true;
+            lk.unlock();
+            const double t_launch = now_us();
+            if (cudaEventCreate(&g.t0) != cudaSuccess || cudaEventRecord(g.t0, s) != cudaSuccess) {
+                cudaGetLastError();
+                if (g.t0) cudaEventDestroy(g.t0);
+                g.t0 = nullptr;
+            }
+            std::vector<fe_batch_item> items;
+            for (Member &m : mem) {
+                m.rc = fe_alloc(sv->ctx, (void **)&m.values, m.v_bytes, s);
+                if (m.rc == FE_OK && !m.req.elem_mats) {
+                    m.rc = fe_alloc(sv->ctx, (void **)&m.K, m.k_bytes, s);
+                    if (m.rc == FE_OK)
+                        m.rc = launch_generate(m.req.k_ref, m.req.dofs_per_elem, m.req.n_elem, m.req.seed, m.K,
+                                               sv->ctx->num_sms, s);
                 }
-                if (rc == FE_OK && t.req.ready_event) cudaStreamWaitEvent(s, (cudaEvent_t)t.req.ready_event, 0);
-                if (rc != FE_OK) {
-                    finish(sv, t, rc);
-                    it = sv->ready.erase(it);
+                if (m.rc == FE_OK && m.req.ready_event) cudaStreamWaitEvent(s, (cudaEvent_t)m.req.ready_event, 0);
+                if (m.rc == FE_OK) items.push_back(fe_batch_item{m.pattern, m.K ? m.K : m.req.elem_mats, m.values});
+            }
+            int rc = FE_OK;
+            if (!items.empty()) {
+                FeRange range("serve: batched launch");
+                rc = fe_assemble_batch(sv->ctx, items.data(), (int32_t)items.size(), fmt, mode, 0, nullptr, s);
+                if (rc == FE_OK && cudaEventCreate(&g.done) != cudaSuccess) rc = FE_ERR_DEVICE;
+                if (rc == FE_OK && cudaEventRecord(g.done, s) != cudaSuccess) rc = FE_ERR_DEVICE;
+            }
+            lk.lock();
+            for (Member &m : mem) {
+                Ticket &t = *m.t;
+                t.values = m.values;
+                t.K = m.K;
+                t.v_bytes = m.v_bytes;
+                if (m.rc != FE_OK || rc != FE_OK) {
+                    finish(sv, t, m.rc != FE_OK ? m.rc : rc);
                     continue;
                 }
                 // footprint: the values charge becomes exact
@@ -399,23 +437,10 @@ void scheduler_loop(fe_server *sv)
                     sv->in_use -= std::min(drop, sv->in_use);
                     t.v_charged = t.v_bytes;
                 }
-                t.state = FE_STATE_RUNNING;
-                t.t_start = now_us();
-                t.stream = g.stream;
-                items.push_back(fe_batch_item{t.pattern, t.K ? t.K : t.req.elem_mats, t.values});
-                g.ids.push_back(*it);
-                it = sv->ready.erase(it);
+                t.t_start = t_launch;
+                g.ids.push_back(m.id);
             }
-            if (items.empty()) {
-                if (g.t0) cudaEventDestroy(g.t0);
-                continue;
-            }
-            FeRange range("serve: batched launch");
-            int rc = fe_assemble_batch(sv->ctx, items.data(), (int32_t)items.size(), fmt, mode, 0, nullptr, s);
-            if (rc == FE_OK && cudaEventCreate(&g.done) != cudaSuccess) rc = FE_ERR_DEVICE;
-            if (rc == FE_OK && cudaEventRecord(g.done, s) != cudaSuccess) rc = FE_ERR_DEVICE;
-            if (rc != FE_OK) {
-                for (uint64_t id : g.ids) finish(sv, sv->tickets[id], rc);
+            if (g.ids.empty()) {
                 if (g.done) cudaEventDestroy(g.done);
                 if (g.t0) cudaEventDestroy(g.t0);
                 continue;
@@ -423,7 +448,6 @@ void scheduler_loop(fe_server *sv)
             ++sv->stats.launches;
             sv->stats.batched_requests += g.ids.size();
             sv->inflight.push_back(std::move(g));
-            progress = true;
         }
         if (!progress) sv->cv.wait_for(lk, std::chrono::microseconds(sv->inflight.empty() ? 2000 : 20));
     }

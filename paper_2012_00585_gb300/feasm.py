@@ -96,7 +96,8 @@ class fe_schedule(ctypes.Structure):
 
 
 class fe_batch_item(ctypes.Structure):
-    _fields_ = [("pattern", ctypes.c_void_p), ("elem_mats", ctypes.c_void_p), ("values", ctypes.c_void_p)]
+    _fields_ = [("pattern", ctypes.c_void_p), ("elem_mats", ctypes.c_void_p), ("values", ctypes.c_void_p),
+                ("times_ns", ctypes.c_void_p)]
 
 
 FE_STATE_PENDING = 0
@@ -372,13 +373,15 @@ def fe_spmv_crac(ctx, pattern, values, x, y, stream=None):
 
 
 def _items(items):
-    """items: sequence of (pattern handle or Pattern, K tensor/addr, values tensor/addr)."""
+    """items: sequence of (pattern handle or Pattern, K tensor/addr, values tensor/addr[, times tensor/addr])."""
     arr = (fe_batch_item * max(len(items), 1))()
-    for k, (pat, K, v) in enumerate(items):
+    for k, item in enumerate(items):
+        pat, K, v = item[:3]
         h = pat.handle if isinstance(pat, Pattern) else pat
         arr[k].pattern = h.value if isinstance(h, ctypes.c_void_p) else h
         arr[k].elem_mats = _addr(K)
         arr[k].values = _addr(v)
+        arr[k].times_ns = _addr(item[3]) if len(item) > 3 else None
     return arr
 
 

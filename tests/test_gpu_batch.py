@@ -259,3 +259,31 @@ def test_tune_cache_file(tmp_path, monkeypatch):
         for p in pats:
             p.free()
         feasm.fe_destroy(c1)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_per_item_timestamps(ctx, batch, mode):
+    """With a times array per item, one batched launch (and its graph replay)
+    records when each item's first tile started and its last tile finished:
+    every item gets both, start <= finish, all within the launch, and the
+    results are unchanged."""
+    import torch
+    from paper_2012_00585_gb300 import feasm
+    times = torch.zeros((len(batch), 2), dtype=torch.int64, device="cuda")
+    items = [(r["pat"], r["Kd"], r["v"], times[k]) for k, r in enumerate(batch)]
+    for launch in ("direct", "graph"):
+        times.zero_()
+        for r in batch:
+            r["v"].fill_(float("nan"))
+        if launch == "direct":
+            feasm.fe_assemble_batch(ctx, items, 0, mode)
+        else:
+            g = feasm.fe_batch_graph_create(ctx, items, 0, mode)
+            feasm.fe_batch_graph_launch(g)
+        torch.cuda.synchronize()
+        t = times.cpu().numpy()
+        assert np.all(t[:, 0] > 0) and np.all(t[:, 1] >= t[:, 0])
+        assert t[:, 1].max() - t[:, 0].min() < 10 * 10 ** 9  # one launch, well under 10 s
+        _check(batch, mode)
+        if launch == "graph":
+            feasm.fe_batch_graph_destroy(g)
