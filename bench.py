@@ -1169,6 +1169,9 @@ def serve_trace(ctx, traffic, arrivals, kinds, n_streams, max_batch, warm_s=0.0,
            "p50_ms_small_warm": _pct(sel(lambda x: not x[1] and x[2]), 50),
            "p99_ms_small_warm": _pct(sel(lambda x: not x[1] and x[2]), 99),
            "p99_ms_large": _pct(sel(lambda x: x[1]), 99), "p99_ms_cold": _pct(sel(lambda x: not x[2]), 99),
+           "p50_ms_large_warm": _pct(sel(lambda x: x[1] and x[2]), 50),
+           "p99_ms_large_warm": _pct(sel(lambda x: x[1] and x[2]), 99),
+           "p99_ms_large_cold": _pct(sel(lambda x: x[1] and not x[2]), 99),
            "assembly_p50_ms": _pct(asm, 50), "assembly_p99_ms": _pct(asm, 99),
            "Gentries_per_s": round(ent / window_s / 1e9, 2) if window_s > 0 else None,
            "drain_s": round(drain_s, 3) if drain_s is not None else None, "keeps_pace": keeps_pace,

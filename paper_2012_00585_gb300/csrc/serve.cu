@@ -599,7 +599,7 @@ int fe_server_start(fe_ctx *ctx, int32_t n_streams, int32_t max_batch, size_t hb
     sv->n_small = n_streams;
     if (!sv->strict_fifo) {
         int least = 0, greatest = 0;
-        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) rc = FE_ERR_DEVICE;
+        if (rc == FE_OK && cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) rc = FE_ERR_DEVICE;
         for (int k = 0; k < N_BIG_STREAMS && rc == FE_OK; ++k) {
             cudaStream_t s;
             if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest) != cudaSuccess) rc = FE_ERR_DEVICE;
@@ -607,9 +607,13 @@ int fe_server_start(fe_ctx *ctx, int32_t n_streams, int32_t max_batch, size_t hb
         }
         if (rc == FE_OK) sv->n_big = N_BIG_STREAMS;
     }
+    // pattern builds are on the critical path of every cold request: their
+    // streams take the highest priority, like the large requests' launches
+    int least = 0, greatest = 0;
+    if (rc == FE_OK && cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) rc = FE_ERR_DEVICE;
     for (int k = 0; k < N_BUILDERS && rc == FE_OK; ++k) {
         cudaStream_t s;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) rc = FE_ERR_DEVICE;
+        if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest) != cudaSuccess) rc = FE_ERR_DEVICE;
         else sv->build_streams.push_back(s);
     }
     if (rc == FE_OK) sv->build_stream = sv->build_streams[0];
