@@ -470,6 +470,9 @@ typedef struct fe_server_stats {
     int64_t bytes_in_use, budget_bytes, cached_patterns;
     int64_t rebuilds;  /* builds of a key whose pattern had been evicted       */
     int64_t expired;   /* requests failed by the watchdog (deadline passed)    */
+    int64_t admission_waits;    /* times the admission queue found a request that
+                                   did not fit the budget                     */
+    int64_t peak_bytes_in_use;  /* largest bytes charged at once                */
 } fe_server_stats;
 
 /* One span of device work seen by the server: a launched group of requests

@@ -162,10 +162,12 @@ size_t values_estimate(const fe_request &r, const fe_pattern *p)
 // request drops its hold only after its completion event was seen, and the
 // builder waits for each build): its memory is released stream-ordered on the
 // build stream, without a host wait under the lock.  Caller holds the lock.
-void evict_for(fe_server *sv, size_t need)
+void evict_for(fe_server *sv, size_t need, std::unordered_set<uint64_t> &wanted, bool &wanted_ready)
 {
-    std::unordered_set<uint64_t> wanted;
-    for (uint64_t id : sv->pending) wanted.insert(sv->tickets[id].req.pattern_key);
+    if (!wanted_ready) {  // keys queued requests will use, gathered once per admission pass
+        for (uint64_t id : sv->pending) wanted.insert(sv->tickets[id].req.pattern_key);
+        wanted_ready = true;
+    }
     while (sv->in_use + need > sv->budget) {
         uint64_t victim = 0;
         bool found = false;
@@ -290,12 +292,22 @@ void scheduler_loop(fe_server *sv)
             sv->cv_done.notify_all();
         }
         if (expire_overdue(sv)) progress = true;
-        // admission (arrival order)
-        while (!sv->pending.empty()) {
-            const uint64_t id = sv->pending.front();
+        // admission, in arrival order.  A request that does not fit waits
+        // for memory; requests behind it keep their order, except that small
+        // ones (a footprint under 1/16 of the budget) may pass a waiting
+        // large one: their memory turns over within milliseconds, so the
+        // large request still gets its memory as soon as in-flight large
+        // work completes, while small requests do not queue behind it.
+        bool blocked = false;
+        std::unordered_set<uint64_t> wanted;
+        bool wanted_ready = false;
+        int passed = 0;  // requests looked at behind a waiting one (bounded: the lock is held)
+        for (auto it = sv->pending.begin(); it != sv->pending.end();) {
+            if (blocked && ++passed > 256) break;
+            const uint64_t id = *it;
             Ticket &t = sv->tickets[id];
             if (t.state == FE_STATE_CANCELLED) {
-                sv->pending.pop_front();
+                it = sv->pending.erase(it);
                 continue;
             }
             auto ce = sv->cache.find(t.req.pattern_key);
@@ -305,16 +317,28 @@ void scheduler_loop(fe_server *sv)
             const size_t v_est = values_estimate(t.req, p);
             const size_t need = k_bytes + v_est + (cached ? 0 : pattern_estimate(t.req));
             if (need > sv->budget) {
-                sv->pending.pop_front();
+                it = sv->pending.erase(it);
                 finish(sv, t, FE_ERR_ADMISSION);
                 progress = true;
                 continue;
             }
             if (sv->strict_fifo && sv->active > 0) break;
-            if (sv->in_use + need > sv->budget) evict_for(sv, need);
-            if (sv->in_use + need > sv->budget) break;  // wait for memory to free up
-            sv->pending.pop_front();
+            const bool small = need <= sv->budget / 16;
+            if (blocked && (!small || sv->strict_fifo)) {
+                ++it;  // behind a waiting request: only small ones pass
+                continue;
+            }
+            if (sv->in_use + need > sv->budget) evict_for(sv, need, wanted, wanted_ready);
+            if (sv->in_use + need > sv->budget) {  // wait for memory to free up
+                if (!blocked) ++sv->stats.admission_waits;
+                blocked = true;
+                if (sv->strict_fifo) break;
+                ++it;
+                continue;
+            }
+            it = sv->pending.erase(it);
             sv->in_use += need;
+            sv->stats.peak_bytes_in_use = std::max(sv->stats.peak_bytes_in_use, (int64_t)sv->in_use);
             t.foot = need;
             t.k_bytes = k_bytes;
             t.v_charged = v_est;

@@ -127,7 +127,7 @@ class fe_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "admitted", "completed", "failed", "cancelled",
                                               "launches", "batched_requests", "patterns_built", "evictions",
                                               "bytes_in_use", "budget_bytes", "cached_patterns", "rebuilds",
-                                              "expired")]
+                                              "expired", "admission_waits", "peak_bytes_in_use")]
 
 
 class fe_span(ctypes.Structure):

@@ -369,3 +369,47 @@ def test_timeline_and_one_off_eviction(ctx):
         assert all(0 <= a <= b for a, b, _, _ in spans)
     finally:
         fe.fe_server_stop(sv)
+
+
+def test_small_request_passes_a_waiting_large_one(ctx):
+    """Admission keeps arrival order, except that a small request may pass a
+    large one waiting for memory.  Request A holds its memory on the GPU (its
+    assembly waits for an event recorded after a bounded sleep kernel on
+    another stream); B, as large and on a new mesh, cannot fit beside A and
+    waits; S, tiny, arrives after B and completes while B is still waiting.
+    Then A, B and S are all exact."""
+    import torch
+    from paper_2012_00585_gb300 import feasm as fe
+    D, n_dofs = wl.hex_q1_grid(20, 3)
+    Kr = wl.elasticity_q1_hex(1 / 20)
+    Dd, Krd = torch.from_numpy(D).cuda(), torch.from_numpy(Kr).cuda()
+    Ds, ns = wl.hex_q1_grid(3, 1)
+    Krs = wl.laplace_q1_hex(1 / 3)
+    Dsd, Krsd = torch.from_numpy(Ds).cuda(), torch.from_numpy(Krs).cuda()
+    n_e, n_loc = D.shape
+    # the server's charge for a request on a new mesh: K, values bound, pattern bound
+    need = 2 * n_e * n_loc * n_loc * 8 + n_e * n_loc * n_loc * 6 + n_dofs * 64 + (1 << 20)
+    sv = fe.fe_server_start(ctx, 4, 8, hbm_budget_bytes=int(1.3 * need))
+    try:
+        side = torch.cuda.Stream()
+        ev = torch.cuda.Event()
+        with torch.cuda.stream(side):
+            torch.cuda._sleep(int(1.5e9))  # about 0.7 s at GB300 clocks
+            ev.record(side)
+        (ta,) = fe.fe_batch_submit(sv, [fe.make_request(1, Dd, n_dofs, k_ref=Krd, seed=1, ready_event=ev)])
+        (tb,) = fe.fe_batch_submit(sv, [fe.make_request(2, Dd, n_dofs, k_ref=Krd, seed=2)])
+        (ts,) = fe.fe_batch_submit(sv, [fe.make_request(3, Dsd, ns, k_ref=Krsd, seed=3)])
+        rs = fe.fe_wait(sv, ts, 30)
+        rb = fe.fe_poll(sv, tb)
+        assert rs["state"] == fe.FE_STATE_DONE
+        assert rb["state"] == fe.FE_STATE_PENDING  # still waiting for A's memory
+        for t, (DD, nd, KR, seed) in ((ta, (D, n_dofs, Kr, 1)), (tb, (D, n_dofs, Kr, 2)), (ts, (Ds, ns, Krs, 3))):
+            r = fe.fe_wait(sv, t, 60)
+            assert r["state"] == fe.FE_STATE_DONE, r
+            _, _, v_o, _ = _oracle_values(DD, nd, KR, seed)
+            assert np.array_equal(_values_of(fe, r).view(np.uint64), v_o.view(np.uint64))
+            fe.fe_release(sv, t)
+        st = fe.fe_server_stats_get(sv)
+        assert st["admission_waits"] >= 1 and st["peak_bytes_in_use"] <= st["budget_bytes"]
+    finally:
+        fe.fe_server_stop(sv)
