@@ -1073,7 +1073,7 @@ def serve_trace(ctx, traffic, arrivals, kinds, n_streams, max_batch, warm_s=0.0,
             while tickets[k] is None:
                 time.sleep(1e-4)
             r = fe.fe_wait(sv, tickets[k], 900)
-            res[k] = (r["state"], r["t_submit_us"], r["t_start_us"], r["t_done_us"], r["t_admit_us"])
+            res[k] = (r["state"], r["t_submit_us"], r["t_start_us"], r["t_done_us"], r["t_admit_us"], r["t_ready_us"])
             if k not in keep or r["state"] != fe.FE_STATE_DONE:
                 fe.fe_release(sv, tickets[k])
         done.set()
@@ -1173,10 +1173,12 @@ def serve_trace(ctx, traffic, arrivals, kinds, n_streams, max_batch, warm_s=0.0,
            "p99_ms_large_warm": _pct(sel(lambda x: x[1] and x[2]), 99),
            "p99_ms_large_cold": _pct(sel(lambda x: x[1] and not x[2]), 99),
            # where a large cold request's time goes (p99 of each part): waiting for
-           # admission, admitted until launched (pattern build), launched until done
+           # admission, admitted until its pattern is built, pattern ready until
+           # launched, launched (memory, element generation, assembly) until done
            "large_cold_parts_p99_ms": {
                "admission_wait": _pct([(res[k][4] - arr_us(k)) * 1e-3 for k in cnt if kinds[k][1] and not kinds[k][2]], 99),
-               "admit_to_launch": _pct([(res[k][2] - res[k][4]) * 1e-3 for k in cnt if kinds[k][1] and not kinds[k][2]], 99),
+               "pattern_build": _pct([(res[k][5] - res[k][4]) * 1e-3 for k in cnt if kinds[k][1] and not kinds[k][2]], 99),
+               "ready_to_launch": _pct([(res[k][2] - res[k][5]) * 1e-3 for k in cnt if kinds[k][1] and not kinds[k][2]], 99),
                "launch_to_done": _pct([(res[k][3] - res[k][2]) * 1e-3 for k in cnt if kinds[k][1] and not kinds[k][2]], 99)},
            "assembly_p50_ms": _pct(asm, 50), "assembly_p99_ms": _pct(asm, 99),
            "Gentries_per_s": round(ent / window_s / 1e9, 2) if window_s > 0 else None,
@@ -1190,6 +1192,8 @@ def serve_trace(ctx, traffic, arrivals, kinds, n_streams, max_batch, warm_s=0.0,
            "evictions": st["evictions"] - st0["evictions"], "rebuilds": st["rebuilds"] - st0["rebuilds"],
            "admission_waits": st["admission_waits"] - st0["admission_waits"],
            "peak_GB_charged": round(st["peak_bytes_in_use"] / 1e9, 1), "budget_GB": round(st["budget_bytes"] / 1e9, 1),
+           "alloc_ms_max": round(st["alloc_ms_max"], 3),
+           "alloc_ms_total": round(st["alloc_ms_total"] - st0["alloc_ms_total"], 1),
            "overlap_frac": overlap, "device_busy_ms": busy_ms}
     if verify:
         out["verified"] = {"checked": checked, "equal": equal,

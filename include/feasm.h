@@ -382,8 +382,9 @@ typedef struct fe_batch_item {
                                    finished (per-item latency inside one launch) */
 } fe_batch_item;
 
-/* Assemble n_items meshes in one persistent launch on `stream` (plus one
- * zeroing launch in FE_ATOMIC without accumulation).  format: FE_FORMAT_CSR /
+/* Assemble n_items meshes in one persistent launch on `stream` (in FE_ATOMIC
+ * without accumulation each item's values are zeroed inside the same launch,
+ * just before its own elements are scattered).  format: FE_FORMAT_CSR /
  * FE_FORMAT_CRAC; mode, accumulate as in fe_assemble_csr.  sched = NULL uses
  * the schedule fe_batch_autotune found for a batch of this signature (element
  * shapes, format, mode, size class), else a default.  The item array is read
@@ -462,6 +463,7 @@ typedef struct fe_result {
     const int32_t *col_idx;    /* device, borrowed                                     */
     const double *values;      /* device, library-owned until fe_release               */
     double t_submit_us, t_admit_us, t_start_us, t_done_us;  /* host steady clock       */
+    double t_ready_us;         /* when its pattern was available (cached: at admission) */
 } fe_result;
 
 typedef struct fe_server_stats {
@@ -473,6 +475,8 @@ typedef struct fe_server_stats {
     int64_t admission_waits;    /* times the admission queue found a request that
                                    did not fit the budget                     */
     int64_t peak_bytes_in_use;  /* largest bytes charged at once                */
+    double alloc_ms_total, alloc_ms_max;  /* host time in the launches' device
+                                   allocations (values, generated K)          */
 } fe_server_stats;
 
 /* One span of device work seen by the server: a launched group of requests

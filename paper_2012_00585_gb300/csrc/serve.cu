@@ -73,7 +73,7 @@ struct Ticket {
     double *K = nullptr;       // generated element matrices, freed at completion
     size_t foot = 0;           // bytes charged against the budget
     size_t k_bytes = 0, v_bytes = 0, v_charged = 0;
-    double t_submit = 0, t_admit = 0, t_start = 0, t_done = 0;
+    double t_submit = 0, t_admit = 0, t_ready = 0, t_start = 0, t_done = 0;
     int stream = -1;
 };
 
@@ -355,6 +355,7 @@ void scheduler_loop(fe_server *sv)
                     sv->to_build.push_back(id);  // the builder hands it on when the pattern exists
                 } else {
                     t.pattern = ce->second.p;
+                    t.t_ready = t.t_admit;
                     sv->ready.push_back(id);
                 }
             } else {
@@ -426,14 +427,16 @@ void scheduler_loop(fe_server *sv)
                 g.t0 = nullptr;
             }
             std::vector<fe_batch_item> items;
+            double alloc_ms = 0.0;
             for (Member &m : mem) {
+                const double a0 = now_us();
                 m.rc = fe_alloc(sv->ctx, (void **)&m.values, m.v_bytes, s);
-                if (m.rc == FE_OK && !m.req.elem_mats) {
-                    m.rc = fe_alloc(sv->ctx, (void **)&m.K, m.k_bytes, s);
-                    if (m.rc == FE_OK)
-                        m.rc = launch_generate(m.req.k_ref, m.req.dofs_per_elem, m.req.n_elem, m.req.seed, m.K,
-                                               sv->ctx->num_sms, s);
-                }
+                if (m.rc == FE_OK && !m.req.elem_mats) m.rc = fe_alloc(sv->ctx, (void **)&m.K, m.k_bytes, s);
+                const double da = (now_us() - a0) * 1e-3;
+                alloc_ms += da;
+                if (m.rc == FE_OK && !m.req.elem_mats)
+                    m.rc = launch_generate(m.req.k_ref, m.req.dofs_per_elem, m.req.n_elem, m.req.seed, m.K,
+                                           sv->ctx->num_sms, s);
                 if (m.rc == FE_OK && m.req.ready_event) cudaStreamWaitEvent(s, (cudaEvent_t)m.req.ready_event, 0);
                 if (m.rc == FE_OK) items.push_back(fe_batch_item{m.pattern, m.K ? m.K : m.req.elem_mats, m.values});
             }
@@ -445,6 +448,8 @@ void scheduler_loop(fe_server *sv)
                 if (rc == FE_OK && cudaEventRecord(g.done, s) != cudaSuccess) rc = FE_ERR_DEVICE;
             }
             lk.lock();
+            sv->stats.alloc_ms_total += alloc_ms;
+            sv->stats.alloc_ms_max = std::max(sv->stats.alloc_ms_max, alloc_ms);
             for (Member &m : mem) {
                 Ticket &t = *m.t;
                 t.values = m.values;
@@ -495,6 +500,7 @@ void builder_loop(fe_server *sv, int idx)
             CacheEntry &ce = sv->cache[t.req.pattern_key];
             if (!ce.building) {  // built meanwhile by another request
                 t.pattern = ce.p;
+                t.t_ready = now_us();
                 sv->ready.push_back(*it);
                 sv->to_build.erase(it);
                 sv->cv.notify_one();
@@ -560,6 +566,7 @@ void builder_loop(fe_server *sv, int idx)
         sv->in_use = sv->in_use - std::min(est, sv->in_use) + ce.bytes;
         t.foot = t.foot - std::min(est, t.foot);
         t.pattern = p;
+        t.t_ready = now_us();
         sv->ready.push_back(id);
         sv->cv.notify_one();
     }
@@ -596,6 +603,7 @@ void fill_result(const Ticket &t, fe_result *out)
     out->t_admit_us = t.t_admit;
     out->t_start_us = t.t_start;
     out->t_done_us = t.t_done;
+    out->t_ready_us = t.t_ready;
 }
 
 }  // namespace

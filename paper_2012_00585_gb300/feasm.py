@@ -120,14 +120,16 @@ class fe_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("state", ctypes.c_int32), ("cold", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
                 ("col_idx", ctypes.c_void_p), ("values", ctypes.c_void_p), ("t_submit_us", ctypes.c_double),
-                ("t_admit_us", ctypes.c_double), ("t_start_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+                ("t_admit_us", ctypes.c_double), ("t_start_us", ctypes.c_double), ("t_done_us", ctypes.c_double),
+                ("t_ready_us", ctypes.c_double)]
 
 
 class fe_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "admitted", "completed", "failed", "cancelled",
                                               "launches", "batched_requests", "patterns_built", "evictions",
                                               "bytes_in_use", "budget_bytes", "cached_patterns", "rebuilds",
-                                              "expired", "admission_waits", "peak_bytes_in_use")]
+                                              "expired", "admission_waits", "peak_bytes_in_use")] + \
+        [("alloc_ms_total", ctypes.c_double), ("alloc_ms_max", ctypes.c_double)]
 
 
 class fe_span(ctypes.Structure):
