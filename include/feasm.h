@@ -382,9 +382,8 @@ typedef struct fe_batch_item {
                                    finished (per-item latency inside one launch) */
 } fe_batch_item;
 
-/* Assemble n_items meshes in one persistent launch on `stream` (in FE_ATOMIC
- * without accumulation each item's values are zeroed inside the same launch,
- * just before its own elements are scattered).  format: FE_FORMAT_CSR /
+/* Assemble n_items meshes in one persistent launch on `stream` (plus one
+ * zeroing launch in FE_ATOMIC without accumulation).  format: FE_FORMAT_CSR /
  * FE_FORMAT_CRAC; mode, accumulate as in fe_assemble_csr.  sched = NULL uses
  * the schedule fe_batch_autotune found for a batch of this signature (element
  * shapes, format, mode, size class), else a default.  The item array is read
@@ -496,7 +495,9 @@ typedef struct fe_server fe_server;
  * requests per launch, hbm_budget_bytes of device memory for admitted
  * requests and cached patterns (0 = the context's budget).  Requests of at
  * least 2^26 element-matrix entries are launched alone on one of two extra
- * high-priority streams (never grouped with small ones).  n_streams = 1
+ * high-priority streams (never grouped with small ones), their kernels on at
+ * most 3/4 of the GPU's resident blocks so that pattern builds and small
+ * requests always find free SMs.  n_streams = 1
  * with max_batch = 1 is a strict FIFO: one request at a time from admission
  * to completion on one stream (the one-launch-per-request baseline). */
 int fe_server_start(fe_ctx *ctx, int32_t n_streams, int32_t max_batch, size_t hbm_budget_bytes,

@@ -49,13 +49,7 @@ struct BatchItemDev {
     int32_t nln, B, shape, map_bytes;
     int32_t staged;      // FE_SCHED_WARP_PER_ELEMENT_TMA: K_e moved by a bulk copy
     uint64_t *times;     // the caller's [first tile started, last tile finished] (ns) or null
-    int64_t zero_tiles;  // FE_ATOMIC without accumulation: tiles zeroing values, before the item's others
 };
-
-// Doubles of values one zero tile clears.
-constexpr int64_t ZERO_CHUNK = 4096;
-// Spin limit of an atomic tile waiting for its item's zero tiles.
-constexpr unsigned int ZERO_WAIT_LIMIT = 1u << 22;
 
 __device__ __forceinline__ uint64_t global_ns()
 {
@@ -64,13 +58,12 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// tc holds three counters per item: tiles started, assembly tiles finished
-// (per-item timestamps, items with a times array: the first start and the
-// last finish write the global timer) and zero tiles finished.  Called by one
-// thread per tile.
+// Per-item timestamps (items with a times array): tc holds two counters per
+// item, tiles started and tiles finished; the first start and the last
+// finish write the global timer.  Called by one thread per tile.
 __device__ __forceinline__ void tile_started(const BatchItemDev &it, int i, unsigned int *tc)
 {
-    if (it.times && atomicAdd(&tc[3 * i], 1u) == 0) it.times[0] = global_ns();
+    if (it.times && atomicAdd(&tc[2 * i], 1u) == 0) it.times[0] = global_ns();
 }
 
 __device__ __forceinline__ void tile_finished(const BatchItemDev &it, int i, unsigned int *tc, int tile)
@@ -78,41 +71,7 @@ __device__ __forceinline__ void tile_finished(const BatchItemDev &it, int i, uns
     if (!it.times) return;
     __threadfence();
     const unsigned int n_tiles = (unsigned int)((it.units + tile - 1) / tile);
-    if (atomicAdd(&tc[3 * i + 1], 1u) + 1 == n_tiles) it.times[1] = global_ns();
-}
-
-// Zero tile z of an item: ZERO_CHUNK doubles of its values, by `nthreads`
-// threads (rank r); the last one to finish counts it (after the caller's
-// barrier: see zero_tile_done).
-__device__ __forceinline__ void zero_tile(const BatchItemDev &it, int64_t z, int r, int nthreads)
-{
-    const int64_t a = z * ZERO_CHUNK, b = min(a + ZERO_CHUNK, it.nnz);
-    for (int64_t k = a + r; k < b; k += nthreads) it.values[k] = 0.0;
-}
-
-__device__ __forceinline__ void zero_tile_done(int i, unsigned int *tc)
-{
-    __threadfence();
-    atomicAdd(&tc[3 * i + 2], 1u);
-}
-
-// Before an assembly tile of an item whose values are zeroed in this launch:
-// wait (bounded) until all the item's zero tiles are done.  Every zero tile
-// precedes the item's assembly tiles in the tile order and was taken by a
-// running warp or block that does not wait, so the wait ends; false (and
-// FE_ERR_TIMEOUT recorded) if it runs out, and the tile is skipped.
-__device__ __forceinline__ bool wait_zeroed(const BatchItemDev &it, int i, unsigned int *tc, int *status)
-{
-    const volatile unsigned int *done = tc + 3 * i + 2;
-    for (unsigned int n = 0; *done < (unsigned int)it.zero_tiles; ++n) {
-        if (n >= ZERO_WAIT_LIMIT) {
-            atomicCAS(status, 0, FE_ERR_TIMEOUT);
-            return false;
-        }
-        __nanosleep(128);
-    }
-    __threadfence();
-    return true;
+    if (atomicAdd(&tc[2 * i + 1], 1u) + 1 == n_tiles) it.times[1] = global_ns();
 }
 
 int shape_of(const fe_pattern *p)
@@ -362,15 +321,16 @@ __host__ __device__ constexpr size_t batch_tables_bytes(int warps)
     return (size_t)warps * FE_MAX_NLOC * 8 + (size_t)warps * 2 * FE_MAX_NLOC * 4;
 }
 
-// Block size of a schedule (one size for all; 4-warp blocks of the
-// bulk-copy schedule measured slower).
-constexpr int sched_threads(int) { return SCHED_THREADS; }
+// Block size of a schedule: 4-warp blocks for the row gather, 8-warp blocks
+// for the others (4-warp blocks of the bulk-copy schedule measured slower).
+constexpr int sched_threads(int sched) { return sched == FE_SCHED_WARP_PER_ROW ? 128 : SCHED_THREADS; }
 
-// The row-gather schedule is capped at 80 registers (3 blocks of 8 warps per
-// SM): measured on the 256-mesh batch, 6.54 ms against 6.73 ms at 64
-// registers (which spilled in the per-tile call) and 7.65 ms at 128.
+// The row-gather schedule runs 4-warp blocks capped at 73 registers (7 blocks,
+// 28 warps per SM): measured on the 256-mesh batch, 6.29 ms, against 6.54 ms
+// with 8-warp blocks at 80 registers, 6.73 ms at 64 registers (which spilled
+// in the per-tile call) and 7.65 ms at 128.
 template <bool CRAC, int SCHED>
-__global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW ? 3 : 1) k_batch(const BatchItemDev *__restrict__ items, int n_items,
+__global__ void __launch_bounds__(sched_threads(SCHED), SCHED == FE_SCHED_WARP_PER_ROW ? 7 : 1) k_batch(const BatchItemDev *__restrict__ items, int n_items,
                                                          int64_t total_tiles, int tile, int cap, int accumulate,
                                                          unsigned long long *counter, int stage, int *status,
                                                          unsigned int *tc)
@@ -390,21 +350,8 @@ __global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW 
             if (t >= (unsigned long long)total_tiles) break;
             const int ii = find_item(items, n_items, (int64_t)t);
             const BatchItemDev &it = items[ii];
-            const int64_t local = (int64_t)t - it.tile_begin;
+            const int64_t u0 = ((int64_t)t - it.tile_begin) * tile, u1 = min(u0 + tile, it.units);
             if (threadIdx.x == 0) tile_started(it, ii, tc);
-            if (local < it.zero_tiles) {
-                zero_tile(it, local, threadIdx.x, blockDim.x);
-                __syncthreads();
-                if (threadIdx.x == 0) zero_tile_done(ii, tc);
-                continue;
-            }
-            if (it.zero_tiles) {
-                __shared__ int zero_ok;
-                if (threadIdx.x == 0) zero_ok = wait_zeroed(it, ii, tc, status) ? 1 : 0;
-                __syncthreads();
-                if (!zero_ok) continue;
-            }
-            const int64_t u0 = (local - it.zero_tiles) * tile, u1 = min(u0 + tile, it.units);
             const int B = it.B, nln = it.nln, n_loc = nln * B;
             const int NN = n_loc * n_loc;
             for (int64_t e = u0; e < u1; ++e) {
@@ -471,20 +418,8 @@ __global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW 
             if (t >= (unsigned long long)total_tiles) break;
             const int ii = find_item(items, n_items, (int64_t)t);
             const BatchItemDev &it = items[ii];
-            const int64_t local = (int64_t)t - it.tile_begin;
+            const int64_t u0 = ((int64_t)t - it.tile_begin) * tile, u1 = min(u0 + tile, it.units);
             if (lane == 0) tile_started(it, ii, tc);
-            if (local < it.zero_tiles) {
-                zero_tile(it, local, lane, 32);
-                __syncwarp();
-                if (lane == 0) zero_tile_done(ii, tc);
-                continue;
-            }
-            if (it.zero_tiles) {
-                int zero_ok = 1;
-                if (lane == 0) zero_ok = wait_zeroed(it, ii, tc, status) ? 1 : 0;
-                if (!__shfl_sync(0xffffffffu, zero_ok, 0)) continue;
-            }
-            const int64_t u0 = (local - it.zero_tiles) * tile, u1 = min(u0 + tile, it.units);
             if (it.staged) {
                 const bool ok = it.map_bytes == 1
                                     ? staged_tile_any<uint8_t, CRAC>(&it, it.shape, u0, u1, lane, kst, stage, bar,
@@ -512,20 +447,8 @@ __global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW 
             if (t >= (unsigned long long)total_tiles) break;
             const int ii = find_item(items, n_items, (int64_t)t);
             const BatchItemDev &it = items[ii];
-            const int64_t local = (int64_t)t - it.tile_begin;
+            const int64_t u0 = ((int64_t)t - it.tile_begin) * tile, u1 = min(u0 + tile, it.units);
             if (lane == 0) tile_started(it, ii, tc);
-            if (local < it.zero_tiles) {
-                zero_tile(it, local, lane, 32);
-                __syncwarp();
-                if (lane == 0) zero_tile_done(ii, tc);
-                continue;
-            }
-            if (it.zero_tiles) {
-                int zero_ok = 1;
-                if (lane == 0) zero_ok = wait_zeroed(it, ii, tc, status) ? 1 : 0;
-                if (!__shfl_sync(0xffffffffu, zero_ok, 0)) continue;
-            }
-            const int64_t u0 = (local - it.zero_tiles) * tile, u1 = min(u0 + tile, it.units);
             if (SCHED == FE_SCHED_WARP_PER_ROW) {
                 if (it.shape == SH_4_1 || it.shape == SH_8_1) {
                     // one-DOF rows: several per warp (gather_small.cuh)
@@ -572,6 +495,17 @@ __global__ void __launch_bounds__(SCHED_THREADS, SCHED == FE_SCHED_WARP_PER_ROW 
     }
 }
 
+// Zero every item's values (FE_ATOMIC without accumulation) in one launch.
+__global__ void k_batch_zero(const BatchItemDev *__restrict__ items, int n_items)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int i = 0; i < n_items; ++i) {
+        double *v = items[i].values;
+        const int64_t n = items[i].nnz;
+        for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) v[k] = 0.0;
+    }
+}
+
 struct Plan {
     std::vector<BatchItemDev> host;
     int64_t total_tiles = 0;
@@ -582,10 +516,7 @@ struct Plan {
 // Largest K_e (doubles) a bulk-copy stage holds: 32 x 32.
 constexpr int STAGE_MAX = 32 * 32;
 
-// FE_ATOMIC without accumulation zeroes each item's values inside the launch:
-// the item's zero tiles come right before its assembly tiles in the tile
-// order, so that zeroing later items overlaps the scatter of earlier ones.
-int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mode, int acc, int tile, Plan &plan)
+int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mode, int tile, Plan &plan)
 {
     plan.host.resize(n);
     plan.total_tiles = 0;
@@ -615,8 +546,6 @@ int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
         d.units = mode == FE_ATOMIC ? p->n_e : p->n_nodes;
         d.nnz = p->nnz;
         d.tile_begin = plan.total_tiles;
-        d.zero_tiles = (mode == FE_ATOMIC && !acc) ? (p->nnz + ZERO_CHUNK - 1) / ZERO_CHUNK : 0;
-        plan.total_tiles += d.zero_tiles;
         d.nln = p->nln;
         d.B = p->B;
         d.map_bytes = p->map_bytes;
@@ -637,7 +566,7 @@ int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
 size_t batch_smem(int mode, int sched, int cap, int stage)
 {
     const int W = SCHED_THREADS / 32;
-    if (mode == FE_DETERMINISTIC) return (size_t)W * cap * 8;
+    if (mode == FE_DETERMINISTIC) return (size_t)(sched_threads(FE_SCHED_WARP_PER_ROW) / 32) * cap * 8;
     if (sched == FE_SCHED_BLOCK_PER_ELEMENT) return (size_t)FE_MAX_NLOC * 16;
     if (sched == FE_SCHED_WARP_PER_ELEMENT_TMA) {
         const int w = sched_threads(sched) / 32;
@@ -648,7 +577,7 @@ size_t batch_smem(int mode, int sched, int cap, int stage)
 
 template <bool CRAC, int SCHED>
 int launch_batch_t(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t total, int tile, int cap, int acc,
-                   unsigned long long *counter, size_t smem, int stage, unsigned int *tc, cudaStream_t s)
+                   unsigned long long *counter, size_t smem, int stage, unsigned int *tc, double frac, cudaStream_t s)
 {
     auto kern = k_batch<CRAC, SCHED>;
     constexpr int threads = sched_threads(SCHED);
@@ -657,7 +586,9 @@ int launch_batch_t(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t tota
     FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) return FE_ERR_UNSUPPORTED;
     const int64_t want = SCHED == FE_SCHED_BLOCK_PER_ELEMENT ? total : (total + threads / 32 - 1) / (threads / 32);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * per_sm, want));
+    // frac < 1: the persistent grid takes only that share of the resident blocks
+    const int64_t resident = std::max<int64_t>(1, (int64_t)((double)ctx->num_sms * per_sm * frac));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident, want));
     kern<<<grid, threads, smem, s>>>(d_items, n, total, tile, cap, acc, counter, stage, ctx->d_status, tc);
     fe_note_launch();
     FE_CUDA(cudaGetLastError());
@@ -666,27 +597,27 @@ int launch_batch_t(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t tota
 
 int launch_batch(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t total, int format, int mode, int acc,
                  int sched, int tile, int cap, int stage, unsigned long long *counter, unsigned int *tc,
-                 cudaStream_t s)
+                 double frac, cudaStream_t s)
 {
     const size_t smem = batch_smem(mode, sched, cap, stage);
     if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
     const bool crac = format == FE_FORMAT_CRAC;
     if (mode == FE_DETERMINISTIC)
-        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s)
-                    : launch_batch_t<false, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s);
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
     switch (sched) {
     case FE_SCHED_THREAD_PER_ENTRY:
-        return crac ? launch_batch_t<true, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s)
-                    : launch_batch_t<false, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s);
+        return crac ? launch_batch_t<true, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
+                    : launch_batch_t<false, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
     case FE_SCHED_BLOCK_PER_ELEMENT:
-        return crac ? launch_batch_t<true, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s)
-                    : launch_batch_t<false, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s);
+        return crac ? launch_batch_t<true, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
+                    : launch_batch_t<false, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
     case FE_SCHED_WARP_PER_ELEMENT_TMA:
-        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s)
-                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s);
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
     default:
-        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s)
-                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, s);
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
     }
 }
 
@@ -870,21 +801,26 @@ int upload(fe_ctx *ctx, void *dst, const void *src, size_t n, cudaStream_t s)
 // Plan upload + launch on stream s.  The item table and the tile counter are
 // stream-ordered allocations freed after the launch.
 int run_batch(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mode, int acc, fe_schedule sc,
-              cudaStream_t s)
+              cudaStream_t s, double frac = 1.0)
 {
     Plan plan;
-    FE_TRY(make_plan(ctx, items, n, format, mode, acc, sc.tile, plan));
+    FE_TRY(make_plan(ctx, items, n, format, mode, sc.tile, plan));
     BatchItemDev *d_items = nullptr;
     unsigned long long *counter = nullptr;
     FE_TRY(fe_alloc(ctx, (void **)&d_items, sizeof(BatchItemDev) * n, s));
-    // the tile counter, then three tile counters per item (timestamps, zeroing)
-    const size_t cbytes = sizeof(unsigned long long) + sizeof(unsigned int) * 3 * (size_t)n;
+    // the tile counter, then two tile counters per item (per-item timestamps)
+    const size_t cbytes = sizeof(unsigned long long) + sizeof(unsigned int) * 2 * (size_t)n;
     int rc = fe_alloc(ctx, (void **)&counter, cbytes, s);
     if (rc == FE_OK) rc = upload(ctx, d_items, plan.host.data(), sizeof(BatchItemDev) * n, s);
     if (rc == FE_OK && cudaMemsetAsync(counter, 0, cbytes, s) != cudaSuccess) rc = FE_ERR_DEVICE;
+    if (rc == FE_OK && mode == FE_ATOMIC && !acc) {
+        k_batch_zero<<<ctx->num_sms * 4, 256, 0, s>>>(d_items, n);
+        fe_note_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = FE_ERR_DEVICE;
+    }
     if (rc == FE_OK && plan.total_tiles > 0)
         rc = launch_batch(ctx, d_items, n, plan.total_tiles, format, mode, acc, sc.kind, sc.tile, plan.cap, plan.stage,
-                          counter, (unsigned int *)(counter + 1), s);
+                          counter, (unsigned int *)(counter + 1), frac, s);
     fe_free_async(d_items, s);
     fe_free_async(counter, s);
     return rc;
@@ -924,6 +860,34 @@ int fe_assemble_batch(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, 
     }
     return run_batch(ctx, items, n_items, format, mode, accumulate, sc, (cudaStream_t)stream);
 }
+
+}  // extern "C"
+
+// fe_assemble_batch (sched = NULL) whose persistent grid takes only `frac` of
+// the resident blocks: the server launches large requests this way, so that
+// pattern builds and small requests always find free SMs (a persistent grid
+// holds every SM until its last tile is done, and a running block is never
+// preempted by a higher-priority stream's).
+int fe_assemble_batch_share(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
+                            int32_t accumulate, void *stream, double frac)
+{
+    if (!ctx || n_items <= 0 || !items || !(frac > 0.0 && frac <= 1.0)) return FE_ERR_INVALID_ARG;
+    if ((format != FE_FORMAT_CSR && format != FE_FORMAT_CRAC) || (mode != FE_ATOMIC && mode != FE_DETERMINISTIC) ||
+        (accumulate != 0 && accumulate != 1))
+        return FE_ERR_INVALID_ARG;
+    FeRange range("fe_assemble_batch (share of the GPU)");
+    DeviceScope ds(ctx->device);
+    fe_schedule sc = default_schedule(mode);
+    {
+        fe_batch_state *st = state_of(ctx);
+        std::lock_guard<std::mutex> lk(st->mu);
+        auto it = st->tuned.find(signature(items, n_items, format, mode));
+        if (it != st->tuned.end()) sc = it->second;
+    }
+    return run_batch(ctx, items, n_items, format, mode, accumulate, sc, (cudaStream_t)stream, frac);
+}
+
+extern "C" {
 
 int fe_batch_tuned(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
                    fe_schedule *out)
@@ -1025,12 +989,12 @@ int fe_batch_graph_create(fe_ctx *ctx, const fe_batch_item *items, int32_t n_ite
         if (it != st->tuned.end()) sc = it->second;
     }
     Plan plan;
-    FE_TRY(make_plan(ctx, items, n_items, format, mode, accumulate, sc.tile, plan));
+    FE_TRY(make_plan(ctx, items, n_items, format, mode, sc.tile, plan));
     fe_batch_graph *g = new fe_batch_graph();
     g->ctx = ctx;
     int rc = FE_OK;
     // the graph's own item table and counter live as long as the graph
-    const size_t cbytes = sizeof(unsigned long long) + sizeof(unsigned int) * 3 * (size_t)n_items;
+    const size_t cbytes = sizeof(unsigned long long) + sizeof(unsigned int) * 2 * (size_t)n_items;
     if (cudaMalloc((void **)&g->d_items, sizeof(BatchItemDev) * n_items) != cudaSuccess ||
         cudaMalloc((void **)&g->counter, cbytes) != cudaSuccess)
         rc = FE_ERR_OOM;
@@ -1044,9 +1008,13 @@ int fe_batch_graph_create(fe_ctx *ctx, const fe_batch_item *items, int32_t n_ite
     if (rc == FE_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = FE_ERR_DEVICE;
     if (rc == FE_OK) {
         int lrc = cudaMemsetAsync(g->counter, 0, cbytes, cs) == cudaSuccess ? FE_OK : FE_ERR_DEVICE;
+        if (lrc == FE_OK && mode == FE_ATOMIC && !accumulate) {
+            k_batch_zero<<<ctx->num_sms * 4, 256, 0, cs>>>(g->d_items, n_items);
+            if (cudaGetLastError() != cudaSuccess) lrc = FE_ERR_DEVICE;
+        }
         if (lrc == FE_OK && plan.total_tiles > 0)
             lrc = launch_batch(ctx, g->d_items, n_items, plan.total_tiles, format, mode, accumulate, sc.kind, sc.tile,
-                               plan.cap, plan.stage, g->counter, (unsigned int *)(g->counter + 1), cs);
+                               plan.cap, plan.stage, g->counter, (unsigned int *)(g->counter + 1), 1.0, cs);
         const cudaError_t ec = cudaStreamEndCapture(cs, &g->graph);
         rc = lrc != FE_OK ? lrc : (ec == cudaSuccess ? FE_OK : FE_ERR_DEVICE);
     }

@@ -124,6 +124,10 @@ int fe_assemble_rowlock(const fe_pattern *p, const double *K, double *values, in
                         cudaStream_t s);
 
 void fe_batch_state_destroy(fe_ctx *ctx);
+// fe_assemble_batch with the persistent grid limited to a share of the GPU
+// (batch.cu; used by the server for large requests).
+int fe_assemble_batch_share(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
+                            int32_t accumulate, void *stream, double frac);
 
 // Host-side count of kernel launches made by this library (all threads).
 void fe_note_launch();

@@ -100,6 +100,9 @@ struct Group {
 // time while small requests fill the SMs around them.
 constexpr int64_t BIG_ENTRIES = (int64_t)1 << 26;
 constexpr int N_BIG_STREAMS = 2;
+// Share of the GPU's resident blocks a large request's kernels take (the
+// rest stays free for pattern builds and small requests).
+constexpr double BIG_SHARE = 0.75;
 
 bool is_big(const fe_request &r) { return r.n_elem * (int64_t)r.dofs_per_elem * r.dofs_per_elem >= BIG_ENTRIES; }
 
@@ -436,14 +439,17 @@ void scheduler_loop(fe_server *sv)
                 alloc_ms += da;
                 if (m.rc == FE_OK && !m.req.elem_mats)
                     m.rc = launch_generate(m.req.k_ref, m.req.dofs_per_elem, m.req.n_elem, m.req.seed, m.K,
-                                           sv->ctx->num_sms, s);
+                                           big ? std::max(1, (int)(sv->ctx->num_sms * BIG_SHARE)) : sv->ctx->num_sms,
+                                           s);
                 if (m.rc == FE_OK && m.req.ready_event) cudaStreamWaitEvent(s, (cudaEvent_t)m.req.ready_event, 0);
                 if (m.rc == FE_OK) items.push_back(fe_batch_item{m.pattern, m.K ? m.K : m.req.elem_mats, m.values});
             }
             int rc = FE_OK;
             if (!items.empty()) {
                 FeRange range("serve: batched launch");
-                rc = fe_assemble_batch(sv->ctx, items.data(), (int32_t)items.size(), fmt, mode, 0, nullptr, s);
+                rc = big ? fe_assemble_batch_share(sv->ctx, items.data(), (int32_t)items.size(), fmt, mode, 0, s,
+                                                   BIG_SHARE)
+                         : fe_assemble_batch(sv->ctx, items.data(), (int32_t)items.size(), fmt, mode, 0, nullptr, s);
                 if (rc == FE_OK && cudaEventCreate(&g.done) != cudaSuccess) rc = FE_ERR_DEVICE;
                 if (rc == FE_OK && cudaEventRecord(g.done, s) != cudaSuccess) rc = FE_ERR_DEVICE;
             }
