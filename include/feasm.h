@@ -419,10 +419,13 @@ int fe_batch_graph_destroy(fe_batch_graph *graph);
 
 /* ---- serving: requests admitted by HBM footprint, continuous batching ------
  * Not in the paper.  A server owns a scheduler thread (admission, launches,
- * completions) and a pattern-builder thread.  Patterns are cached by
- * `pattern_key`; a request for a cached key is numeric-only.  Admitted
- * requests are assembled together (fe_assemble_batch) on one of n_streams
- * streams, so new requests are admitted and run while others are in flight. */
+ * completions) and three pattern-builder threads (large meshes first, each
+ * on its own high-priority stream).  Patterns are cached by `pattern_key`; a
+ * request for a cached key is numeric-only; when memory runs short, patterns
+ * no queued request needs are evicted, meshes used once before meshes used
+ * again.  Admitted requests are assembled together (fe_assemble_batch) on one
+ * of n_streams streams, so new requests are admitted and run while others are
+ * in flight. */
 #define FE_STATE_PENDING 0    /* submitted, waiting for admission            */
 #define FE_STATE_ADMITTED 1   /* memory reserved, pattern being built/looked up */
 #define FE_STATE_RUNNING 2    /* launched                                     */
