@@ -419,8 +419,8 @@ int fe_batch_graph_destroy(fe_batch_graph *graph);
 
 /* ---- serving: requests admitted by HBM footprint, continuous batching ------
  * Not in the paper.  A server owns a scheduler thread (admission, launches,
- * completions) and three pattern-builder threads (large meshes first, each
- * on its own high-priority stream).  Patterns are cached by `pattern_key`; a
+ * completions) and two pattern-builder threads (each on its own
+ * high-priority stream).  Patterns are cached by `pattern_key`; a
  * request for a cached key is numeric-only; when memory runs short, patterns
  * no queued request needs are evicted, meshes used once before meshes used
  * again.  Admitted requests are assembled together (fe_assemble_batch) on one

@@ -492,7 +492,7 @@ void scheduler_loop(fe_server *sv)
 // request (and any that waited for the same key) on to the ready queue.
 // Several builder threads, each on its own stream, so that the builds of
 // different meshes (each waits on the host to size its arrays) overlap.
-constexpr int N_BUILDERS = 3;
+constexpr int N_BUILDERS = 2;
 
 void builder_loop(fe_server *sv, int idx)
 {
@@ -513,13 +513,12 @@ void builder_loop(fe_server *sv, int idx)
                 id = UINT64_MAX;
                 break;
             }
-            if (t.cold && !id) id = *it;  // the first cold request, unless a large one follows
-            if (t.cold && is_big(t.req)) {
-                id = *it;  // large builds first: they set the tail latency
+            if (t.cold) {
+                id = *it;
+                sv->to_build.erase(it);
                 break;
             }
         }
-        if (id && id != UINT64_MAX) sv->to_build.erase(std::find(sv->to_build.begin(), sv->to_build.end(), id));
         if (id == UINT64_MAX) continue;
         if (id == 0) {
             sv->cv_build.wait_for(lk, std::chrono::milliseconds(2));

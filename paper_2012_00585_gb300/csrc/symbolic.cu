@@ -167,6 +167,48 @@ __global__ void k_node_conn(const int32_t *__restrict__ D, int64_t n_e, int32_t 
 {
     const int lane = threadIdx.x & 31;
     int64_t spread = 0;
+    if (nln <= 16) {
+        // small elements: 32 / P elements per warp, P = nln rounded up to a
+        // power of two lanes each (one mask word per element)
+        int P = 1;
+        while (P < nln) P <<= 1;
+        const int G = 32 / P, grp = lane / P, k = lane - grp * P;
+        const unsigned gmask = P == 32 ? 0xffffffffu : ((1u << P) - 1u);
+        // element 0's run starts, the reference of the uniform-layout test
+        const bool v0 = n_e > 0 && k < nln;
+        const int32_t nd0 = v0 ? D[(int64_t)B * k] / B : 0;
+        const int32_t pv0 = (v0 && k > 0) ? D[(int64_t)B * (k - 1)] / B : 0;
+        const bool start0 = v0 && (k == 0 || nd0 != pv0 + 1);
+        const unsigned m0 = (__ballot_sync(0xffffffffu, start0) >> (grp * P)) & gmask;
+        bool differs = false;
+        for (int64_t e0 = fe_warp_id() * G; e0 < n_e; e0 += fe_warps() * G) {
+            const int64_t e = e0 + grp;
+            const bool valid = e < n_e && k < nln;
+            const int32_t nd = valid ? D[e * n_loc + (int64_t)B * k] / B : 0;
+            const int32_t pv = (valid && k > 0) ? D[e * n_loc + (int64_t)B * (k - 1)] / B : 0;
+            const bool start = valid && (k == 0 || nd != pv + 1);
+            const unsigned m = (__ballot_sync(0xffffffffu, start) >> (grp * P)) & gmask;
+            int32_t lo = valid ? nd : INT32_MAX, hi = valid ? nd : 0;
+            if (valid) {
+                N[e * nln + k] = nd;
+                atomicAdd(&deg[nd], 1);
+            }
+            for (int o = P >> 1; o > 0; o >>= 1) {
+                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            if (k == 0 && e < n_e) {
+                run_mask[e * mask_words] = m;
+                runs[e] = __popc(m);
+                spread += hi - lo;
+                if (m != m0) differs = true;
+            }
+        }
+        if (__any_sync(0xffffffffu, differs) && lane == 0) sc[S_NONUNIFORM] = 1;
+        for (int o = 16; o > 0; o >>= 1) spread += __shfl_xor_sync(0xffffffffu, spread, o);
+        if (lane == 0 && spread) atomicAdd((unsigned long long *)&sc[S_SPREAD], (unsigned long long)spread);
+        return;
+    }
     for (int64_t e = fe_warp_id(); e < n_e; e += fe_warps()) {
         int nr = 0;
         bool differs = false;
@@ -452,22 +494,25 @@ __global__ void __launch_bounds__(256) k_expand(int64_t n_nodes, int32_t B_rt, i
                 const int rho = idx / B;
                 col_idx[rb + idx] = B * kv[rho] + (idx - rho * B);
             }
-            if (col_align) {
-                const int64_t cb = cb0 + (int64_t)j * R2;
-                int rr = 0;
-                for (int k0 = 0; k0 < L; k0 += 32) {
-                    const int k = k0 + lane;
-                    const int32_t x = k < L ? kv[k] : 0;
-                    const int32_t pv = (k > 0 && k < L) ? kv[k - 1] : 0;
-                    const bool rs = k < L && (k == 0 || (int64_t)pv != (int64_t)x - 1);
-                    const unsigned mr = __ballot_sync(0xffffffffu, rs);
-                    if (rs) {
-                        const int r = rr + __popc(mr & lanemask_lt());
+        }
+        if (col_align) {
+            // the block row's runs, found once and written for each of its B rows
+            int rr = 0;
+            for (int k0 = 0; k0 < L; k0 += 32) {
+                const int k = k0 + lane;
+                const int32_t x = k < L ? kv[k] : 0;
+                const int32_t pv = (k > 0 && k < L) ? kv[k - 1] : 0;
+                const bool rs = k < L && (k == 0 || (int64_t)pv != (int64_t)x - 1);
+                const unsigned mr = __ballot_sync(0xffffffffu, rs);
+                if (rs) {
+                    const int r = rr + __popc(mr & lanemask_lt());
+                    for (int j = 0; j < B; ++j) {
+                        const int64_t cb = cb0 + (int64_t)j * R2;
                         col_align[cb + 2 * r] = B * x;
-                        col_align[cb + 2 * r + 1] = (int32_t)(rb + (int64_t)B * k);
+                        col_align[cb + 2 * r + 1] = (int32_t)(rb0 + (int64_t)j * B * L + (int64_t)B * k);
                     }
-                    rr += __popc(mr);
                 }
+                rr += __popc(mr);
             }
         }
         __syncwarp();
@@ -736,7 +781,8 @@ void pattern_release(fe_pattern *p, cudaStream_t s)
 {
     fe_colouring_free(p, s);
     void *ptrs[] = {p->node_dofs, p->row_ptr, p->col_idx, p->crac_ptr, p->col_align, p->adj_ptr, p->adj,
-                    p->map_csr,   p->run_mask, p->run_ptr, p->map_crac, p->map_crac_blk, p->elem_order};
+                    p->map_csr,   p->run_mask, p->run_ptr, p->map_crac,
+                    p->map_crac_blk != p->map_csr ? p->map_crac_blk : nullptr, p->elem_order};
     for (void *x : ptrs) fe_free_async(x, s);
     delete p;
 }
@@ -1036,8 +1082,13 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
             FE_CUDA(cudaGetLastError());
         }
     }
-    // the CRAC gather's block map, expanded from the run map
-    if (p->flags & FE_PATTERN_MAP_CRAC) {
+    // the CRAC gather's block map, expanded from the run map.  With the CSR
+    // map built too the expansion would be that map byte for byte (a block's
+    // position in its row does not depend on the format): it is shared
+    // instead.  Patterns built with FE_PATTERN_MAP_CRAC alone expand it.
+    if ((p->flags & FE_PATTERN_MAP_CRAC) && p->map_csr) {
+        p->map_crac_blk = p->map_csr;
+    } else if (p->flags & FE_PATTERN_MAP_CRAC) {
         FE_TRY(alloc_into(p, &p->map_crac_blk, (size_t)(n_ninc * nln + 1) * p->map_bytes, s));
         if (n_ninc > 0) {
             const int g = fe_grid_for(n_ninc * nln, 256, sms, 16);

@@ -513,3 +513,31 @@ def test_signed_zero_contributions(ctx, fmt):
         got = g.assemble(K, fmt, feasm.FE_DETERMINISTIC).cpu().numpy()
         assert np.array_equal(got.view(np.uint64), exp.view(np.uint64))
         g.free()
+
+
+@pytest.mark.parametrize("case", ["hex_d3", "tets_permuted", "quads_q3"])
+def test_crac_only_pattern(ctx, case):
+    """A pattern built for CRAC alone (no CSR slot map): the CRAC gather then
+    reads the run map expanded per column block in the symbolic phase (with
+    both maps built it shares the CSR map instead), bit-exact against the
+    oracle; the atomic CRAC path within the row tolerance; the CSR assembly
+    reports that its map was not built."""
+    from paper_2012_00585_gb300 import feasm
+    if case == "hex_d3":
+        D, n_dofs = wl.hex_q1_grid(6, 3)
+    elif case == "tets_permuted":
+        D, n_dofs = wl.tet_p2_kuhn(3, d=3, seed=4)
+    else:
+        D, n_dofs = wl.quad_qp_grid(5, 3, 1)
+    K = wl.random_matrices(D.shape[0], D.shape[1], seed=11)
+    g = gu.GpuAssembly(ctx, D, n_dofs, flags=feasm.FE_PATTERN_CRAC | feasm.FE_PATTERN_MAP_CRAC)
+    rp_o, ci_o = oracle.csr_pattern(D, n_dofs)
+    v_o = oracle.assemble_csr(D, K, rp_o, ci_o)
+    det = g.assemble(K, "crac", feasm.FE_DETERMINISTIC).cpu().numpy()
+    assert np.array_equal(det.view(np.uint64), v_o.view(np.uint64))
+    at = g.assemble(K, "crac", feasm.FE_ATOMIC).cpu().numpy()
+    gu.assert_within_row_tol(rp_o, at, v_o, gu.row_tolerance(rp_o, v_o, gu.contribution_abs_row_sums(D, K, n_dofs)))
+    with pytest.raises(feasm.FeError) as ei:
+        g.assemble(K, "csr", feasm.FE_DETERMINISTIC)
+    assert ei.value.code == feasm.FE_ERR_NOT_BUILT
+    g.free()
