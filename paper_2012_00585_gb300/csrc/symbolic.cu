@@ -519,6 +519,132 @@ __global__ void __launch_bounds__(256) k_expand(int64_t n_nodes, int32_t B_rt, i
     }
 }
 
+// A3-A5 in one pass over the block rows, for rows of at most `cap` blocks:
+// the expansion of k_expand (CSR row pointers and columns, the CRAC pairs,
+// the row's runs found once) followed, with the row's sorted blocks and its
+// runs still in shared memory, by the row's slot maps: for every incidence
+// (element e, local block k) of the row, the position of each block of e in
+// the row (binary search, the CSR map) and the position of the first block
+// of each run of e (the CRAC block search of Listing 1 over the row's runs:
+// walk to the last run starting at or before the block, then check that the
+// block lies in it; the CRAC map).  A block missing from its row (a bad
+// pattern) records FE_ERR_DEVICE.
+template <int BT, typename MT>
+__global__ void __launch_bounds__(256) k_expand_maps(
+    int64_t n_nodes, int32_t B_rt, int32_t nln, const int64_t *__restrict__ adj_ptr, const uint32_t *__restrict__ adj,
+    const int32_t *__restrict__ N, const int32_t *__restrict__ keys, const int32_t *__restrict__ node_len,
+    const int32_t *__restrict__ node_runs2, const int64_t *__restrict__ nrp, const int64_t *__restrict__ ncp,
+    int64_t *__restrict__ row_ptr, int64_t *__restrict__ crac_ptr, int32_t *__restrict__ col_idx,
+    int32_t *__restrict__ col_align, MT *__restrict__ map, MT *__restrict__ mapc,
+    const uint32_t *__restrict__ run_mask, const int64_t *__restrict__ run_ptr, int mask_words, int rmax,
+    int uniform_R, int cap, int64_t *sc)
+{
+    extern __shared__ int32_t kbuf[];
+    const int B = BT > 0 ? BT : B_rt;
+    const int lane = threadIdx.x & 31;
+    int32_t *ks = kbuf + (size_t)(threadIdx.x >> 5) * 3 * cap;  // the row's blocks
+    int32_t *rf = ks + cap;                                      // first block of each run
+    int32_t *rk = rf + cap;                                      // its position in the row
+    for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
+        const int L = node_len[v];
+        const int R2 = node_runs2[v];
+        const int64_t a = adj_ptr[v], b = adj_ptr[v + 1];
+        const int32_t *kv_g = keys + a * nln;
+        for (int k = lane; k < L; k += 32) ks[k] = kv_g[k];
+        __syncwarp();
+        const int64_t rb0 = (int64_t)B * B * nrp[v];
+        const int64_t cb0 = (int64_t)B * ncp[v];
+        for (int j = lane; j < B; j += 32) {
+            row_ptr[(int64_t)B * v + j] = rb0 + (int64_t)j * B * L;
+            crac_ptr[(int64_t)B * v + j] = cb0 + (int64_t)j * R2;
+        }
+        for (int j = 0; j < B; ++j) {
+            const int64_t rb = rb0 + (int64_t)j * B * L;
+            for (int idx = lane; idx < B * L; idx += 32) {
+                const int rho = idx / B;
+                col_idx[rb + idx] = B * ks[rho] + (idx - rho * B);
+            }
+        }
+        int nruns = 0;
+        for (int k0 = 0; k0 < L; k0 += 32) {
+            const int k = k0 + lane;
+            const int32_t x = k < L ? ks[k] : 0;
+            const int32_t pv = (k > 0 && k < L) ? ks[k - 1] : 0;
+            const bool st = k < L && (k == 0 || (int64_t)pv != (int64_t)x - 1);
+            const unsigned mr = __ballot_sync(0xffffffffu, st);
+            if (st) {
+                const int r = nruns + __popc(mr & lanemask_lt());
+                rf[r] = x;
+                rk[r] = k;
+                for (int j = 0; j < B; ++j) {
+                    const int64_t cb = cb0 + (int64_t)j * R2;
+                    col_align[cb + 2 * r] = B * x;
+                    col_align[cb + 2 * r + 1] = (int32_t)(rb0 + (int64_t)j * B * L + (int64_t)B * k);
+                }
+            }
+            nruns += __popc(mr);
+        }
+        __syncwarp();
+        if (map) {
+            const int total = (int)(b - a) * nln;
+            for (int q = lane; q < total; q += 32) {
+                const int s_ = q / nln;
+                const int kc = q - s_ * nln;
+                const uint32_t t = adj[a + s_];
+                const int32_t j = N[(int64_t)(t / (uint32_t)nln) * nln + kc];
+                int lo = 0, hi = L;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (ks[mid] < j) lo = mid + 1; else hi = mid;
+                }
+                if (lo >= L || ks[lo] != j) set_err(sc, FE_ERR_DEVICE);
+                map[(int64_t)t * nln + kc] = (MT)lo;
+            }
+        }
+        if (mapc) {
+            const int total = (int)(b - a) * rmax;
+            for (int q = lane; q < total; q += 32) {
+                const int s_ = q / rmax;
+                const int ri = q - s_ * rmax;
+                const uint32_t t = adj[a + s_];
+                const int64_t e = t / (uint32_t)nln;
+                const int k = (int)(t - (uint32_t)(e * nln));
+                const uint32_t *m = uniform_R ? run_mask : run_mask + e * mask_words;
+                // local block starting the element's ri-th run (ri-th set bit of its mask)
+                int kc = -1, seen = 0;
+                for (int w = 0; w < mask_words && kc < 0; ++w) {
+                    uint32_t x = m[w];
+                    const int cnt = __popc(x);
+                    if (ri < seen + cnt) {
+                        for (int i = 0; i < ri - seen; ++i) x &= x - 1;
+                        kc = 32 * w + __ffs(x) - 1;
+                    }
+                    seen += cnt;
+                }
+                if (kc < 0) continue;  // the element has fewer runs
+                int64_t rp;
+                int nr;
+                if (uniform_R) {
+                    nr = uniform_R;
+                    rp = e * uniform_R;
+                } else {
+                    rp = run_ptr[e];
+                    nr = (int)(run_ptr[e + 1] - rp);
+                }
+                const int32_t j = N[e * nln + kc];
+                int pr = 0;
+                while (pr + 1 < nruns && rf[pr + 1] <= j) ++pr;
+                const int len = (pr + 1 < nruns ? rk[pr + 1] : L) - rk[pr];
+                int32_t rel = 0;
+                if (j >= rf[pr] && j < rf[pr] + len) rel = rk[pr] + (j - rf[pr]);
+                else set_err(sc, FE_ERR_DEVICE);
+                mapc[rp * nln + (int64_t)k * nr + ri] = (MT)rel;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void k_tail(int64_t *row_ptr, int64_t *crac_ptr, const int64_t *nrp, const int64_t *ncp, int64_t n_nodes,
                        int64_t n_dofs, int32_t B)
 {
@@ -1017,7 +1143,40 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
     FE_TRY(alloc_into(p, (void **)&p->crac_ptr, sizeof(int64_t) * (size_t)(n_dofs + 1), s));
     FE_TRY(alloc_into(p, (void **)&p->col_idx, sizeof(int32_t) * (size_t)(p->nnz + 1), s));
     FE_TRY(alloc_into(p, (void **)&p->col_align, sizeof(int32_t) * (size_t)p->n_ca, s));
-    if (n_nodes > 0) {
+    // rows of up to 1024 blocks: the slot maps are computed in the same pass
+    const bool fused = n_nodes > 0 && n_e > 0 && p->max_node_len <= 1024 &&
+                       (p->flags & (FE_PATTERN_MAP_CSR | FE_PATTERN_MAP_CRAC));
+    if (fused) {
+        ph.next("A3-A5 rows, CSR, CRAC and slot maps");
+        if (p->flags & FE_PATTERN_MAP_CSR)
+            FE_TRY(alloc_into(p, &p->map_csr, (size_t)(n_ninc * nln + 1) * p->map_bytes, s));
+        if (p->flags & FE_PATTERN_MAP_CRAC)
+            FE_TRY(alloc_into(p, &p->map_crac, (size_t)(p->n_runs * nln + 1) * p->map_bytes, s));
+        const int kcap = std::max(1, p->max_node_len);
+        const size_t ksm = (size_t)8 * 3 * kcap * 4;
+        const int eg = fe_grid_for(n_nodes * 32, 256, sms, 8);
+        const int rmax = p->uniform_runs ? p->runs_per_elem : nln;
+        const int uR = p->uniform_runs ? p->runs_per_elem : 0;
+        auto launch = [&](auto kern, auto *map, auto *mapc) -> int {
+            FE_TRY(configure_smem(kern, ksm));
+            FE_LAUNCH((kern<<<eg, 256, ksm, s>>>(n_nodes, B, nln, p->adj_ptr, p->adj, p->node_dofs, keys, node_len,
+                                                  node_runs2, nrp, ncp, p->row_ptr, p->crac_ptr, p->col_idx,
+                                                  p->col_align, map, mapc, p->run_mask, p->run_ptr, p->mask_words,
+                                                  rmax, uR, kcap, sc)));
+            return FE_OK;
+        };
+        if (p->map_bytes == 1) {
+            uint8_t *m = (uint8_t *)p->map_csr, *mc = (uint8_t *)p->map_crac;
+            if (B == 3) FE_TRY(launch(k_expand_maps<3, uint8_t>, m, mc));
+            else if (B == 1) FE_TRY(launch(k_expand_maps<1, uint8_t>, m, mc));
+            else FE_TRY(launch(k_expand_maps<0, uint8_t>, m, mc));
+        } else {
+            uint16_t *m = (uint16_t *)p->map_csr, *mc = (uint16_t *)p->map_crac;
+            if (B == 3) FE_TRY(launch(k_expand_maps<3, uint16_t>, m, mc));
+            else if (B == 1) FE_TRY(launch(k_expand_maps<1, uint16_t>, m, mc));
+            else FE_TRY(launch(k_expand_maps<0, uint16_t>, m, mc));
+        }
+    } else if (n_nodes > 0) {
         const int kcap = std::max(1, std::min(p->max_node_len, 1024));
         const size_t ksm = (size_t)8 * kcap * 4;
         const int eg = fe_grid_for(n_nodes * 32, 256, sms, 8);
@@ -1042,7 +1201,7 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
     // A5: slot maps
     ph.next("A5 slot maps");
     const int WM = 8;
-    if (p->flags & FE_PATTERN_MAP_CSR) {
+    if ((p->flags & FE_PATTERN_MAP_CSR) && !fused) {
         FE_TRY(alloc_into(p, &p->map_csr, (size_t)(n_ninc * nln + 1) * p->map_bytes, s));
         const int cap = std::max(1, std::min(p->max_node_len, 4096));
         const size_t smem = (size_t)WM * cap * 4;
@@ -1061,7 +1220,7 @@ int build_impl(fe_pattern *p, const int32_t *elem_dofs, cudaStream_t s)
             FE_CUDA(cudaGetLastError());
         }
     }
-    if (p->flags & FE_PATTERN_MAP_CRAC) {
+    if ((p->flags & FE_PATTERN_MAP_CRAC) && !fused) {
         FE_TRY(alloc_into(p, &p->map_crac, (size_t)(p->n_runs * nln + 1) * p->map_bytes, s));
         const int cap = std::max(4, std::min(2 * p->max_node_len + 2, 8192));
         const size_t smem = (size_t)WM * cap * 4;
