@@ -102,13 +102,25 @@ __global__ void __launch_bounds__(256) k_validate(const int32_t *__restrict__ D,
     uint32_t blocks_all = 0xffffffffu;
     bool bad_range = false, dup = false;
     const int nw = (n_loc + 31) / 32;
-    for (int64_t e = fe_warp_id(); e < n_e; e += fe_warps()) {
-        const int32_t *De = D + e * n_loc;
-        int32_t dv[MAXW];
+    // the next element's DOFs are loaded one element ahead
+    int32_t nx[MAXW];
+    {
+        const int64_t e = fe_warp_id();
 #pragma unroll
         for (int w = 0; w < MAXW; ++w) {
             const int c = 32 * w + lane;
-            dv[w] = (w < nw && c < n_loc) ? De[c] : INT32_MIN + w;
+            nx[w] = (e < n_e && w < nw && c < n_loc) ? D[e * n_loc + c] : INT32_MIN + w;
+        }
+    }
+    for (int64_t e = fe_warp_id(); e < n_e; e += fe_warps()) {
+        int32_t dv[MAXW];
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w) dv[w] = nx[w];
+        const int64_t en = e + fe_warps();
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w) {
+            const int c = 32 * w + lane;
+            nx[w] = (en < n_e && w < nw && c < n_loc) ? D[en * n_loc + c] : INT32_MIN + w;
         }
         uint32_t ok = 0xffffffffu;
 #pragma unroll
@@ -352,19 +364,40 @@ __global__ void __launch_bounds__(256) k_row_keys(const int32_t *__restrict__ N,
 {
     const int lane = threadIdx.x & 31;
     int row_max = 0;
-    for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
-        const int64_t a = adj_ptr[v];
-        const int n = (int)(adj_ptr[v + 1] - a) * nln;
+    // the next row's adjacency range and incidences are loaded one row ahead
+    const int64_t W = fe_warps();
+    int64_t an = 0;
+    int nn = 0;
+    uint32_t tn[V];
+    auto fetch = [&](int64_t v) {
+        an = 0;
+        nn = 0;
+        if (v < n_nodes) {
+            an = adj_ptr[v];
+            nn = (int)(adj_ptr[v + 1] - an) * nln;
+        }
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int g = lane * V + q;
+            tn[q] = g < nn ? adj[an + g / nln] : 0u;
+        }
+    };
+    fetch(fe_warp_id());
+    for (int64_t v = fe_warp_id(); v < n_nodes; v += W) {
+        const int64_t a = an;
+        const int n = nn;
+        uint32_t tc[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) tc[q] = tn[q];
+        fetch(v + W);
         int32_t x[V];
 #pragma unroll
         for (int q = 0; q < V; ++q) {
             const int g = lane * V + q;
             x[q] = PAD;
             if (g < n) {
-                const int s = g / nln;
-                const int c = g - s * nln;
-                const uint32_t t = adj[a + s];
-                x[q] = N[(int64_t)(t / (uint32_t)nln) * nln + c];
+                const int c = g - (g / nln) * nln;
+                x[q] = N[(int64_t)(tc[q] / (uint32_t)nln) * nln + c];
             }
         }
         warp_sort_regs<V>(x, lane);
