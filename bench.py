@@ -1213,7 +1213,7 @@ def served_block(ctx, fe, dev, quick=False):
     there estimates its capacity C; (2) the highest rate that keeps pace:
     an 11 s trace (1 s warm-up, 10 s counted) at 0.85 C, else 0.7 C, else
     0.55 C; (3) p50/p99 at 50 % and 80 % of that rate, continuous and FIFO
-    on the same trace (5 s counted after 1 s).  Overlap: of the time with
+    on the same trace (10 s counted after 1 s).  Overlap: of the time with
     the server's device work in flight, the fraction with two or more streams
     busy at once (CUDA events around every launch group and build)."""
     traffic = ServedTraffic(fe, dev)
@@ -1239,7 +1239,7 @@ def served_block(ctx, fe, dev, quick=False):
     out["sustainable"] = sustained
     R = sustained["rate_per_s"]
     for name, frac in (("at_50pct", 0.5), ("at_80pct", 0.8)):
-        arr, kinds = traffic.trace(frac * R, 2.0 if quick else 6.0, seed=13 + int(frac * 10))
+        arr, kinds = traffic.trace(frac * R, 2.0 if quick else 11.0, seed=13 + int(frac * 10))
         c = serve_trace(ctx, traffic, arr, kinds, *CONT, warm_s=1.0, verify=6 if name == "at_80pct" else 0)
         f = serve_trace(ctx, traffic, arr, kinds, *FIFO, warm_s=1.0)
         out[name] = {"rate_per_s": round(frac * R, 1), "counted_s": round(float(arr[-1]) - 1.0, 3),

@@ -500,7 +500,8 @@ typedef struct fe_server fe_server;
  * least 2^26 element-matrix entries are launched alone on one of two extra
  * high-priority streams (never grouped with small ones), their kernels on at
  * most 3/4 of the GPU's resident blocks so that pattern builds and small
- * requests always find free SMs.  n_streams = 1
+ * requests always find free SMs; while one runs, small groups take at most
+ * 1/4 of them, leaving it most of the memory bandwidth.  n_streams = 1
  * with max_batch = 1 is a strict FIFO: one request at a time from admission
  * to completion on one stream (the one-launch-per-request baseline). */
 int fe_server_start(fe_ctx *ctx, int32_t n_streams, int32_t max_batch, size_t hbm_budget_bytes,

@@ -101,8 +101,11 @@ struct Group {
 constexpr int64_t BIG_ENTRIES = (int64_t)1 << 26;
 constexpr int N_BIG_STREAMS = 2;
 // Share of the GPU's resident blocks a large request's kernels take (the
-// rest stays free for pattern builds and small requests).
+// rest stays free for pattern builds and small requests), and the share
+// small groups take while a large request runs (so that it keeps most of the
+// memory bandwidth; small requests still progress beside it).
 constexpr double BIG_SHARE = 0.75;
+constexpr double SMALL_SHARE_BESIDE_BIG = 0.25;
 
 bool is_big(const fe_request &r) { return r.n_elem * (int64_t)r.dofs_per_elem * r.dofs_per_elem >= BIG_ENTRIES; }
 
@@ -125,6 +128,7 @@ struct fe_server {
     size_t cache_bytes = 0;  // bytes of the built patterns in the cache (part of in_use)
     std::vector<cudaStream_t> streams;          // n_small launch streams, then n_big high-priority ones
     int n_small = 0, n_big = 0, next_big = 0;
+    int inflight_big = 0;  // launched large groups not yet complete
     cudaStream_t build_stream = nullptr;       // = build_streams[0]; evicted patterns are freed on it
     std::vector<cudaStream_t> build_streams;   // one per builder thread
     int next_stream = 0, max_batch = 64;
@@ -288,6 +292,7 @@ void scheduler_loop(fe_server *sv)
                 }
                 finish(sv, t, st);
             }
+            if (it->stream >= sv->n_small && sv->inflight_big > 0) --sv->inflight_big;
             cudaEventDestroy(it->t0);
             cudaEventDestroy(it->done);
             it = sv->inflight.erase(it);
@@ -422,6 +427,7 @@ void scheduler_loop(fe_server *sv)
             }
             if (mem.empty()) continue;
             progress = true;
+            const double small_share = sv->inflight_big > 0 ? SMALL_SHARE_BESIDE_BIG : 1.0;
             lk.unlock();
             const double t_launch = now_us();
             if (cudaEventCreate(&g.t0) != cudaSuccess || cudaEventRecord(g.t0, s) != cudaSuccess) {
@@ -447,9 +453,8 @@ void scheduler_loop(fe_server *sv)
             int rc = FE_OK;
             if (!items.empty()) {
                 FeRange range("serve: batched launch");
-                rc = big ? fe_assemble_batch_share(sv->ctx, items.data(), (int32_t)items.size(), fmt, mode, 0, s,
-                                                   BIG_SHARE)
-                         : fe_assemble_batch(sv->ctx, items.data(), (int32_t)items.size(), fmt, mode, 0, nullptr, s);
+                rc = fe_assemble_batch_share(sv->ctx, items.data(), (int32_t)items.size(), fmt, mode, 0, s,
+                                             big ? BIG_SHARE : small_share);
                 if (rc == FE_OK && cudaEventCreate(&g.done) != cudaSuccess) rc = FE_ERR_DEVICE;
                 if (rc == FE_OK && cudaEventRecord(g.done, s) != cudaSuccess) rc = FE_ERR_DEVICE;
             }
@@ -482,6 +487,7 @@ void scheduler_loop(fe_server *sv)
             }
             ++sv->stats.launches;
             sv->stats.batched_requests += g.ids.size();
+            if (g.stream >= sv->n_small) ++sv->inflight_big;
             sv->inflight.push_back(std::move(g));
         }
         if (!progress) sv->cv.wait_for(lk, std::chrono::microseconds(sv->inflight.empty() ? 2000 : 20));
