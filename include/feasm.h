@@ -418,9 +418,9 @@ int fe_batch_graph_launch(fe_batch_graph *graph, void *stream);
 int fe_batch_graph_destroy(fe_batch_graph *graph);
 
 /* ---- serving: requests admitted by HBM footprint, continuous batching ------
- * Not in the paper.  A server owns a scheduler thread (admission, launches,
- * completions) and two pattern-builder threads (each on its own
- * high-priority stream).  Patterns are cached by `pattern_key`; a
+ * Not in the paper.  A server owns a scheduler thread (admission, launches
+ * of small requests, completions), a launcher thread for large requests and
+ * two pattern-builder threads (each on its own high-priority stream).  Patterns are cached by `pattern_key`; a
  * request for a cached key is numeric-only; when memory runs short, patterns
  * no queued request needs are evicted, meshes used once before meshes used
  * again.  Admitted requests are assembled together (fe_assemble_batch) on one

@@ -93,6 +93,26 @@ struct Group {
     int stream = 0;
 };
 
+// A request of a group being launched: what the launch needs, copied from its
+// ticket under the lock, and what the launch produces.
+struct Member {
+    uint64_t id;
+    Ticket *t;
+    fe_request req;
+    const fe_pattern *pattern;
+    size_t k_bytes, v_bytes;
+    double *values = nullptr, *K = nullptr;
+    int rc = FE_OK;
+};
+
+struct LaunchJob {
+    Group g;
+    std::vector<Member> mem;
+    int fmt = 0, mode = 0;
+    bool big = false;
+    double share = 1.0;  // of the resident blocks the group's kernels take
+};
+
 // Requests of at least this many element-matrix entries are launched alone
 // on a high-priority stream: they are not grouped with small requests (whose
 // completion would wait for theirs), and the GPU's block scheduler serves
@@ -138,6 +158,12 @@ struct fe_server {
     bool stop = false;
     std::thread sched;
     std::vector<std::thread> builders;
+    // large requests are launched by a thread of their own: their device
+    // allocations (gigabytes, which can take milliseconds) then do not hold
+    // up the scheduler's launches of small groups
+    std::deque<LaunchJob> big_jobs;
+    std::condition_variable cv_big;
+    std::thread big_launcher;
     fe_server_stats stats{};
     cudaEvent_t t_ref = nullptr;               // origin of the timeline (server start)
     std::vector<fe_span> timeline;             // device spans of launched groups and builds
@@ -266,6 +292,94 @@ bool expire_overdue(fe_server *sv)
     return any;
 }
 
+// Launch one group: its requests' values and generated K, the element
+// generation and the batched assembly on the group's stream, with the lock
+// released (an allocation that grows the memory pool can take
+// milliseconds); then the outcome is booked.  Called with the lock held;
+// returns with it held.  The members are RUNNING meanwhile: no other thread
+// touches a RUNNING ticket (release, cancel and the watchdog skip it).
+void run_launch(fe_server *sv, LaunchJob &job, std::unique_lock<std::mutex> &lk)
+{
+    Group &g = job.g;
+    cudaStream_t s = sv->streams[g.stream];
+    lk.unlock();
+    const double t_launch = now_us();
+    if (cudaEventCreate(&g.t0) != cudaSuccess || cudaEventRecord(g.t0, s) != cudaSuccess) {
+        cudaGetLastError();
+        if (g.t0) cudaEventDestroy(g.t0);
+        g.t0 = nullptr;
+    }
+    std::vector<fe_batch_item> items;
+    double alloc_ms = 0.0;
+    const int gen_sms = std::max(1, (int)(sv->ctx->num_sms * job.share));
+    for (Member &m : job.mem) {
+        const double a0 = now_us();
+        m.rc = fe_alloc(sv->ctx, (void **)&m.values, m.v_bytes, s);
+        if (m.rc == FE_OK && !m.req.elem_mats) m.rc = fe_alloc(sv->ctx, (void **)&m.K, m.k_bytes, s);
+        alloc_ms += (now_us() - a0) * 1e-3;
+        if (m.rc == FE_OK && !m.req.elem_mats)
+            m.rc = launch_generate(m.req.k_ref, m.req.dofs_per_elem, m.req.n_elem, m.req.seed, m.K, gen_sms, s);
+        if (m.rc == FE_OK && m.req.ready_event) cudaStreamWaitEvent(s, (cudaEvent_t)m.req.ready_event, 0);
+        if (m.rc == FE_OK) items.push_back(fe_batch_item{m.pattern, m.K ? m.K : m.req.elem_mats, m.values});
+    }
+    int rc = FE_OK;
+    if (!items.empty()) {
+        FeRange range("serve: batched launch");
+        rc = fe_assemble_batch_share(sv->ctx, items.data(), (int32_t)items.size(), job.fmt, job.mode, 0, s,
+                                     job.share);
+        if (rc == FE_OK && cudaEventCreate(&g.done) != cudaSuccess) rc = FE_ERR_DEVICE;
+        if (rc == FE_OK && cudaEventRecord(g.done, s) != cudaSuccess) rc = FE_ERR_DEVICE;
+    }
+    lk.lock();
+    sv->stats.alloc_ms_total += alloc_ms;
+    sv->stats.alloc_ms_max = std::max(sv->stats.alloc_ms_max, alloc_ms);
+    for (Member &m : job.mem) {
+        Ticket &t = *m.t;
+        t.values = m.values;
+        t.K = m.K;
+        t.v_bytes = m.v_bytes;
+        if (m.rc != FE_OK || rc != FE_OK) {
+            finish(sv, t, m.rc != FE_OK ? m.rc : rc);
+            continue;
+        }
+        // footprint: the values charge becomes exact
+        if (t.v_charged > t.v_bytes) {
+            const size_t drop = t.v_charged - t.v_bytes;
+            t.foot -= std::min(drop, t.foot);
+            sv->in_use -= std::min(drop, sv->in_use);
+            t.v_charged = t.v_bytes;
+        }
+        t.t_start = t_launch;
+        g.ids.push_back(m.id);
+    }
+    if (g.ids.empty()) {
+        if (g.done) cudaEventDestroy(g.done);
+        if (g.t0) cudaEventDestroy(g.t0);
+        return;
+    }
+    ++sv->stats.launches;
+    sv->stats.batched_requests += g.ids.size();
+    if (g.stream >= sv->n_small) ++sv->inflight_big;
+    sv->inflight.push_back(std::move(g));
+    sv->cv.notify_one();
+}
+
+// The large requests' launcher thread.
+void big_launch_loop(fe_server *sv)
+{
+    cudaSetDevice(sv->ctx->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    while (!sv->stop) {
+        if (sv->big_jobs.empty()) {
+            sv->cv_big.wait_for(lk, std::chrono::milliseconds(2));
+            continue;
+        }
+        LaunchJob job = std::move(sv->big_jobs.front());
+        sv->big_jobs.pop_front();
+        run_launch(sv, job, lk);
+    }
+}
+
 // Admission, launches and completions; runs on the scheduler thread.
 void scheduler_loop(fe_server *sv)
 {
@@ -377,13 +491,10 @@ void scheduler_loop(fe_server *sv)
                 sv->cv_build.notify_one();
             }
         }
-        // launches: ready requests grouped by (format, mode).  The members
-        // are taken from the ready queue under the lock; their memory, the
-        // element generation and the batched assembly are issued with the
-        // lock released (an allocation that grows the memory pool can take
-        // milliseconds), and the outcome is booked under the lock again.
-        // Members are marked RUNNING meanwhile: no other thread touches a
-        // RUNNING ticket (release, cancel and the watchdog skip it).
+        // launches: ready requests grouped by (format, mode), taken from
+        // the ready queue under the lock and marked RUNNING.  A small group
+        // is launched here (run_launch); a large request is handed to the
+        // large-request launcher thread.
         while (!sv->ready.empty()) {
             const uint64_t id0 = sv->ready.front();
             const int fmt = sv->tickets[id0].req.format, mode = sv->tickets[id0].req.mode;
@@ -398,16 +509,6 @@ void scheduler_loop(fe_server *sv)
                 g.stream = sv->next_stream;
                 sv->next_stream = (sv->next_stream + 1) % sv->n_small;
             }
-            cudaStream_t s = sv->streams[g.stream];
-            struct Member {
-                uint64_t id;
-                Ticket *t;
-                fe_request req;
-                const fe_pattern *pattern;
-                size_t k_bytes, v_bytes;
-                double *values = nullptr, *K = nullptr;
-                int rc = FE_OK;
-            };
             std::vector<Member> mem;
             const int cap = big ? 1 : sv->max_batch;
             for (auto it = sv->ready.begin(); it != sv->ready.end() && (int)mem.size() < cap;) {
@@ -427,68 +528,20 @@ void scheduler_loop(fe_server *sv)
             }
             if (mem.empty()) continue;
             progress = true;
-            const double small_share = sv->inflight_big > 0 ? SMALL_SHARE_BESIDE_BIG : 1.0;
-            lk.unlock();
-            const double t_launch = now_us();
-            if (cudaEventCreate(&g.t0) != cudaSuccess || cudaEventRecord(g.t0, s) != cudaSuccess) {
-                cudaGetLastError();
-                if (g.t0) cudaEventDestroy(g.t0);
-                g.t0 = nullptr;
+            LaunchJob job;
+            job.g = std::move(g);
+            job.mem = std::move(mem);
+            job.fmt = fmt;
+            job.mode = mode;
+            job.big = big;
+            job.share = big ? BIG_SHARE
+                            : (sv->inflight_big > 0 || !sv->big_jobs.empty() ? SMALL_SHARE_BESIDE_BIG : 1.0);
+            if (big) {
+                sv->big_jobs.push_back(std::move(job));
+                sv->cv_big.notify_one();
+            } else {
+                run_launch(sv, job, lk);
             }
-            std::vector<fe_batch_item> items;
-            double alloc_ms = 0.0;
-            for (Member &m : mem) {
-                const double a0 = now_us();
-                m.rc = fe_alloc(sv->ctx, (void **)&m.values, m.v_bytes, s);
-                if (m.rc == FE_OK && !m.req.elem_mats) m.rc = fe_alloc(sv->ctx, (void **)&m.K, m.k_bytes, s);
-                const double da = (now_us() - a0) * 1e-3;
-                alloc_ms += da;
-                if (m.rc == FE_OK && !m.req.elem_mats)
-                    m.rc = launch_generate(m.req.k_ref, m.req.dofs_per_elem, m.req.n_elem, m.req.seed, m.K,
-                                           big ? std::max(1, (int)(sv->ctx->num_sms * BIG_SHARE)) : sv->ctx->num_sms,
-                                           s);
-                if (m.rc == FE_OK && m.req.ready_event) cudaStreamWaitEvent(s, (cudaEvent_t)m.req.ready_event, 0);
-                if (m.rc == FE_OK) items.push_back(fe_batch_item{m.pattern, m.K ? m.K : m.req.elem_mats, m.values});
-            }
-            int rc = FE_OK;
-            if (!items.empty()) {
-                FeRange range("serve: batched launch");
-                rc = fe_assemble_batch_share(sv->ctx, items.data(), (int32_t)items.size(), fmt, mode, 0, s,
-                                             big ? BIG_SHARE : small_share);
-                if (rc == FE_OK && cudaEventCreate(&g.done) != cudaSuccess) rc = FE_ERR_DEVICE;
-                if (rc == FE_OK && cudaEventRecord(g.done, s) != cudaSuccess) rc = FE_ERR_DEVICE;
-            }
-            lk.lock();
-            sv->stats.alloc_ms_total += alloc_ms;
-            sv->stats.alloc_ms_max = std::max(sv->stats.alloc_ms_max, alloc_ms);
-            for (Member &m : mem) {
-                Ticket &t = *m.t;
-                t.values = m.values;
-                t.K = m.K;
-                t.v_bytes = m.v_bytes;
-                if (m.rc != FE_OK || rc != FE_OK) {
-                    finish(sv, t, m.rc != FE_OK ? m.rc : rc);
-                    continue;
-                }
-                // footprint: the values charge becomes exact
-                if (t.v_charged > t.v_bytes) {
-                    const size_t drop = t.v_charged - t.v_bytes;
-                    t.foot -= std::min(drop, t.foot);
-                    sv->in_use -= std::min(drop, sv->in_use);
-                    t.v_charged = t.v_bytes;
-                }
-                t.t_start = t_launch;
-                g.ids.push_back(m.id);
-            }
-            if (g.ids.empty()) {
-                if (g.done) cudaEventDestroy(g.done);
-                if (g.t0) cudaEventDestroy(g.t0);
-                continue;
-            }
-            ++sv->stats.launches;
-            sv->stats.batched_requests += g.ids.size();
-            if (g.stream >= sv->n_small) ++sv->inflight_big;
-            sv->inflight.push_back(std::move(g));
         }
         if (!progress) sv->cv.wait_for(lk, std::chrono::microseconds(sv->inflight.empty() ? 2000 : 20));
     }
@@ -674,6 +727,7 @@ int fe_server_start(fe_ctx *ctx, int32_t n_streams, int32_t max_batch, size_t hb
     }
     sv->sched = std::thread(scheduler_loop, sv);
     for (int k = 0; k < N_BUILDERS; ++k) sv->builders.emplace_back(builder_loop, sv, k);
+    sv->big_launcher = std::thread(big_launch_loop, sv);
     *out = sv;
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
     return FE_OK;
@@ -688,8 +742,10 @@ int fe_server_stop(fe_server *sv)
     }
     sv->cv.notify_all();
     sv->cv_build.notify_all();
+    sv->cv_big.notify_all();
     sv->sched.join();
     for (auto &t : sv->builders) t.join();
+    sv->big_launcher.join();
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != sv->ctx->device) cudaSetDevice(sv->ctx->device);
