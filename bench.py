@@ -50,6 +50,7 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the serving block of the default line")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched block of the default line")
     ap.add_argument("--knob", action="append", default=[], metavar="NAME=VALUE",
                     help="set a schedule knob before the run, e.g. GATHER_KERNEL=4 (FE_KNOB_<NAME>)")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "served", "sweep", "tet96"],
@@ -670,10 +671,12 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_batched(args, local_rank):
+def batched_block(local_rank, n_meshes=256):
     """256 independent hex meshes (n ~ logU[8,48]; half Q1 Laplace 8x8, half
     Q1 elasticity 24x24), K_e = alpha_e K_ref on the device: one launch per
-    mesh versus one autotuned persistent launch and its CUDA-graph replay."""
+    mesh versus one autotuned persistent launch and its CUDA-graph replay,
+    in both modes, with each mesh's completion latency inside the step.
+    Returns (modes, figures of the workload)."""
     import torch
 
     import workloads as wl
@@ -683,7 +686,7 @@ def run_batched(args, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
     ctx = fe.fe_create(local_rank)
-    sizes = wl.batched_mesh_sizes(args.meshes, seed=0)
+    sizes = wl.batched_mesh_sizes(n_meshes, seed=0)
     meshes = []
     n_ent = 0
     nnz_tot = 0
@@ -766,6 +769,22 @@ def run_batched(args, local_rank):
             "meshes": len(meshes), "repeats": reps,
             "definition": "time from the start of the step until a mesh's values are complete, over every mesh"}
         out[mode_name] = res
+    for p, _, _, _, _ in meshes:
+        fe.fe_pattern_free(p)
+    fe.fe_destroy(ctx)
+    hbm, _ = measured_peaks()
+    for res in out.values():
+        for name in ("per_mesh", "batched", "graph"):
+            res[name]["frac_of_peak"] = round(res[name]["alg_GBps"] / hbm, 4)
+    return out, {"entries_per_step": n_ent, "nnz_total": nnz_tot, "alg_bytes_per_step": alg, "meshes": len(meshes)}
+
+
+def run_batched(args, local_rank):
+    """The batched workload on its own (--workload batched): one JSON line
+    whose value is the better of the batched and graph-replayed
+    deterministic step."""
+    out, fig = batched_block(local_rank, args.meshes)
+    n_ent, nnz_tot, alg = fig["entries_per_step"], fig["nnz_total"], fig["alg_bytes_per_step"]
     hbm, _ = measured_peaks()
     best = min(out["det"]["graph"]["ms_median"], out["det"]["batched"]["ms_median"])
     line = {"metric": METRIC, "value": n_ent / (best * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": 10, "warmup": 3,
@@ -777,9 +796,6 @@ def run_batched(args, local_rank):
             "roofline": {"bound": "hbm", "achieved": round(alg / (best * 1e-3) / 1e9, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(alg / (best * 1e-3) / 1e9 / hbm, 4), "traffic": None},
             "modes": out}
-    for p, _, _, _, _ in meshes:
-        fe.fe_pattern_free(p)
-    fe.fe_destroy(ctx)
     return line
 
 
@@ -1033,6 +1049,16 @@ def _overlap(spans):
     return (round(multi / busy, 4) if busy > 0 else None), round(busy, 3)
 
 
+SERVE_WAIT_S = 60.0  # longest wait for one served request before the trace is reported stuck
+
+
+class ServeStuck(RuntimeError):
+    """A served trace whose requests did not all finish; carries the details."""
+
+
+STUCK_SERVERS = []  # servers left running after a stuck trace (never stopped or freed)
+
+
 def serve_trace(ctx, traffic, arrivals, kinds, n_streams, max_batch, warm_s=0.0, verify=0, seed_base=1000):
     """Serve one trace on a fresh server (n_streams streams, at most
     max_batch requests per launch; 1 and 1 = strict FIFO), deterministic
@@ -1068,15 +1094,26 @@ def serve_trace(ctx, traffic, arrivals, kinds, n_streams, max_batch, warm_s=0.0,
     res = [None] * m
     done = threading.Event()
 
+    stuck = []  # (index, state, stage times) of requests not done within WAIT_S of their turn
+
     def collect():
-        for k in range(m):
-            while tickets[k] is None:
-                time.sleep(1e-4)
-            r = fe.fe_wait(sv, tickets[k], 900)
-            res[k] = (r["state"], r["t_submit_us"], r["t_start_us"], r["t_done_us"], r["t_admit_us"], r["t_ready_us"])
-            if k not in keep or r["state"] != fe.FE_STATE_DONE:
-                fe.fe_release(sv, tickets[k])
-        done.set()
+        try:
+            for k in range(m):
+                while tickets[k] is None:
+                    time.sleep(1e-4)
+                try:
+                    r = fe.fe_wait(sv, tickets[k], SERVE_WAIT_S)
+                except fe.FeError:
+                    r = fe.fe_poll(sv, tickets[k])
+                    stuck.append({"request": k, "large": bool(kinds[k][1]), "warm": bool(kinds[k][2]),
+                                  "state": r["state"], "t_admit_us": r["t_admit_us"], "t_ready_us": r["t_ready_us"],
+                                  "t_start_us": r["t_start_us"], "t_submit_us": r["t_submit_us"]})
+                    continue
+                res[k] = (r["state"], r["t_submit_us"], r["t_start_us"], r["t_done_us"], r["t_admit_us"], r["t_ready_us"])
+                if k not in keep or r["state"] != fe.FE_STATE_DONE:
+                    fe.fe_release(sv, tickets[k])
+        finally:
+            done.set()
 
     cold_key = 1 << 40
     reqs = []
@@ -1109,11 +1146,23 @@ def serve_trace(ctx, traffic, arrivals, kinds, n_streams, max_batch, warm_s=0.0,
         for i, t in enumerate(ts):
             tickets[k + i] = t
         k = j
-    done.wait()
+    done.wait(SERVE_WAIT_S * 4 + 60)
     sys.setswitchinterval(switch)
-    th.join()
+    th.join(60)
     st = fe.fe_server_stats_get(sv)
     spans = fe.fe_server_timeline(sv)[spans0:]
+    if stuck or th.is_alive():
+        # a request the server did not finish: report it with the server's
+        # state instead of waiting on it.  The server is left running (the
+        # collector may still be waiting on it); the process ends with
+        # os._exit after the bench line is printed.
+        STUCK_SERVERS.append(sv)
+        raise ServeStuck({"stuck": stuck[:8], "n_stuck": len(stuck), "collector_alive": th.is_alive(),
+                          "stats": {k2: st[k2] for k2 in ("submitted", "admitted", "completed", "failed",
+                                                          "bytes_in_use", "budget_bytes", "cached_patterns",
+                                                          "launches", "patterns_built", "evictions", "n_pending",
+                                                          "n_to_build", "n_ready", "n_big_jobs", "n_running",
+                                                          "n_inflight_groups")}})
 
 
     import torch
@@ -1257,7 +1306,11 @@ def run_served(args, local_rank):
     from paper_2012_00585_gb300 import feasm as fe
     torch.cuda.set_device(local_rank)
     ctx = fe.fe_create(local_rank)
-    blk = served_block(ctx, fe, torch.device("cuda", local_rank), quick=args.duration < 2.0)
+    try:
+        blk = served_block(ctx, fe, torch.device("cuda", local_rank), quick=args.duration < 2.0)
+    except ServeStuck as e:
+        return {"metric": "served p99 latency at 80% of the sustainable rate", "value": None, "unit": "ms",
+                "error": "a served request did not finish within %d s" % SERVE_WAIT_S, "detail": e.args[0]}
     fe.fe_destroy(ctx)
     p99 = blk["at_80pct"]["continuous"]["p99_ms"]
     return {"metric": "served p99 latency at 80% of the sustainable rate", "value": p99, "unit": "ms",
@@ -1280,6 +1333,8 @@ def main():
     if args.workload == "served":
         if rank == 0:
             print(json.dumps(run_served(args, local_rank)), flush=True)
+        if STUCK_SERVERS:
+            os._exit(0)
         return
     if args.workload == "sweep":
         if rank == 0:
@@ -1299,12 +1354,31 @@ def main():
         import torch
         from paper_2012_00585_gb300 import feasm
         sctx = feasm.fe_create(local_rank)
-        out["served"] = served_block(sctx, feasm, torch.device("cuda", local_rank))
-        feasm.fe_destroy(sctx)
+        try:
+            out["served"] = served_block(sctx, feasm, torch.device("cuda", local_rank))
+            feasm.fe_destroy(sctx)
+        except ServeStuck as e:
+            # the server's state is kept in the line; the stuck server and its
+            # context are left to process exit
+            out["served"] = {"error": "a served request did not finish within %d s" % SERVE_WAIT_S,
+                             "detail": e.args[0]}
+    if rank == 0 and world == 1 and not args.no_batched:
+        try:
+            modes, fig = batched_block(local_rank)
+            out["batched"] = {"workload": "256 hex meshes n~logU[8,48] (seeded), half Q1 Laplace 8x8 (d=1), half "
+                                          "Q1 elasticity 24x24 (d=3), CSR; one step = every mesh assembled once",
+                              **fig, "modes": modes}
+        except Exception as e:  # reported in the line; the step's own figures stand
+            out["batched"] = {"error": repr(e)[:300]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.n)
     if rank == 0:
         print(json.dumps(out), flush=True)
+    if STUCK_SERVERS:
+        # a server still holds a request it never finished: end the process
+        # without running its destructors under the server's threads
+        sys.stdout.flush()
+        os._exit(0)
     if world > 1:
         import torch.distributed as tdist
         tdist.barrier()

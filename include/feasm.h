@@ -159,8 +159,9 @@ int fe_debug_checks(void);
                                     lanes each; slices of <= 16 entries)    */
 #define FE_KNOB_GATHER_BATCH 1   /* incidences per register batch: 4 or 8   */
 #define FE_KNOB_GATHER_WARPS 2   /* warps per block of the gather: 1..8      */
-#define FE_KNOB_ATOMIC_KERNEL 3  /* FE_ATOMIC: 1 register warp-per-element,
-                                    2 bulk-copy (TMA) staged warp-per-element */
+#define FE_KNOB_ATOMIC_KERNEL 3  /* FE_ATOMIC: 0 default (1), 1 register
+                                    warp-per-element, 2 bulk-copy (TMA)
+                                    staged warp-per-element                 */
 #define FE_KNOB_ATOMIC_WARPS 4   /* warps per block of the staged kernel     */
 #define FE_KNOB_ATOMIC_ORDER 5   /* read by fe_pattern_build: the element
                                     order of the FE_ATOMIC scatter.  0 auto
@@ -479,6 +480,10 @@ typedef struct fe_server_stats {
     int64_t peak_bytes_in_use;  /* largest bytes charged at once                */
     double alloc_ms_total, alloc_ms_max;  /* host time in the launches' device
                                    allocations (values, generated K)          */
+    /* requests in each stage now: waiting for admission, waiting for a
+       pattern build, ready to launch, handed to the large-request launcher,
+       launched and not complete; groups in flight */
+    int64_t n_pending, n_to_build, n_ready, n_big_jobs, n_running, n_inflight_groups;
 } fe_server_stats;
 
 /* One span of device work seen by the server: a launched group of requests

@@ -132,7 +132,7 @@ __device__ __forceinline__ void atomic_element(const double *__restrict__ K, int
                 if (q < NN && FE_IN_BOUNDS(b + (int64_t)BB * pos + c % BB, g.nnz, g.status)) {
                     double *dst = values + b + (int64_t)BB * pos + c % BB;
                     if (PLAIN) *dst = *dst + kv[u];
-                    else atomicAdd(dst, kv[u]);
+                    else fe_red_add_f64(dst, kv[u]);
                 }
             }
         }
@@ -172,7 +172,7 @@ __device__ __forceinline__ void atomic_element_generic(const double *__restrict_
         if (!FE_IN_BOUNDS(base_s[r] + (int64_t)B * pos + c % B, g.nnz, g.status)) continue;
         double *dst = values + base_s[r] + (int64_t)B * pos + c % B;
         if (PLAIN) *dst = *dst + __ldcs(Ke + q);
-        else atomicAdd(dst, __ldcs(Ke + q));
+        else fe_red_add_f64(dst, __ldcs(Ke + q));
     }
     __syncwarp();
 }

@@ -187,7 +187,7 @@ __device__ __noinline__ bool staged_tile(const BatchItemDev *__restrict__ it, in
                     pos = pos_s[(r / BB) * (kw >> 16) + (kw & 0xffff)] + off_s[kc];
                 }
                 if (FE_IN_BOUNDS(base_s[r] + BB * pos + c % BB, g.nnz, g.status))
-                    atomicAdd(values + base_s[r] + BB * pos + c % BB, stg[q]);
+                    fe_red_add_f64(values + base_s[r] + BB * pos + c % BB, stg[q]);
             }
         }
         __syncwarp();
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(sched_threads(SCHED), SCHED == FE_SCHED_WARP_P
                                                  : (int)((const uint16_t *)it.mapc)[mi]) + off_s[kc];
                     }
                     if (FE_IN_BOUNDS(base_s[r] + (int64_t)B * pos + c % B, it.g.nnz, it.g.status))
-                        atomicAdd(it.values + base_s[r] + (int64_t)B * pos + c % B, __ldcs(it.K + e * NN + q));
+                        fe_red_add_f64(it.values + base_s[r] + (int64_t)B * pos + c % B, __ldcs(it.K + e * NN + q));
                 }
                 __syncthreads();
             }

@@ -178,5 +178,13 @@ inline int fe_grid_resident(KernelT kernel, int64_t work, int threads, int num_s
     return fe_grid_for(work, threads, num_sms, fe_resident_blocks((const void *)kernel, threads, smem));
 }
 
+// FP64 add into global memory whose old value is not needed: issued as a
+// reduction (RED, performed in L2, nothing returned), with no compiler
+// memory barrier, so independent loads may be scheduled across it.
+__device__ __forceinline__ void fe_red_add_f64(double *p, double v)
+{
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v));
+}
+
 __device__ __forceinline__ int64_t fe_warp_id() { return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
 __device__ __forceinline__ int64_t fe_warps() { return ((int64_t)gridDim.x * blockDim.x) >> 5; }

@@ -20,12 +20,13 @@
 // row start read from the CRAC pairs (Listing 5's contiguous slices).
 //
 // Kernels (defaults first; the others are schedule knobs, every one
-// parity-tested): atomic -- k_atomic_tma (K_e staged by a bulk copy),
-// k_atomic_elem, k_atomic_generic; deterministic -- k_gather_node (3-DOF
-// and other specialised shapes), k_gather_small (slices of at most 16
-// entries, several rows per warp), k_gather_generic (any shape), and the
-// variants k_gather_async, k_gather_pipe, k_gather_bulk, k_gather_pair.
-// FE_COLOURED and FE_ROWLOCK are in colour.cu and rowlock.cu.
+// parity-tested): atomic -- k_atomic_elem (K_e through registers),
+// k_atomic_tma (K_e staged by a bulk copy), k_atomic_generic (any shape);
+// deterministic -- k_gather_node (3-DOF and other specialised shapes),
+// k_gather_small (slices of at most 16 entries, several rows per warp),
+// k_gather_generic (any shape).  Every FP64 add of the atomic kernels is a
+// reduction (fe_red_add_f64).  FE_COLOURED and FE_ROWLOCK are in colour.cu
+// and rowlock.cu.
 #include "assemble_body.cuh"
 #include "internal.cuh"
 #include "tma.cuh"
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(256) k_atomic_elem(const double *__restrict__ 
                         const int off = __shfl_sync(0xffffffffu, koff, kc);
                         pos = (int)mapc[rp * NLN + (r / BB) * nr + k] + off;
                     }
-                    if (q < NN) atomicAdd(values + b + (int64_t)BB * pos + c % BB, kv[u]);
+                    if (q < NN) fe_red_add_f64(values + b + (int64_t)BB * pos + c % BB, kv[u]);
                 }
             }
         }
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(256) k_atomic_generic(const double *__restrict
             int pos;
             if (!CRAC) pos = (int)map[(e * nln + r / B) * nln + kc];
             else pos = (int)mapc[rp * nln + (int64_t)(r / B) * nr + k_s[w][kc]] + off_s[w][kc];
-            atomicAdd(values + base_s[w][r] + (int64_t)B * pos + c % B, __ldcs(Ke + q));
+            fe_red_add_f64(values + base_s[w][r] + (int64_t)B * pos + c % B, __ldcs(Ke + q));
         }
         __syncwarp();
     }
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(128) k_atomic_tma(const double *__restrict__ K
                     pos = pos_s[(r / BB) * (kw >> 16) + (kw & 0xffff)] + off_s[kc];
                 }
                 if (FE_IN_BOUNDS(base_s[r] + BB * pos + c % BB, g.nnz, g.status))
-                    atomicAdd(values + base_s[r] + BB * pos + c % BB, stg[q]);
+                    fe_red_add_f64(values + base_s[r] + BB * pos + c % BB, stg[q]);
             }
         }
         __syncwarp();
@@ -435,7 +436,10 @@ int launch_atomic(const fe_pattern *p, const double *K, double *values, cudaStre
     const int sms = p->ctx->num_sms;
     if constexpr (NLN > 0) {
         constexpr int NLOC = NLN * BB;
-        if (p->ctx->knob[FE_KNOB_ATOMIC_KERNEL] != 1 && tma_ok(p, K, NLOC * NLOC)) {
+        // default: the register kernel (C2 CSR 520 vs 601 us, C3 CSR 21.4 vs
+        // 29.5 ms, CRAC 20.5 vs 22.9 ms against the staged kernel, once the
+        // adds were issued as reductions); the staged kernel on request
+        if (p->ctx->knob[FE_KNOB_ATOMIC_KERNEL] == 2 && tma_ok(p, K, NLOC * NLOC)) {
             const int W = (p->ctx->knob[FE_KNOB_ATOMIC_WARPS] > 0 && p->ctx->knob[FE_KNOB_ATOMIC_WARPS] <= 4)
                               ? p->ctx->knob[FE_KNOB_ATOMIC_WARPS]
                               : 4;  // launch bound: 128 threads

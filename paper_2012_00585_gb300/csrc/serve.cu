@@ -864,6 +864,14 @@ int fe_server_stats_get(fe_server *sv, fe_server_stats *out)
     out->bytes_in_use = (int64_t)sv->in_use;
     out->budget_bytes = (int64_t)sv->budget;
     out->cached_patterns = (int64_t)sv->cache.size();
+    out->n_pending = (int64_t)sv->pending.size();
+    out->n_to_build = (int64_t)sv->to_build.size();
+    out->n_ready = (int64_t)sv->ready.size();
+    out->n_big_jobs = (int64_t)sv->big_jobs.size();
+    int64_t running = 0;
+    for (const Group &g : sv->inflight) running += (int64_t)g.ids.size();
+    out->n_running = running;
+    out->n_inflight_groups = (int64_t)sv->inflight.size();
     return FE_OK;
 }
 

@@ -129,7 +129,9 @@ class fe_server_stats(ctypes.Structure):
                                               "launches", "batched_requests", "patterns_built", "evictions",
                                               "bytes_in_use", "budget_bytes", "cached_patterns", "rebuilds",
                                               "expired", "admission_waits", "peak_bytes_in_use")] + \
-        [("alloc_ms_total", ctypes.c_double), ("alloc_ms_max", ctypes.c_double)]
+        [("alloc_ms_total", ctypes.c_double), ("alloc_ms_max", ctypes.c_double)] + \
+        [(n, ctypes.c_int64) for n in ("n_pending", "n_to_build", "n_ready", "n_big_jobs", "n_running",
+                                       "n_inflight_groups")]
 
 
 class fe_span(ctypes.Structure):

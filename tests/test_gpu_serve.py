@@ -394,7 +394,7 @@ def test_small_request_passes_a_waiting_large_one(ctx):
         side = torch.cuda.Stream()
         ev = torch.cuda.Event()
         with torch.cuda.stream(side):
-            torch.cuda._sleep(int(1.5e9))  # about 0.7 s at GB300 clocks
+            torch.cuda._sleep(int(5e9))  # about 2.4 s at GB300 clocks: S is done long before
             ev.record(side)
         (ta,) = fe.fe_batch_submit(sv, [fe.make_request(1, Dd, n_dofs, k_ref=Krd, seed=1, ready_event=ev)])
         (tb,) = fe.fe_batch_submit(sv, [fe.make_request(2, Dd, n_dofs, k_ref=Krd, seed=2)])
