@@ -1094,24 +1094,60 @@ def serve_trace(ctx, traffic, arrivals, kinds, n_streams, max_batch, warm_s=0.0,
     res = [None] * m
     done = threading.Event()
 
-    stuck = []  # (index, state, stage times) of requests not done within WAIT_S of their turn
+    stuck = []  # requests still unfinished after SERVE_WAIT_S without any completion
 
     def collect():
+        # Results are released as soon as they are done, in any order: a
+        # result the client still holds keeps its values and its pattern
+        # charged against the server's budget, so waiting on one slow
+        # request while later ones sit finished could starve the admission
+        # of the slow one (a large request waiting for memory).  Each pass
+        # waits briefly on the oldest outstanding ticket and polls a window
+        # of the ones behind it.
+        fin = (fe.FE_STATE_DONE, fe.FE_STATE_FAILED, fe.FE_STATE_CANCELLED)
+        outstanding = []  # submitted, not yet finished, in submission order
+        nxt = 0
+        n_fin = 0
+        last = time.perf_counter()
+
+        def book(k, r):
+            res[k] = (r["state"], r["t_submit_us"], r["t_start_us"], r["t_done_us"], r["t_admit_us"], r["t_ready_us"])
+            if k not in keep or r["state"] != fe.FE_STATE_DONE:
+                fe.fe_release(sv, tickets[k])
+
         try:
-            for k in range(m):
-                while tickets[k] is None:
+            while n_fin < m:
+                while nxt < m and tickets[nxt] is not None:
+                    outstanding.append(nxt)
+                    nxt += 1
+                if not outstanding:
                     time.sleep(1e-4)
-                try:
-                    r = fe.fe_wait(sv, tickets[k], SERVE_WAIT_S)
-                except fe.FeError:
-                    r = fe.fe_poll(sv, tickets[k])
-                    stuck.append({"request": k, "large": bool(kinds[k][1]), "warm": bool(kinds[k][2]),
-                                  "state": r["state"], "t_admit_us": r["t_admit_us"], "t_ready_us": r["t_ready_us"],
-                                  "t_start_us": r["t_start_us"], "t_submit_us": r["t_submit_us"]})
                     continue
-                res[k] = (r["state"], r["t_submit_us"], r["t_start_us"], r["t_done_us"], r["t_admit_us"], r["t_ready_us"])
-                if k not in keep or r["state"] != fe.FE_STATE_DONE:
-                    fe.fe_release(sv, tickets[k])
+                finished = set()
+                try:
+                    r = fe.fe_wait(sv, tickets[outstanding[0]], 0.002)
+                except fe.FeError:
+                    r = None
+                if r is not None and r["state"] in fin:
+                    book(outstanding[0], r)
+                    finished.add(0)
+                for i in range(1, min(len(outstanding), 257)):
+                    r = fe.fe_poll(sv, tickets[outstanding[i]])
+                    if r["state"] in fin:
+                        book(outstanding[i], r)
+                        finished.add(i)
+                now = time.perf_counter()
+                if finished:
+                    outstanding = [k for i, k in enumerate(outstanding) if i not in finished]
+                    n_fin += len(finished)
+                    last = now
+                elif nxt == m and now - last > SERVE_WAIT_S:
+                    for k in outstanding:
+                        r = fe.fe_poll(sv, tickets[k])
+                        stuck.append({"request": k, "large": bool(kinds[k][1]), "warm": bool(kinds[k][2]),
+                                      "state": r["state"], "t_admit_us": r["t_admit_us"],
+                                      "t_ready_us": r["t_ready_us"], "t_start_us": r["t_start_us"]})
+                    break
         finally:
             done.set()
 
