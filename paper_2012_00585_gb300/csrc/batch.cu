@@ -331,9 +331,9 @@ constexpr int sched_threads(int sched) { return sched == FE_SCHED_WARP_PER_ROW ?
 // in the per-tile call) and 7.65 ms at 128.
 template <bool CRAC, int SCHED>
 __global__ void __launch_bounds__(sched_threads(SCHED), SCHED == FE_SCHED_WARP_PER_ROW ? 7 : 1) k_batch(const BatchItemDev *__restrict__ items, int n_items,
-                                                         int64_t total_tiles, int tile, int cap, int accumulate,
-                                                         unsigned long long *counter, int stage, int *status,
-                                                         unsigned int *tc)
+                                                         int64_t t_lo, int64_t total_tiles, int tile, int cap,
+                                                         int accumulate, unsigned long long *counter, int stage,
+                                                         int *status, unsigned int *tc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long block_tile;
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(sched_threads(SCHED), SCHED == FE_SCHED_WARP_P
         int32_t *k_s = (int32_t *)(base_s + FE_MAX_NLOC);  // [FE_MAX_NLOC] run index (CRAC)
         int32_t *off_s = k_s + FE_MAX_NLOC;                // [FE_MAX_NLOC] offset in run (CRAC)
         for (;;) {
-            if (threadIdx.x == 0) block_tile = atomicAdd(counter, 1ull);
+            if (threadIdx.x == 0) block_tile = (unsigned long long)t_lo + atomicAdd(counter, 1ull);
             __syncthreads();
             const unsigned long long t = block_tile;
             __syncthreads();
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(sched_threads(SCHED), SCHED == FE_SCHED_WARP_P
         uint32_t phase = 0;
         for (;;) {
             unsigned long long t = 0;
-            if (lane == 0) t = atomicAdd(counter, 1ull);
+            if (lane == 0) t = (unsigned long long)t_lo + atomicAdd(counter, 1ull);
             t = __shfl_sync(0xffffffffu, t, 0);
             if (t >= (unsigned long long)total_tiles) break;
             const int ii = find_item(items, n_items, (int64_t)t);
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(sched_threads(SCHED), SCHED == FE_SCHED_WARP_P
     } else {
         for (;;) {
             unsigned long long t = 0;
-            if (lane == 0) t = atomicAdd(counter, 1ull);
+            if (lane == 0) t = (unsigned long long)t_lo + atomicAdd(counter, 1ull);
             t = __shfl_sync(0xffffffffu, t, 0);
             if (t >= (unsigned long long)total_tiles) break;
             const int ii = find_item(items, n_items, (int64_t)t);
@@ -506,12 +506,72 @@ __global__ void k_batch_zero(const BatchItemDev *__restrict__ items, int n_items
     }
 }
 
+// FE_DETERMINISTIC items of one specialised 3-DOF shape with one-byte slot
+// maps (the bulk of a batch of elasticity meshes): tiles [t_lo, t_hi) of
+// items [i_lo, i_hi) through the single-mesh row loop, inlined, so that the
+// kernel needs the registers of that loop alone (no per-shape dispatch, no
+// call).  Incidences two at a time, 9 blocks of 4 warps per SM (56
+// registers): measured on the 256-mesh batch, 5.78 ms, against 5.80 ms at 8
+// blocks, 5.76 ms at 10 (more spills), 5.94 ms with four incidences at a
+// time and 7 blocks, and 6.28 ms through the general kernel.
+template <int NLN, int BB, bool CRAC>
+__global__ void __launch_bounds__(128, 9) k_batch_rows(const BatchItemDev *__restrict__ items, int i_lo, int i_hi,
+                                                       int64_t t_lo, int64_t t_hi, int tile, int cap, int accumulate,
+                                                       unsigned long long *counter, unsigned int *tc)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    double *acc = (double *)smem_raw + (size_t)(threadIdx.x >> 5) * cap;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = (unsigned long long)t_lo + atomicAdd(counter, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= (unsigned long long)t_hi) break;
+        const int ii = i_lo + find_item(items + i_lo, i_hi - i_lo, (int64_t)t);
+        const BatchItemDev &it = items[ii];
+        const int64_t u0 = ((int64_t)t - it.tile_begin) * tile, u1 = min(u0 + tile, it.units);
+        if (lane == 0) tile_started(it, ii, tc);
+        Geo g;
+        if (CRAC) {
+            g.crac_ptr = it.g.crac_ptr;
+            g.col_align = it.g.col_align;
+        } else {
+            g.row_ptr = it.g.row_ptr;
+        }
+        g.adj_ptr = it.g.adj_ptr;
+        g.adj = it.g.adj;
+        g.crac_rows = CRAC ? 1 : 0;
+        g.nnz = it.g.nnz;
+        g.status = it.g.status;
+        gather_node_rows<NLN, BB, uint8_t, 2>(it.K, g, (const uint8_t *)it.map, acc, cap, accumulate, it.values, u0,
+                                              u1, 1, lane);
+        __syncwarp();
+        if (lane == 0) tile_finished(it, ii, tc, tile);
+    }
+}
+
+// Items of one specialised class occupy a contiguous range of the plan.
+struct RowClass {
+    int shape = 0;
+    int i_lo = 0, i_hi = 0;
+    int64_t t_lo = 0, t_hi = 0;
+};
+
 struct Plan {
     std::vector<BatchItemDev> host;
     int64_t total_tiles = 0;
     int cap = 1;    // doubles of accumulator per warp (deterministic)
     int stage = 0;  // doubles per bulk-copy stage (FE_SCHED_WARP_PER_ELEMENT_TMA)
+    // FE_DETERMINISTIC: the items of the specialised row classes come first,
+    // one class after the other; the rest of the tiles [rest_t, total) go to
+    // the general kernel
+    std::vector<RowClass> classes;
+    int64_t rest_t = 0;
 };
+
+// Counters of a batched launch: the general kernel's, one per row class,
+// then two tile counters per item (per-item timestamps).
+constexpr int BATCH_COUNTERS = 3;
 
 // Largest K_e (doubles) a bulk-copy stage holds: 32 x 32.
 constexpr int STAGE_MAX = 32 * 32;
@@ -521,7 +581,32 @@ int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
     plan.host.resize(n);
     plan.total_tiles = 0;
     plan.cap = 1;
-    for (int i = 0; i < n; ++i) {
+    plan.classes.clear();
+    // FE_DETERMINISTIC: 3-DOF items with one-byte maps first, by shape, for
+    // their specialised kernels; the rest keep their order after them
+    std::vector<int> order;
+    order.reserve(n);
+    if (mode == FE_DETERMINISTIC) {
+        for (int sh : {SH_8_3, SH_10_3}) {
+            RowClass rc;
+            rc.shape = sh;
+            rc.i_lo = (int)order.size();
+            for (int i = 0; i < n; ++i) {
+                const fe_pattern *p = items[i].pattern;
+                if (p && p->ctx == ctx && shape_of(p) == sh && p->map_bytes == 1) order.push_back(i);
+            }
+            rc.i_hi = (int)order.size();
+            if (rc.i_hi > rc.i_lo) plan.classes.push_back(rc);
+        }
+    }
+    {
+        std::vector<char> taken(n, 0);
+        for (int i : order) taken[i] = 1;
+        for (int i = 0; i < n; ++i)
+            if (!taken[i]) order.push_back(i);
+    }
+    for (int slot = 0; slot < n; ++slot) {
+        const int i = order[slot];
         const fe_pattern *p = items[i].pattern;
         if (!p || p->ctx != ctx) return FE_ERR_INVALID_ARG;
         if ((p->n_e > 0 && !items[i].elem_mats) || (p->nnz > 0 && !items[i].values)) return FE_ERR_INVALID_ARG;
@@ -531,7 +616,7 @@ int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
         if (format == FE_FORMAT_CSR && !p->map_csr) return FE_ERR_NOT_BUILT;
         if (format == FE_FORMAT_CRAC && (!p->map_crac || !p->col_align || !p->map_crac_blk)) return FE_ERR_NOT_BUILT;
         if (mode == FE_DETERMINISTIC && !p->adj) return FE_ERR_NOT_BUILT;
-        BatchItemDev &d = plan.host[i];
+        BatchItemDev &d = plan.host[slot];
         d.g = geo_of(p);
         d.K = items[i].elem_mats;
         d.values = items[i].values;
@@ -560,6 +645,12 @@ int make_plan(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
         if (d.shape == SH_4_1) plan.cap = std::max(plan.cap, SmallRows<4>::RPW * p->max_row_len);
         if (d.shape == SH_8_1) plan.cap = std::max(plan.cap, SmallRows<8>::RPW * p->max_row_len);
     }
+    plan.rest_t = 0;
+    for (RowClass &rc : plan.classes) {
+        rc.t_lo = plan.host[rc.i_lo].tile_begin;
+        rc.t_hi = rc.i_hi < n ? plan.host[rc.i_hi].tile_begin : plan.total_tiles;
+        plan.rest_t = rc.t_hi;
+    }
     return FE_OK;
 }
 
@@ -576,8 +667,9 @@ size_t batch_smem(int mode, int sched, int cap, int stage)
 }
 
 template <bool CRAC, int SCHED>
-int launch_batch_t(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t total, int tile, int cap, int acc,
-                   unsigned long long *counter, size_t smem, int stage, unsigned int *tc, double frac, cudaStream_t s)
+int launch_batch_t(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t t_lo, int64_t total, int tile, int cap,
+                   int acc, unsigned long long *counter, size_t smem, int stage, unsigned int *tc, double frac,
+                   cudaStream_t s)
 {
     auto kern = k_batch<CRAC, SCHED>;
     constexpr int threads = sched_threads(SCHED);
@@ -585,40 +677,90 @@ int launch_batch_t(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t tota
     int per_sm = 0;
     FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) return FE_ERR_UNSUPPORTED;
-    const int64_t want = SCHED == FE_SCHED_BLOCK_PER_ELEMENT ? total : (total + threads / 32 - 1) / (threads / 32);
+    const int64_t want = SCHED == FE_SCHED_BLOCK_PER_ELEMENT ? total - t_lo
+                                                             : (total - t_lo + threads / 32 - 1) / (threads / 32);
     // frac < 1: the persistent grid takes only that share of the resident blocks
     const int64_t resident = std::max<int64_t>(1, (int64_t)((double)ctx->num_sms * per_sm * frac));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident, want));
-    kern<<<grid, threads, smem, s>>>(d_items, n, total, tile, cap, acc, counter, stage, ctx->d_status, tc);
+    kern<<<grid, threads, smem, s>>>(d_items, n, t_lo, total, tile, cap, acc, counter, stage, ctx->d_status, tc);
     fe_note_launch();
     FE_CUDA(cudaGetLastError());
     return FE_OK;
 }
 
-int launch_batch(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t total, int format, int mode, int acc,
-                 int sched, int tile, int cap, int stage, unsigned long long *counter, unsigned int *tc,
+int launch_batch(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t t_lo, int64_t total, int format, int mode,
+                 int acc, int sched, int tile, int cap, int stage, unsigned long long *counter, unsigned int *tc,
                  double frac, cudaStream_t s)
 {
     const size_t smem = batch_smem(mode, sched, cap, stage);
     if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
     const bool crac = format == FE_FORMAT_CRAC;
     if (mode == FE_DETERMINISTIC)
-        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
-                    : launch_batch_t<false, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
     switch (sched) {
     case FE_SCHED_THREAD_PER_ENTRY:
-        return crac ? launch_batch_t<true, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
-                    : launch_batch_t<false, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
+        return crac ? launch_batch_t<true, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
+                    : launch_batch_t<false, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
     case FE_SCHED_BLOCK_PER_ELEMENT:
-        return crac ? launch_batch_t<true, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
-                    : launch_batch_t<false, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
+        return crac ? launch_batch_t<true, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
+                    : launch_batch_t<false, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
     case FE_SCHED_WARP_PER_ELEMENT_TMA:
-        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
-                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
     default:
-        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
-                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
     }
+}
+
+template <int NLN, int BB, bool CRAC>
+int launch_rows_t(fe_ctx *ctx, const BatchItemDev *d_items, const RowClass &rc, int tile, int cap, int acc,
+                  unsigned long long *counter, unsigned int *tc, double frac, cudaStream_t s)
+{
+    auto kern = k_batch_rows<NLN, BB, CRAC>;
+    const size_t smem = (size_t)4 * cap * 8;
+    if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
+    if (smem > 48 * 1024) FE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem));
+    if (per_sm < 1) return FE_ERR_UNSUPPORTED;
+    const int64_t want = (rc.t_hi - rc.t_lo + 3) / 4;
+    const int64_t resident = std::max<int64_t>(1, (int64_t)((double)ctx->num_sms * per_sm * frac));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident, want));
+    kern<<<grid, 128, smem, s>>>(d_items, rc.i_lo, rc.i_hi, rc.t_lo, rc.t_hi, tile, cap, acc, counter, tc);
+    fe_note_launch();
+    FE_CUDA(cudaGetLastError());
+    return FE_OK;
+}
+
+// Every kernel of a planned batch on stream s: for FE_DETERMINISTIC the
+// general kernel on the tiles outside the specialised row classes first
+// (those items are the smaller ones of a mixed batch: they complete early),
+// then the row classes; counters: BATCH_COUNTERS tile counters, then the
+// per-item tile counts.
+int launch_plan(fe_ctx *ctx, const BatchItemDev *d_items, int n, const Plan &plan, int format, int mode, int acc,
+                const fe_schedule &sc, unsigned long long *counters, double frac, cudaStream_t s)
+{
+    unsigned int *tc = (unsigned int *)(counters + BATCH_COUNTERS);
+    const int64_t rest = plan.rest_t;
+    if (plan.total_tiles > rest)
+        FE_TRY(launch_batch(ctx, d_items, n, rest, plan.total_tiles, format, mode, acc, sc.kind, sc.tile, plan.cap,
+                            plan.stage, counters, tc, frac, s));
+    if (mode != FE_DETERMINISTIC) return FE_OK;
+    for (size_t k = 0; k < plan.classes.size(); ++k) {
+        const RowClass &rc = plan.classes[k];
+        if (rc.t_hi <= rc.t_lo) continue;
+        const bool crac = format == FE_FORMAT_CRAC;
+        unsigned long long *ctr = counters + 1 + k;
+        if (rc.shape == SH_8_3)
+            FE_TRY(crac ? (launch_rows_t<8, 3, true>(ctx, d_items, rc, sc.tile, plan.cap, acc, ctr, tc, frac, s))
+                        : (launch_rows_t<8, 3, false>(ctx, d_items, rc, sc.tile, plan.cap, acc, ctr, tc, frac, s)));
+        else
+            FE_TRY(crac ? (launch_rows_t<10, 3, true>(ctx, d_items, rc, sc.tile, plan.cap, acc, ctr, tc, frac, s))
+                        : (launch_rows_t<10, 3, false>(ctx, d_items, rc, sc.tile, plan.cap, acc, ctr, tc, frac, s)));
+    }
+    return FE_OK;
 }
 
 bool sched_valid(int mode, const fe_schedule &sc)
@@ -808,8 +950,8 @@ int run_batch(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
     BatchItemDev *d_items = nullptr;
     unsigned long long *counter = nullptr;
     FE_TRY(fe_alloc(ctx, (void **)&d_items, sizeof(BatchItemDev) * n, s));
-    // the tile counter, then two tile counters per item (per-item timestamps)
-    const size_t cbytes = sizeof(unsigned long long) + sizeof(unsigned int) * 2 * (size_t)n;
+    // the tile counters, then two tile counters per item (per-item timestamps)
+    const size_t cbytes = sizeof(unsigned long long) * BATCH_COUNTERS + sizeof(unsigned int) * 2 * (size_t)n;
     int rc = fe_alloc(ctx, (void **)&counter, cbytes, s);
     if (rc == FE_OK) rc = upload(ctx, d_items, plan.host.data(), sizeof(BatchItemDev) * n, s);
     if (rc == FE_OK && cudaMemsetAsync(counter, 0, cbytes, s) != cudaSuccess) rc = FE_ERR_DEVICE;
@@ -818,9 +960,7 @@ int run_batch(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
         fe_note_launch();
         if (cudaGetLastError() != cudaSuccess) rc = FE_ERR_DEVICE;
     }
-    if (rc == FE_OK && plan.total_tiles > 0)
-        rc = launch_batch(ctx, d_items, n, plan.total_tiles, format, mode, acc, sc.kind, sc.tile, plan.cap, plan.stage,
-                          counter, (unsigned int *)(counter + 1), frac, s);
+    if (rc == FE_OK && plan.total_tiles > 0) rc = launch_plan(ctx, d_items, n, plan, format, mode, acc, sc, counter, frac, s);
     fe_free_async(d_items, s);
     fe_free_async(counter, s);
     return rc;
@@ -994,7 +1134,7 @@ int fe_batch_graph_create(fe_ctx *ctx, const fe_batch_item *items, int32_t n_ite
     g->ctx = ctx;
     int rc = FE_OK;
     // the graph's own item table and counter live as long as the graph
-    const size_t cbytes = sizeof(unsigned long long) + sizeof(unsigned int) * 2 * (size_t)n_items;
+    const size_t cbytes = sizeof(unsigned long long) * BATCH_COUNTERS + sizeof(unsigned int) * 2 * (size_t)n_items;
     if (cudaMalloc((void **)&g->d_items, sizeof(BatchItemDev) * n_items) != cudaSuccess ||
         cudaMalloc((void **)&g->counter, cbytes) != cudaSuccess)
         rc = FE_ERR_OOM;
@@ -1013,8 +1153,7 @@ int fe_batch_graph_create(fe_ctx *ctx, const fe_batch_item *items, int32_t n_ite
             if (cudaGetLastError() != cudaSuccess) lrc = FE_ERR_DEVICE;
         }
         if (lrc == FE_OK && plan.total_tiles > 0)
-            lrc = launch_batch(ctx, g->d_items, n_items, plan.total_tiles, format, mode, accumulate, sc.kind, sc.tile,
-                               plan.cap, plan.stage, g->counter, (unsigned int *)(g->counter + 1), 1.0, cs);
+            lrc = launch_plan(ctx, g->d_items, n_items, plan, format, mode, accumulate, sc, g->counter, 1.0, cs);
         const cudaError_t ec = cudaStreamEndCapture(cs, &g->graph);
         rc = lrc != FE_OK ? lrc : (ec == cudaSuccess ? FE_OK : FE_ERR_DEVICE);
     }
