@@ -333,7 +333,7 @@ template <bool CRAC, int SCHED>
 __global__ void __launch_bounds__(sched_threads(SCHED), SCHED == FE_SCHED_WARP_PER_ROW ? 7 : 1) k_batch(const BatchItemDev *__restrict__ items, int n_items,
                                                          int64_t t_lo, int64_t total_tiles, int tile, int cap,
                                                          int accumulate, unsigned long long *counter, int stage,
-                                                         int *status, unsigned int *tc)
+                                                         int *status, unsigned int *tc, int max_tiles)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long block_tile;
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(sched_threads(SCHED), SCHED == FE_SCHED_WARP_P
         int64_t *base_s = (int64_t *)smem_raw;            // [FE_MAX_NLOC] row starts
         int32_t *k_s = (int32_t *)(base_s + FE_MAX_NLOC);  // [FE_MAX_NLOC] run index (CRAC)
         int32_t *off_s = k_s + FE_MAX_NLOC;                // [FE_MAX_NLOC] offset in run (CRAC)
-        for (;;) {
+        for (int nt = 0; nt < max_tiles; ++nt) {
             if (threadIdx.x == 0) block_tile = (unsigned long long)t_lo + atomicAdd(counter, 1ull);
             __syncthreads();
             const unsigned long long t = block_tile;
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(sched_threads(SCHED), SCHED == FE_SCHED_WARP_P
         __syncwarp();
         const uint64_t pol = fe_policy_evict_first();
         uint32_t phase = 0;
-        for (;;) {
+        for (int nt = 0; nt < max_tiles; ++nt) {
             unsigned long long t = 0;
             if (lane == 0) t = (unsigned long long)t_lo + atomicAdd(counter, 1ull);
             t = __shfl_sync(0xffffffffu, t, 0);
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(sched_threads(SCHED), SCHED == FE_SCHED_WARP_P
             if (lane == 0) tile_finished(it, ii, tc, tile);
         }
     } else {
-        for (;;) {
+        for (int nt = 0; nt < max_tiles; ++nt) {
             unsigned long long t = 0;
             if (lane == 0) t = (unsigned long long)t_lo + atomicAdd(counter, 1ull);
             t = __shfl_sync(0xffffffffu, t, 0);
@@ -517,12 +517,12 @@ __global__ void k_batch_zero(const BatchItemDev *__restrict__ items, int n_items
 template <int NLN, int BB, bool CRAC>
 __global__ void __launch_bounds__(128, 9) k_batch_rows(const BatchItemDev *__restrict__ items, int i_lo, int i_hi,
                                                        int64_t t_lo, int64_t t_hi, int tile, int cap, int accumulate,
-                                                       unsigned long long *counter, unsigned int *tc)
+                                                       unsigned long long *counter, unsigned int *tc, int max_tiles)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     double *acc = (double *)smem_raw + (size_t)(threadIdx.x >> 5) * cap;
-    for (;;) {
+    for (int nt = 0; nt < max_tiles; ++nt) {
         unsigned long long t = 0;
         if (lane == 0) t = (unsigned long long)t_lo + atomicAdd(counter, 1ull);
         t = __shfl_sync(0xffffffffu, t, 0);
@@ -669,7 +669,7 @@ size_t batch_smem(int mode, int sched, int cap, int stage)
 template <bool CRAC, int SCHED>
 int launch_batch_t(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t t_lo, int64_t total, int tile, int cap,
                    int acc, unsigned long long *counter, size_t smem, int stage, unsigned int *tc, double frac,
-                   cudaStream_t s)
+                   int max_tiles, cudaStream_t s)
 {
     auto kern = k_batch<CRAC, SCHED>;
     constexpr int threads = sched_threads(SCHED);
@@ -681,8 +681,13 @@ int launch_batch_t(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t t_lo
                                                              : (total - t_lo + threads / 32 - 1) / (threads / 32);
     // frac < 1: the persistent grid takes only that share of the resident blocks
     const int64_t resident = std::max<int64_t>(1, (int64_t)((double)ctx->num_sms * per_sm * frac));
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident, want));
-    kern<<<grid, threads, smem, s>>>(d_items, n, t_lo, total, tile, cap, acc, counter, stage, ctx->d_status, tc);
+    int64_t blocks = std::min<int64_t>(resident, want);
+    // max_tiles > 0: every warp (block) takes at most that many tiles, and the
+    // grid has as many blocks as the tiles need
+    if (max_tiles > 0) blocks = (want + max_tiles - 1) / max_tiles;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, INT32_MAX));
+    kern<<<grid, threads, smem, s>>>(d_items, n, t_lo, total, tile, cap, acc, counter, stage, ctx->d_status, tc,
+                                     max_tiles > 0 ? max_tiles : INT32_MAX);
     fe_note_launch();
     FE_CUDA(cudaGetLastError());
     return FE_OK;
@@ -690,33 +695,33 @@ int launch_batch_t(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t t_lo
 
 int launch_batch(fe_ctx *ctx, const BatchItemDev *d_items, int n, int64_t t_lo, int64_t total, int format, int mode,
                  int acc, int sched, int tile, int cap, int stage, unsigned long long *counter, unsigned int *tc,
-                 double frac, cudaStream_t s)
+                 double frac, int max_tiles, cudaStream_t s)
 {
     const size_t smem = batch_smem(mode, sched, cap, stage);
     if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
     const bool crac = format == FE_FORMAT_CRAC;
     if (mode == FE_DETERMINISTIC)
-        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
-                    : launch_batch_t<false, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, max_tiles, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ROW>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, max_tiles, s);
     switch (sched) {
     case FE_SCHED_THREAD_PER_ENTRY:
-        return crac ? launch_batch_t<true, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
-                    : launch_batch_t<false, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
+        return crac ? launch_batch_t<true, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, max_tiles, s)
+                    : launch_batch_t<false, FE_SCHED_THREAD_PER_ENTRY>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, max_tiles, s);
     case FE_SCHED_BLOCK_PER_ELEMENT:
-        return crac ? launch_batch_t<true, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
-                    : launch_batch_t<false, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
+        return crac ? launch_batch_t<true, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, max_tiles, s)
+                    : launch_batch_t<false, FE_SCHED_BLOCK_PER_ELEMENT>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, max_tiles, s);
     case FE_SCHED_WARP_PER_ELEMENT_TMA:
-        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
-                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, max_tiles, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT_TMA>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, max_tiles, s);
     default:
-        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s)
-                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, s);
+        return crac ? launch_batch_t<true, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, max_tiles, s)
+                    : launch_batch_t<false, FE_SCHED_WARP_PER_ELEMENT>(ctx, d_items, n, t_lo, total, tile, cap, acc, counter, smem, stage, tc, frac, max_tiles, s);
     }
 }
 
 template <int NLN, int BB, bool CRAC>
 int launch_rows_t(fe_ctx *ctx, const BatchItemDev *d_items, const RowClass &rc, int tile, int cap, int acc,
-                  unsigned long long *counter, unsigned int *tc, double frac, cudaStream_t s)
+                  unsigned long long *counter, unsigned int *tc, double frac, int max_tiles, cudaStream_t s)
 {
     auto kern = k_batch_rows<NLN, BB, CRAC>;
     const size_t smem = (size_t)4 * cap * 8;
@@ -727,8 +732,11 @@ int launch_rows_t(fe_ctx *ctx, const BatchItemDev *d_items, const RowClass &rc, 
     if (per_sm < 1) return FE_ERR_UNSUPPORTED;
     const int64_t want = (rc.t_hi - rc.t_lo + 3) / 4;
     const int64_t resident = std::max<int64_t>(1, (int64_t)((double)ctx->num_sms * per_sm * frac));
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident, want));
-    kern<<<grid, 128, smem, s>>>(d_items, rc.i_lo, rc.i_hi, rc.t_lo, rc.t_hi, tile, cap, acc, counter, tc);
+    int64_t blocks = std::min<int64_t>(resident, want);
+    if (max_tiles > 0) blocks = (want + max_tiles - 1) / max_tiles;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, INT32_MAX));
+    kern<<<grid, 128, smem, s>>>(d_items, rc.i_lo, rc.i_hi, rc.t_lo, rc.t_hi, tile, cap, acc, counter, tc,
+                                 max_tiles > 0 ? max_tiles : INT32_MAX);
     fe_note_launch();
     FE_CUDA(cudaGetLastError());
     return FE_OK;
@@ -740,13 +748,13 @@ int launch_rows_t(fe_ctx *ctx, const BatchItemDev *d_items, const RowClass &rc, 
 // then the row classes; counters: BATCH_COUNTERS tile counters, then the
 // per-item tile counts.
 int launch_plan(fe_ctx *ctx, const BatchItemDev *d_items, int n, const Plan &plan, int format, int mode, int acc,
-                const fe_schedule &sc, unsigned long long *counters, double frac, cudaStream_t s)
+                const fe_schedule &sc, unsigned long long *counters, double frac, int max_tiles, cudaStream_t s)
 {
     unsigned int *tc = (unsigned int *)(counters + BATCH_COUNTERS);
     const int64_t rest = plan.rest_t;
     if (plan.total_tiles > rest)
         FE_TRY(launch_batch(ctx, d_items, n, rest, plan.total_tiles, format, mode, acc, sc.kind, sc.tile, plan.cap,
-                            plan.stage, counters, tc, frac, s));
+                            plan.stage, counters, tc, frac, max_tiles, s));
     if (mode != FE_DETERMINISTIC) return FE_OK;
     for (size_t k = 0; k < plan.classes.size(); ++k) {
         const RowClass &rc = plan.classes[k];
@@ -754,11 +762,11 @@ int launch_plan(fe_ctx *ctx, const BatchItemDev *d_items, int n, const Plan &pla
         const bool crac = format == FE_FORMAT_CRAC;
         unsigned long long *ctr = counters + 1 + k;
         if (rc.shape == SH_8_3)
-            FE_TRY(crac ? (launch_rows_t<8, 3, true>(ctx, d_items, rc, sc.tile, plan.cap, acc, ctr, tc, frac, s))
-                        : (launch_rows_t<8, 3, false>(ctx, d_items, rc, sc.tile, plan.cap, acc, ctr, tc, frac, s)));
+            FE_TRY(crac ? (launch_rows_t<8, 3, true>(ctx, d_items, rc, sc.tile, plan.cap, acc, ctr, tc, frac, max_tiles, s))
+                        : (launch_rows_t<8, 3, false>(ctx, d_items, rc, sc.tile, plan.cap, acc, ctr, tc, frac, max_tiles, s)));
         else
-            FE_TRY(crac ? (launch_rows_t<10, 3, true>(ctx, d_items, rc, sc.tile, plan.cap, acc, ctr, tc, frac, s))
-                        : (launch_rows_t<10, 3, false>(ctx, d_items, rc, sc.tile, plan.cap, acc, ctr, tc, frac, s)));
+            FE_TRY(crac ? (launch_rows_t<10, 3, true>(ctx, d_items, rc, sc.tile, plan.cap, acc, ctr, tc, frac, max_tiles, s))
+                        : (launch_rows_t<10, 3, false>(ctx, d_items, rc, sc.tile, plan.cap, acc, ctr, tc, frac, max_tiles, s)));
     }
     return FE_OK;
 }
@@ -943,7 +951,7 @@ int upload(fe_ctx *ctx, void *dst, const void *src, size_t n, cudaStream_t s)
 // Plan upload + launch on stream s.  The item table and the tile counter are
 // stream-ordered allocations freed after the launch.
 int run_batch(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mode, int acc, fe_schedule sc,
-              cudaStream_t s, double frac = 1.0)
+              cudaStream_t s, double frac = 1.0, int max_tiles = 0)
 {
     Plan plan;
     FE_TRY(make_plan(ctx, items, n, format, mode, sc.tile, plan));
@@ -960,7 +968,8 @@ int run_batch(fe_ctx *ctx, const fe_batch_item *items, int n, int format, int mo
         fe_note_launch();
         if (cudaGetLastError() != cudaSuccess) rc = FE_ERR_DEVICE;
     }
-    if (rc == FE_OK && plan.total_tiles > 0) rc = launch_plan(ctx, d_items, n, plan, format, mode, acc, sc, counter, frac, s);
+    if (rc == FE_OK && plan.total_tiles > 0)
+        rc = launch_plan(ctx, d_items, n, plan, format, mode, acc, sc, counter, frac, max_tiles, s);
     fe_free_async(d_items, s);
     fe_free_async(counter, s);
     return rc;
@@ -1009,7 +1018,7 @@ int fe_assemble_batch(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, 
 // holds every SM until its last tile is done, and a running block is never
 // preempted by a higher-priority stream's).
 int fe_assemble_batch_share(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
-                            int32_t accumulate, void *stream, double frac)
+                            int32_t accumulate, void *stream, double frac, int max_tiles)
 {
     if (!ctx || n_items <= 0 || !items || !(frac > 0.0 && frac <= 1.0)) return FE_ERR_INVALID_ARG;
     if ((format != FE_FORMAT_CSR && format != FE_FORMAT_CRAC) || (mode != FE_ATOMIC && mode != FE_DETERMINISTIC) ||
@@ -1024,7 +1033,7 @@ int fe_assemble_batch_share(fe_ctx *ctx, const fe_batch_item *items, int32_t n_i
         auto it = st->tuned.find(signature(items, n_items, format, mode));
         if (it != st->tuned.end()) sc = it->second;
     }
-    return run_batch(ctx, items, n_items, format, mode, accumulate, sc, (cudaStream_t)stream, frac);
+    return run_batch(ctx, items, n_items, format, mode, accumulate, sc, (cudaStream_t)stream, frac, max_tiles);
 }
 
 extern "C" {
@@ -1153,7 +1162,7 @@ int fe_batch_graph_create(fe_ctx *ctx, const fe_batch_item *items, int32_t n_ite
             if (cudaGetLastError() != cudaSuccess) lrc = FE_ERR_DEVICE;
         }
         if (lrc == FE_OK && plan.total_tiles > 0)
-            lrc = launch_plan(ctx, g->d_items, n_items, plan, format, mode, accumulate, sc, g->counter, 1.0, cs);
+            lrc = launch_plan(ctx, g->d_items, n_items, plan, format, mode, accumulate, sc, g->counter, 1.0, 0, cs);
         const cudaError_t ec = cudaStreamEndCapture(cs, &g->graph);
         rc = lrc != FE_OK ? lrc : (ec == cudaSuccess ? FE_OK : FE_ERR_DEVICE);
     }

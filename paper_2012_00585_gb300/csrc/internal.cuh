@@ -125,9 +125,13 @@ int fe_assemble_rowlock(const fe_pattern *p, const double *K, double *values, in
 
 void fe_batch_state_destroy(fe_ctx *ctx);
 // fe_assemble_batch with the persistent grid limited to a share of the GPU
-// (batch.cu; used by the server for large requests).
+// (batch.cu; used by the server for large requests), or, with max_tiles > 0,
+// with blocks that take at most max_tiles tiles per warp and exit (a grid of
+// as many blocks as the tiles need), so that the SMs turn over every few
+// tiles and kernels of higher-priority streams get them quickly (the
+// server's small groups).
 int fe_assemble_batch_share(fe_ctx *ctx, const fe_batch_item *items, int32_t n_items, int32_t format, int32_t mode,
-                            int32_t accumulate, void *stream, double frac);
+                            int32_t accumulate, void *stream, double frac, int max_tiles = 0);
 
 // Host-side count of kernel launches made by this library (all threads).
 void fe_note_launch();

@@ -126,6 +126,8 @@ constexpr int N_BIG_STREAMS = 2;
 // memory bandwidth; small requests still progress beside it).
 constexpr double BIG_SHARE = 0.75;
 constexpr double SMALL_SHARE_BESIDE_BIG = 0.25;
+// Tiles a warp of a small group's kernel takes before its block exits.
+constexpr int SMALL_MAX_TILES = 2;
 
 bool is_big(const fe_request &r) { return r.n_elem * (int64_t)r.dofs_per_elem * r.dofs_per_elem >= BIG_ENTRIES; }
 
@@ -325,8 +327,12 @@ void run_launch(fe_server *sv, LaunchJob &job, std::unique_lock<std::mutex> &lk)
     int rc = FE_OK;
     if (!items.empty()) {
         FeRange range("serve: batched launch");
+        // a large request: a persistent grid on a share of the GPU, on a
+        // high-priority stream; a small group: blocks of a few tiles each,
+        // so that SMs turn over often and the high-priority streams' kernels
+        // (pattern builds, large requests) are not held behind it
         rc = fe_assemble_batch_share(sv->ctx, items.data(), (int32_t)items.size(), job.fmt, job.mode, 0, s,
-                                     job.share);
+                                     job.share, job.big ? 0 : SMALL_MAX_TILES);
         if (rc == FE_OK && cudaEventCreate(&g.done) != cudaSuccess) rc = FE_ERR_DEVICE;
         if (rc == FE_OK && cudaEventRecord(g.done, s) != cudaSuccess) rc = FE_ERR_DEVICE;
     }

@@ -394,7 +394,8 @@ def test_small_request_passes_a_waiting_large_one(ctx):
         side = torch.cuda.Stream()
         ev = torch.cuda.Event()
         with torch.cuda.stream(side):
-            torch.cuda._sleep(int(5e9))  # about 2.4 s at GB300 clocks: S is done long before
+            for _ in range(3):  # about 2.2 s at GB300 clocks (3 x 1.5e9 cycles): S is done long before
+                torch.cuda._sleep(int(1.5e9))
             ev.record(side)
         (ta,) = fe.fe_batch_submit(sv, [fe.make_request(1, Dd, n_dofs, k_ref=Krd, seed=1, ready_event=ev)])
         (tb,) = fe.fe_batch_submit(sv, [fe.make_request(2, Dd, n_dofs, k_ref=Krd, seed=2)])
