@@ -578,15 +578,41 @@ __global__ void __launch_bounds__(256) k_expand_maps(
     int32_t *ks = kbuf + (size_t)(threadIdx.x >> 5) * 3 * cap;  // the row's blocks
     int32_t *rf = ks + cap;                                      // first block of each run
     int32_t *rk = rf + cap;                                      // its position in the row
-    for (int64_t v = fe_warp_id(); v < n_nodes; v += fe_warps()) {
-        const int L = node_len[v];
-        const int R2 = node_runs2[v];
-        const int64_t a = adj_ptr[v], b = adj_ptr[v + 1];
+    // The next row's sizes and offsets are loaded one row ahead, and a row's
+    // keys and its first 32 incidences are loaded together as soon as the
+    // row starts, so that a row waits for two rounds of loads (these, then
+    // the elements' blocks of its maps) instead of a chain of five.
+    const int64_t W = fe_warps();
+    int64_t v = fe_warp_id();
+    int L_n = 0, R2_n = 0;
+    int64_t a_n = 0, b_n = 0, nrp_n = 0, ncp_n = 0;
+    if (v < n_nodes) {
+        L_n = node_len[v];
+        R2_n = node_runs2[v];
+        a_n = adj_ptr[v];
+        b_n = adj_ptr[v + 1];
+        nrp_n = nrp[v];
+        ncp_n = ncp[v];
+    }
+    for (; v < n_nodes; v += W) {
+        const int L = L_n;
+        const int R2 = R2_n;
+        const int64_t a = a_n, b = b_n;
+        const int64_t rb0 = (int64_t)B * B * nrp_n;
+        const int64_t cb0 = (int64_t)B * ncp_n;
         const int32_t *kv_g = keys + a * nln;
         for (int k = lane; k < L; k += 32) ks[k] = kv_g[k];
+        const uint32_t t_l = lane < b - a ? adj[a + lane] : 0u;  // incidence a + lane
+        if (v + W < n_nodes) {
+            const int64_t u = v + W;
+            L_n = node_len[u];
+            R2_n = node_runs2[u];
+            a_n = adj_ptr[u];
+            b_n = adj_ptr[u + 1];
+            nrp_n = nrp[u];
+            ncp_n = ncp[u];
+        }
         __syncwarp();
-        const int64_t rb0 = (int64_t)B * B * nrp[v];
-        const int64_t cb0 = (int64_t)B * ncp[v];
         for (int j = lane; j < B; j += 32) {
             row_ptr[(int64_t)B * v + j] = rb0 + (int64_t)j * B * L;
             crac_ptr[(int64_t)B * v + j] = cb0 + (int64_t)j * R2;
@@ -620,10 +646,13 @@ __global__ void __launch_bounds__(256) k_expand_maps(
         __syncwarp();
         if (map) {
             const int total = (int)(b - a) * nln;
-            for (int q = lane; q < total; q += 32) {
+            for (int q0 = 0; q0 < total; q0 += 32) {  // uniform trip count: the shuffle takes every lane
+                const int q = q0 + lane;
                 const int s_ = q / nln;
                 const int kc = q - s_ * nln;
-                const uint32_t t = adj[a + s_];
+                uint32_t t = __shfl_sync(0xffffffffu, t_l, s_ & 31);
+                if (q >= total) continue;
+                if (s_ >= 32) t = adj[a + s_];
                 const int32_t j = N[(int64_t)(t / (uint32_t)nln) * nln + kc];
                 int lo = 0, hi = L;
                 while (lo < hi) {
@@ -636,10 +665,13 @@ __global__ void __launch_bounds__(256) k_expand_maps(
         }
         if (mapc) {
             const int total = (int)(b - a) * rmax;
-            for (int q = lane; q < total; q += 32) {
+            for (int q0 = 0; q0 < total; q0 += 32) {
+                const int q = q0 + lane;
                 const int s_ = q / rmax;
                 const int ri = q - s_ * rmax;
-                const uint32_t t = adj[a + s_];
+                uint32_t t = __shfl_sync(0xffffffffu, t_l, s_ & 31);
+                if (q >= total) continue;
+                if (s_ >= 32) t = adj[a + s_];
                 const int64_t e = t / (uint32_t)nln;
                 const int k = (int)(t - (uint32_t)(e * nln));
                 const uint32_t *m = uniform_R ? run_mask : run_mask + e * mask_words;
